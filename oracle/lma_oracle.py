@@ -107,15 +107,24 @@ class _Cov:
 
 
 def fit(prob, B: int | None = None, keep_blocks: bool = False) -> LMAFit:
-    """Definition 1 per block, Definition 2 sums, alpha, summary-form loglik."""
+    """Definition 1 per block, Definition 2 sums, alpha, summary-form loglik.
+
+    The support-set columns are taken in the whitened basis
+    Sigma_DS L_SS^-T (L_SS = chol(Sigma_SS)): every quantity of Section 3 is
+    invariant under an invertible change of basis of the support coordinates
+    (Q_BB' = Sigma_BS Sigma_SS^-1 Sigma_SB' does not change), and in this basis
+    Sigma_SS becomes I, so the global summary I + L^-1 (Sigma-ddot_SS -
+    Sigma_SS) L^-T no longer inherits the jitter-level conditioning of
+    Sigma_SS.  The paper-basis summaries are recovered as
+    y-ddot_S = L y-ddot and Sigma-ddot_SS = L (I + A) L^T."""
     B = prob.B if B is None else int(B)
     cv = _Cov(prob)
     ptr = prob.block_ptr
     M = len(ptr) - 1
     s = prob.S.shape[0]
     r = prob.y - prob.mean
-    ydd = np.zeros(s)
-    Sdd = np.zeros((s, s))
+    ydd = np.zeros(s)          # whitened y-ddot
+    A = np.zeros((s, s))       # whitened sum of Sigma-dot^T R-dot Sigma-dot
     quad = 0.0
     logdet_R = 0.0
     blocks = []
@@ -124,38 +133,44 @@ def fit(prob, B: int | None = None, keep_blocks: bool = False) -> LMAFit:
         last = min(m + B, M - 1)
         Bk = np.arange(ptr[m + 1], ptr[last + 1]) if last > m else np.zeros(0, dtype=np.int64)
         R_II = cv.R_train(I, I)
-        K_IS = cv.KS(prob.X[I])
+        W_I = cv.W(prob.X[I]).T                                             # Sigma_{D_m S} L^-T
         if Bk.size:
             R_IB = cv.R_train(I, Bk)
             R_BB = cv.R_train(Bk, Bk)
             Rp = sla.cho_solve(sla.cho_factor(R_BB, lower=True), R_IB.T).T      # R' = R_IB R_BB^-1
             ydot = r[I] - Rp @ r[Bk]
             Rdot_inv = R_II - Rp @ R_IB.T
-            Sdot = K_IS - Rp @ cv.KS(prob.X[Bk])
+            Sdot = W_I - Rp @ cv.W(prob.X[Bk]).T
         else:
             Rp = np.zeros((I.size, 0))
             ydot = r[I].copy()
             Rdot_inv = R_II
-            Sdot = K_IS
+            Sdot = W_I
         cf = sla.cho_factor(Rdot_inv, lower=True)
         t = sla.cho_solve(cf, np.column_stack([ydot, Sdot]))                 # R-dot [y-dot, Sigma-dot]
         ydd += Sdot.T @ t[:, 0]
-        Sdd += Sdot.T @ t[:, 1:]
+        A += Sdot.T @ t[:, 1:]
         quad += float(ydot @ t[:, 0])
         logdet_R += _logdet_chol(np.tril(cf[0]))
         if keep_blocks:
-            blocks.append(dict(I=I, Bk=Bk, Rp=Rp, ydot=ydot, Rdot_inv=Rdot_inv, Sdot=Sdot))
-    Sdd = 0.5 * (Sdd + Sdd.T)
-    Sdd_SS = cv.Sigma_SS + Sdd
-    cfS = sla.cho_factor(Sdd_SS, lower=True)
-    alpha = sla.cho_solve(cfS, ydd)
+            blocks.append(dict(I=I, Bk=Bk, Rp=Rp, ydot=ydot, Rdot_inv=Rdot_inv,
+                               Sdot=Sdot @ cv.L_SS.T))                        # paper basis
+    A = 0.5 * (A + A.T)
+    C = np.eye(s) + A
+    Lc = np.linalg.cholesky(C)
+    w = sla.solve_triangular(Lc, ydd, lower=True)
+    beta = sla.solve_triangular(Lc, w, lower=True, trans="T")              # C^-1 y-ddot
+    L = cv.L_SS
+    alpha = sla.solve_triangular(L, beta, lower=True, trans="T")           # Sigma-ddot_SS^-1 y-ddot_S
     N = prob.X.shape[0]
-    loglik = (-0.5 * (quad - ydd @ alpha)
-              - 0.5 * (logdet_R + _logdet_chol(np.tril(cfS[0])) - _logdet_chol(cv.L_SS))
+    loglik = (-0.5 * (quad - w @ w)
+              - 0.5 * (logdet_R + _logdet_chol(Lc))
               - 0.5 * N * LOG2PI)
-    return LMAFit(prob=prob, B=B, Sigma_SS=cv.Sigma_SS, L_SS=cv.L_SS, ydd_S=ydd,
-                  Sdd_SS=Sdd_SS, alpha=alpha, quad=quad, logdet_R=logdet_R,
-                  loglik=float(loglik), blocks=blocks)
+    f = LMAFit(prob=prob, B=B, Sigma_SS=cv.Sigma_SS, L_SS=L, ydd_S=L @ ydd,
+               Sdd_SS=L @ C @ L.T, alpha=alpha, quad=quad, logdet_R=logdet_R,
+               loglik=float(loglik), blocks=blocks)
+    f.A_white, f.ydd_white, f.Lc, f.beta = A, ydd, Lc, beta
+    return f
 
 
 def residual_e(f: LMAFit) -> np.ndarray:
@@ -164,7 +179,7 @@ def residual_e(f: LMAFit) -> np.ndarray:
     cv = _Cov(p)
     out = np.empty(p.X.shape[0])
     for i in range(0, p.X.shape[0], 8192):
-        out[i:i + 8192] = p.y[i:i + 8192] - p.mean - cv.KS(p.X[i:i + 8192]) @ f.alpha
+        out[i:i + 8192] = p.y[i:i + 8192] - p.mean - cv.W(p.X[i:i + 8192]).T @ f.beta
     return out
 
 
@@ -210,7 +225,6 @@ def predict(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True,
     U = XU.shape[0]
     mean = np.full(U, np.nan)
     var = np.full(U, np.nan)
-    cfS = sla.cho_factor(f.Sdd_SS, lower=True)
     it = range(M) if blocks is None else blocks
     for n in it:
         u = np.arange(tptr[n], tptr[n + 1])
@@ -224,13 +238,15 @@ def predict(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True,
         WJ = cv.W(XJ)
         Ru = cv.K(XJ, Xu) - WJ.T @ Wu                       # R_{D_J u} (u not in D: no noise)
         Z = P @ Ru                                          # columns z_u^T
-        KuS = cv.KS(Xu)
-        eJ = p.y[rows] - p.mean - cv.KS(XJ) @ f.alpha
-        mean[u] = p.mean + KuS @ f.alpha + Z.T @ eJ
-        g = cv.KS(XJ).T @ Z - KuS.T                         # s x |u|
+        # whitened support basis: Sigma_uS alpha = W_u^T beta, and with
+        # h = L_SS^-1 g:  g^T Sigma-ddot_SS^-1 g = h^T (I + A)^-1 h
+        eJ = p.y[rows] - p.mean - WJ.T @ f.beta
+        mean[u] = p.mean + Wu.T @ f.beta + Z.T @ eJ
+        h = WJ @ Z - Wu                                     # L_SS^-1 (Sigma_{S D_J} z^T - Sigma_Su)
+        hc = sla.solve_triangular(f.Lc, h, lower=True)
         prior = cv.ss2 + (cv.sn2 if noisy else 0.0)
         var[u] = (prior - np.sum(Wu * Wu, axis=0) - np.sum(Ru * Z, axis=0)
-                  + np.sum(g * sla.cho_solve(cfS, g), axis=0))
+                  + np.sum(hc * hc, axis=0))
     return mean, var
 
 
@@ -310,10 +326,8 @@ def loglik_grad(prob, B: int | None = None) -> tuple[float, np.ndarray]:
     Vt = np.empty((N, s))
     for i in range(0, N, 8192):
         Vt[i:i + 8192] = cv.W(p.X[i:i + 8192]).T
-    beta = L.T @ f.alpha                                     # C^-1 y_V (alpha = L^-T beta)
-    C = sla.solve_triangular(L, sla.solve_triangular(L, f.Sdd_SS, lower=True).T, lower=True)
-    C = 0.5 * (C + C.T)
-    Lc = np.linalg.cholesky(C)
+    beta = f.beta                                            # C^-1 y_V
+    Lc = f.Lc                                                # chol(C), C = I + A
     Cinv = sla.cho_solve((Lc, True), np.eye(s))
     r = p.y - p.mean
     e = r - Vt @ beta
