@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""LMA fit+predict throughput on one GB300 (or N replicas under torchrun).
+
+One step = the whole hot path on one batch of synthetic input: lma_fit (SE-ARD
+blocks, residual windows, blanket-first factorisations and solves, local
+summaries reduced into the global summary, the FP64 global step) followed by
+lma_predict on the test set (local route).  The workload is the C2
+configuration: N=40,960 5-D inputs, |S|=512, 64 blocks of 640 in k-means
+order, Markov order B (default 1), 4,096 test points.
+
+Metric: training points per second of fit+predict (and TFLOP/s of the
+algorithmic flop count), mixed form, next to the plain FP64 GPU form and the
+FP64 CPU oracle timed on the host cores on a bounded sample.
+`--impl reference` times that oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+# ----------------------------------------------------------------------------
+# algorithmic counts (flop = 2 per multiply-add)
+def window_sizes(bptr, B):
+    M = len(bptr) - 1
+    out = []
+    for m in range(M):
+        last = min(m + B, M - 1)
+        out.append((int(bptr[last + 1] - bptr[m]), int(bptr[m + 1] - bptr[m]), int(bptr[last + 1] - bptr[m + 1])))
+    return out
+
+
+def fit_flops(p, B):
+    s, N = p.s, p.N
+    f = N * s * s + 2.0 * s ** 3 / 3.0
+    for n, b, nb in window_sizes(p.block_ptr, B):
+        f += s * n * n + n ** 3 / 3.0 + n * n * (s + 1) + b * s * s
+    return f
+
+
+def sweep_flops(p, B):
+    """Factorisation + solve of every window (Cholesky n^3/3 and the s+1 right-hand sides n^2 (s+1))."""
+    s = p.s
+    return sum(n ** 3 / 3.0 + n * n * (s + 1) for n, _, _ in window_sizes(p.block_ptr, B))
+
+
+def predict_flops(p, B):
+    s = p.s
+    ws = window_sizes(p.block_ptr, B)
+    tp = p.test_block_ptr
+    f = 2.0 * p.U * s * s
+    for nb in range(p.M):
+        nu = int(tp[nb + 1] - tp[nb])
+        if nu == 0:
+            continue
+        for m in range(max(0, nb - B), nb + 1):
+            n, b, nbl = ws[m]
+            kept = n if m == nb else b
+            f += nu * (2.0 * n * s + n * n + 2.0 * kept * s)
+    return f
+
+
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={CLOCK_Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline(p, B, n_blocks=6):
+    """FP64 oracle (as it stands) on the first n_blocks blocks of the workload:
+    fit + local-route prediction of their test points, on the host cores."""
+    import numpy as np
+    from oracle import lma_oracle as O2
+    from workloads.synth import Problem
+    k = min(n_blocks, p.M)
+    nsub = int(p.block_ptr[k])
+    usub = int(p.test_block_ptr[k])
+    sub = Problem(name=p.name + "-sample", X=p.X[:nsub], y=p.y[:nsub], block_ptr=p.block_ptr[:k + 1].copy(),
+                  S=p.S, XU=p.XU[:usub], yU=p.yU[:usub], test_block_ptr=p.test_block_ptr[:k + 1].copy(),
+                  log_ell=p.log_ell, log_sigma_s=p.log_sigma_s, log_sigma_n=p.log_sigma_n, jitter=p.jitter,
+                  mean=p.mean, B=min(B, k - 1))
+    t0 = time.perf_counter()
+    f = O2.fit(sub)
+    O2.predict(f)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v):
+            cores = int(os.environ[v])
+    return dict(value=nsub / dt, unit="train-points/s", cores=cores, kind="oracle",
+                sample=f"first {k} of {p.M} blocks ({nsub} training points, {usub} test points), "
+                       f"same |S|={p.s}, B={sub.B}; fit+predict in {dt:.1f} s"), dt
+
+
+def run_reference(args, p):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    for _ in range(args.warmup):
+        cpu_baseline(p, args.B, n_blocks=args.ref_blocks)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        cb, dt = cpu_baseline(p, args.B, n_blocks=args.ref_blocks)
+        vals.append(dt)
+        last = cb
+    ms = 1e3 * statistics.mean(vals)
+    nsub = int(p.block_ptr[min(args.ref_blocks, p.M)])
+    value = nsub / (ms / 1e3)
+    out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(p, args.B),
+           "cpu_baseline": dict(last, value=value),
+           "e2e": {"value": value, "unit": "train-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def workload_config(p, B):
+    return {"workload": f"C2: N={p.N} d={p.d} |S|={p.s} M={p.M} blocks of {p.N // p.M} (k-means order) "
+                        f"B={B} U={p.U} (RFF SE draw, synthetic)",
+            "N": p.N, "d": p.d, "s": p.s, "M": p.M, "B": B, "U": p.U,
+            "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+
+
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
+    ap.add_argument("--B", type=int, default=1)
+    ap.add_argument("--ref-blocks", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--dominant", default="k_chol_step")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "lma" else args.warmup
+
+    from workloads import make_problem
+    p = make_problem("C2", B=args.B)
+    if args.impl == "reference":
+        run_reference(args, p)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1411_4510_gb300 import build
+    build.build()
+    import paper_1411_4510_gb300 as L
+
+    dev = torch.device("cuda", local)
+    X = torch.as_tensor(p.X, device=dev)
+    y = torch.as_tensor(p.y, device=dev)
+    S = torch.as_tensor(p.S, device=dev)
+    XU = torch.as_tensor(p.XU, device=dev)
+    kw = dict(block_ptr=p.block_ptr, B=args.B, log_ell=p.log_ell, log_sigma_s=p.log_sigma_s,
+              log_sigma_n=p.log_sigma_n, jitter=p.jitter, mean=p.mean)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step(prec=L.MIXED, host=None):
+        if host is None:
+            m = L.lma_fit(X, y, S=S, precision=prec, **kw)
+            return m, L.lma_predict(m, XU, p.test_block_ptr)
+        m = L.lma_fit(host["X"], host["y"], S=host["S"], precision=prec, **kw)
+        return m, L.lma_predict(m, host["XU"], p.test_block_ptr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def timed(nsteps, prec=L.MIXED, host=None, profile=None):
+        evs = []
+        n0 = L.lma_kernel_launch_count()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            L.profile_start(profile)
+        out = None
+        for _ in range(nsteps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            out = step(prec, host)
+            b.record(st)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        prof = L.profile_stop() if profile else None
+        if world > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, L.lma_kernel_launch_count() - n0, prof, out
+
+    with ClockSampler(local) as clk:
+        ms, launches, prof, (model, (mean, var)) = timed(args.steps, profile=args.dominant)
+    step_ms = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    fit_f, pred_f = fit_flops(p, args.B), predict_flops(p, args.B)
+    value = world * p.N / (step_ms / 1e3)
+    mean_mixed = mean.cpu().numpy()
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    host = {k: torch.as_tensor(v).pin_memory() for k, v in dict(X=p.X, y=p.y, S=p.S, XU=p.XU).items()}
+    ems, _, _, _ = timed(max(3, args.steps // 2), host=host)
+    h2d = 8 * (p.N * p.d + p.N + p.s * p.d + p.U * p.d) + 8 * (p.M + 1) * 2
+    e2e = {"value": world * p.N / (statistics.mean(ems) / 1e3), "unit": "train-points/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * p.U}
+
+    # plain FP64 GPU form (per-window launches) and the mixed form's error against it
+    fp64 = None
+    if not args.no_fp64:
+        step(L.FP64)
+        fms, _, _, (_, (m64, v64)) = timed(2, prec=L.FP64)
+        m64 = m64.cpu().numpy()
+        rm64 = float(np.sqrt(np.mean((m64 - p.yU) ** 2)))
+        rmx = float(np.sqrt(np.mean((mean_mixed - p.yU) ** 2)))
+        fms_mean = statistics.mean(fms)
+        fp64 = {"value": p.N / (fms_mean / 1e3), "ms_per_step": fms_mean,
+                "tflops": (fit_f + pred_f) / (fms_mean / 1e3) / 1e12,
+                "mixed_speedup": fms_mean / step_ms,
+                "mixed_mean_rel_err_vs_fp64": float(np.linalg.norm(mean_mixed - m64) / np.linalg.norm(m64)),
+                "rmse_fp64": rm64, "rmse_mixed": rmx}
+
+    # per-kernel breakdown (one extra, untimed step with every launch bracketed)
+    _, _, prof_all, _ = timed(1, profile="k_")
+
+    # roofline of the dominant kernel, from the launches timed above
+    peaks = load_peaks()
+    clocks = clk.summary()
+    roof = None
+    if prof and args.dominant in prof:
+        tot_ms, n_l = prof[args.dominant]
+        work = sweep_flops(p, args.B) * args.steps
+        achieved = work / (tot_ms / 1e3) / 1e12
+        # SIMT FP32 issue rate: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+        sm_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": args.dominant, "launches_timed": n_l,
+                "avg_launch_ms": tot_ms / n_l,
+                "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived, not measured)",
+                "work": "window factorisation + solve flops (sum n^3/3 + n^2 (s+1)) per step"}
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu, _ = cpu_baseline(p, args.B)
+    out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": workload_config(p, args.B),
+           "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
+           "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
+           "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+           "cpu_baseline": cpu, "fp64_gpu_form": fp64,
+           "kernel_ms_one_step": {k: round(v[0], 4) for k, v in sorted((prof_all or {}).items(), key=lambda kv: -kv[1][0])}}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

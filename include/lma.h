@@ -1,0 +1,179 @@
+/*
+ * lma.h — C ABI of the GB300 LMA library (low-rank-cum-Markov approximation
+ * of Gaussian-process regression; Low, Yu, Chen, Jaillet, AAAI 2015).
+ *
+ * Problem statement (Sections 2-3 of the paper): training inputs D with
+ * outputs y_D, a partition of D into blocks D_1..D_M, a support set S, a
+ * Markov order B, the SE-ARD covariance of Section 5 with hyperparameters
+ * (l_1..l_d, sigma_s, sigma_n) and a constant prior mean mu.
+ *
+ * Conventions for every entry point:
+ *  - The caller owns every input and output buffer; no call keeps a caller
+ *    pointer after it returns.  The library owns an lma_model until
+ *    lma_model_free.
+ *  - All GPU work is ordered on options->cuda_stream (a cudaStream_t passed as
+ *    void*, NULL = the legacy default stream).  Every call synchronises that
+ *    stream before returning, so outputs are valid on return.
+ *  - Errors come back as lma_status codes; nothing aborts and no C++
+ *    exception crosses the ABI.  lma_last_error_info gives details of the
+ *    calling thread's last failure.
+ *  - Index arrays (block_ptr, test_block_ptr) and hyperparameter vectors are
+ *    always HOST memory.  Point arrays are host or device memory as the
+ *    *_on_device flag says; device pointers must be on the current device.
+ *  - All matrices are row-major, doubles.
+ */
+#ifndef LMA_H
+#define LMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LMA_OK = 0,
+  LMA_ERR_INVALID_ARG = 1,  /* a size, pointer or partition is inconsistent            */
+  LMA_ERR_NOT_PD = 2,       /* a residual window or Sigma-ddot_SS lost positive definiteness;
+                               lma_last_error_info reports the block index (-1: support set,
+                               -2: global summary)                                       */
+  LMA_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
+  LMA_ERR_OOM = 4,          /* device memory allocation failed                           */
+  LMA_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                             */
+  LMA_ERR_INTERNAL = 6      /* unexpected internal state                                 */
+} lma_status;
+
+typedef enum {
+  LMA_FP64 = 0,   /* plain FP64 GPU form: every step in double, one window per launch   */
+  LMA_MIXED = 1   /* FP32 covariance tiles / factorisations / solves, batched over all
+                     windows; FP64 for Sigma_SS, the global summary and all reductions   */
+} lma_precision;
+
+typedef struct lma_model lma_model;
+
+/* The data (D, y_D), its partition, the support set and the Markov order.
+ * Section 3: D is partitioned into M disjoint blocks D_1..D_M; the Markov
+ * blanket of block m is D^B_m = D_{m+1} u ... u D_{min(m+B, M)}.          */
+typedef struct {
+  int64_t n;            /* |D|                                                  */
+  int64_t d;            /* input dimension, 1..24                               */
+  int64_t m_blocks;     /* M >= 1                                               */
+  int64_t s;            /* |S| >= 1                                             */
+  int64_t markov_order; /* B in [0, M-1]                                        */
+  const double* X;      /* n*d inputs, rows grouped by block                    */
+  const double* y;      /* n outputs                                            */
+  const int64_t* block_ptr; /* M+1 offsets (HOST): block m owns rows
+                               [block_ptr[m], block_ptr[m+1]); block_ptr[0]=0,
+                               block_ptr[M]=n, every block non-empty            */
+  const double* S;      /* s*d support inputs                                   */
+  double mean;          /* constant prior mean mu                               */
+  int inputs_on_device; /* 1: X, y, S are device pointers; 0: host pointers     */
+} lma_problem;
+
+/* SE-ARD hyperparameters (Section 5):
+ *   sigma_xx' = sigma_s^2 exp(-1/2 sum_i (x_i - x'_i)^2 / l_i^2) + sigma_n^2 delta_xx'.
+ * The noise term is applied to the D-D diagonal only; Sigma_SS and the
+ * cross-covariances with S are noise-free.  `jitter` (absolute, >= 0) is
+ * added to the diagonal of Sigma_SS wherever it appears (in Q and in
+ * Sigma-ddot_SS).                                                           */
+typedef struct {
+  const double* log_ell; /* d log length-scales (HOST)                          */
+  double log_sigma_s;    /* log signal standard deviation                       */
+  double log_sigma_n;    /* log noise standard deviation                        */
+  double jitter;         /* absolute diagonal jitter on Sigma_SS                */
+} lma_hyper;
+
+typedef struct {
+  lma_precision precision;
+  int reserved;          /* must be 0                                           */
+  void* cuda_stream;     /* cudaStream_t or NULL                                */
+} lma_options;
+
+/* Fit: the local summaries of Definition 1 for every block, reduced into the
+ * global summary of Definition 2, then Sigma-ddot_SS^-1 y-ddot_S (Theorem 2).
+ * Per block m the residual R (Section 3: R = Sigma - Q, Q_BB' =
+ * Sigma_BS Sigma_SS^-1 Sigma_SB') over D_m u D^B_m is factorised blanket-first
+ * so that its trailing factor is a square root of R-dot_m^-1 (Lemma 1).
+ * *out receives a model owned by the library.  Returns LMA_ERR_NOT_PD when a
+ * window is not positive definite in the selected precision.               */
+lma_status lma_fit(const lma_problem* problem, const lma_hyper* hyper,
+                   const lma_options* options, lma_model** out);
+
+/* Predictive mean and variance of Theorem 2 (equivalently Eqs. vapmu/vapvar)
+ * for u test inputs XU (u*d) partitioned like D: test block n owns rows
+ * [test_block_ptr[n], test_block_ptr[n+1]) (HOST, M+1 entries, may be empty).
+ * noisy=1 returns the variance of the noisy output (sigma_uu includes
+ * sigma_n^2, the paper's convention), noisy=0 that of the latent function.
+ * mean_out / var_out hold u doubles each, in host or device memory as
+ * io_on_device says (XU likewise).                                         */
+lma_status lma_predict(const lma_model* model, int64_t u, const double* XU,
+                       const int64_t* test_block_ptr, int noisy, int io_on_device,
+                       double* mean_out, double* var_out);
+
+/* log N(y_D; mu, Sigma-bar_DD) of a fitted model (Sigma-bar by Eq. acov). */
+lma_status lma_model_loglik(const lma_model* model, double* out);
+
+/* Fit without keeping a model and return log N(y_D; mu, Sigma-bar_DD).     */
+lma_status lma_loglik(const lma_problem* problem, const lma_hyper* hyper,
+                      const lma_options* options, double* out);
+
+/* Log-likelihood and its gradient with respect to
+ * (log l_1..log l_d, log sigma_s, log sigma_n) (d+2 doubles, host memory),
+ * by a hand-written adjoint that recomputes each window's residual and
+ * factor instead of storing them.  The paper does not differentiate its
+ * likelihood; jitter and the partition are held fixed.                    */
+lma_status lma_loglik_grad(const lma_problem* problem, const lma_hyper* hyper,
+                           const lma_options* options, double* loglik_out,
+                           double* grad_out);
+
+/* Global-summary diagnostics of a fitted model, in the whitened support
+ * coordinates V = L_SS^-1 Sigma_SD (L_SS the Cholesky factor of Sigma_SS):
+ *   A_out   (s*s, host): sum_m Sigma-dot^mT R-dot_m Sigma-dot^m whitened,
+ *                        i.e. L_SS^-1 (Sigma-ddot_SS - Sigma_SS) L_SS^-T
+ *   y_out   (s, host):   L_SS^-1 y-ddot_S
+ *   scalars (4, host):   quad = sum_m y-dot_m^T R-dot_m y-dot_m,
+ *                        log|R-bar_DD|, log|I + A|, loglik
+ * Any output pointer may be NULL.                                          */
+lma_status lma_model_summary(const lma_model* model, double* A_out, double* y_out,
+                             double* scalars_out);
+
+/* The residual R = Sigma - Q over the window D_m u D^B_m of block m, as an
+ * n_w x n_w matrix in natural row order (host memory, n_w = number of rows
+ * of D_m u D^B_m), evaluated by the selected precision's kernels before any
+ * factorisation.  For parity tests of the residual-formation kernel.      */
+lma_status lma_window_residual(const lma_problem* problem, const lma_hyper* hyper,
+                               const lma_options* options, int64_t m, double* out);
+
+/* Number of rows of the window D_m u D^B_m (0 on invalid arguments).      */
+int64_t lma_window_rows(const lma_problem* problem, int64_t m);
+
+void lma_model_free(lma_model* model);
+
+const char* lma_status_string(lma_status status);
+
+/* Details of the calling thread's last failure: the block index for
+ * LMA_ERR_NOT_PD (-1 = Sigma_SS, -2 = Sigma-ddot_SS, otherwise the block),
+ * and a message that stays valid until the thread's next call.  Either
+ * pointer may be NULL.                                                    */
+lma_status lma_last_error_info(int64_t* failed_block, const char** message);
+
+/* Number of kernels this library has launched in the calling process.     */
+int64_t lma_kernel_launch_count(void);
+
+/* Launch profiler (a single-threaded diagnostic, off by default; not part of
+ * the paper's method).  lma_profile_start clears earlier records and, until
+ * lma_profile_stop, brackets every launch whose kernel name contains
+ * name_filter (NULL or "" = every launch) with a CUDA event pair recorded on
+ * the launching stream.  lma_profile_stop waits for those events, writes the
+ * distinct kernel names, newline-separated, into names (names_cap bytes,
+ * NUL-terminated, may be NULL) and their summed milliseconds and launch
+ * counts into total_ms / launches (cap entries each, may be NULL), and
+ * returns the number of distinct names.                                   */
+void lma_profile_start(const char* name_filter);
+int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* launches, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMA_H */

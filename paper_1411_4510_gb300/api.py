@@ -1,0 +1,224 @@
+"""Python binding of the LMA C ABI with the same entry-point names.
+
+Argument marshalling only: arrays are converted to contiguous float64 (numpy
+on the host, torch tensors on the host or the current CUDA device) and their
+pointers are handed to the library; every step of the computation runs in
+the CUDA library.  Device tensors are passed as device pointers together with
+torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _abi
+
+try:
+    import torch
+except Exception:  # pragma: no cover - torch is expected but not required for host use
+    torch = None
+
+FP64 = _abi.LMA_FP64
+MIXED = _abi.LMA_MIXED
+
+
+def _is_cuda_tensor(a) -> bool:
+    return torch is not None and isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _f64(a, keep):
+    """(pointer, on_device) of a contiguous float64 view of `a`; `keep` holds references."""
+    if _is_cuda_tensor(a):
+        t = a.detach().to(torch.float64).contiguous()
+        keep.append(t)
+        return t.data_ptr(), True
+    if torch is not None and isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    keep.append(arr)
+    return arr.ctypes.data, False
+
+
+def _i64(a, keep):
+    if torch is not None and isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    if torch is not None and torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean, precision, stream, keep):
+    n, d = int(X.shape[0]), int(X.shape[1])
+    s = int(S.shape[0])
+    M = int(len(block_ptr) - 1)
+    xp, xdev = _f64(X, keep)
+    yp, ydev = _f64(y, keep)
+    sp, sdev = _f64(S, keep)
+    if not (xdev == ydev == sdev):
+        raise ValueError("X, y and S must all be on the host or all on the device")
+    prob = _abi.lma_problem(n, d, M, s, int(B), xp, yp, _i64(block_ptr, keep), sp, float(mean), int(xdev))
+    le = np.ascontiguousarray(np.broadcast_to(np.asarray(log_ell, dtype=np.float64), (d,)))
+    keep.append(le)
+    hyp = _abi.lma_hyper(le.ctypes.data, float(log_sigma_s), float(log_sigma_n), float(jitter))
+    opt = _abi.lma_options(int(precision), 0, _stream(stream))
+    return prob, hyp, opt
+
+
+@dataclass
+class Model:
+    """A fitted model owned by the library (freed with lma_model_free)."""
+    handle: int
+    n_blocks: int
+    s: int
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                _abi.load().lma_model_free(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def lma_fit(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter=1e-6, mean=0.0,
+            precision=MIXED, stream=None) -> Model:
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    h = C.c_void_p()
+    _abi.check(lib.lma_fit(C.byref(prob), C.byref(hyp), C.byref(opt), C.byref(h)))
+    return Model(h.value, prob.m_blocks, prob.s)
+
+
+def lma_predict(model: Model, XU, test_block_ptr, noisy: bool = True, out=None):
+    """Returns (mean, var): numpy arrays for host input, torch CUDA tensors for device input."""
+    lib = _abi.load()
+    keep = []
+    u = int(XU.shape[0])
+    xp, dev = _f64(XU, keep)
+    tp = _i64(test_block_ptr, keep)
+    if dev:
+        mean = torch.empty(u, dtype=torch.float64, device=XU.device) if out is None else out[0]
+        var = torch.empty(u, dtype=torch.float64, device=XU.device) if out is None else out[1]
+        mp, vp = mean.data_ptr(), var.data_ptr()
+    else:
+        mean = np.empty(u) if out is None else out[0]
+        var = np.empty(u) if out is None else out[1]
+        mp, vp = mean.ctypes.data, var.ctypes.data
+    _abi.check(lib.lma_predict(model.handle, u, xp, tp, int(bool(noisy)), int(dev), mp, vp))
+    return mean, var
+
+
+def lma_model_loglik(model: Model) -> float:
+    out = C.c_double()
+    _abi.check(_abi.load().lma_model_loglik(model.handle, C.byref(out)))
+    return out.value
+
+
+def lma_model_summary(model: Model):
+    s = model.s
+    A = np.empty((s, s))
+    yv = np.empty(s)
+    sc = np.empty(4)
+    _abi.check(_abi.load().lma_model_summary(model.handle, A.ctypes.data, yv.ctypes.data, sc.ctypes.data))
+    return dict(A=A, y=yv, quad=sc[0], logdet_R=sc[1], logdet_C=sc[2], loglik=sc[3])
+
+
+def lma_loglik(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter=1e-6, mean=0.0,
+               precision=MIXED, stream=None) -> float:
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    out = C.c_double()
+    _abi.check(lib.lma_loglik(C.byref(prob), C.byref(hyp), C.byref(opt), C.byref(out)))
+    return out.value
+
+
+def lma_loglik_grad(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter=1e-6, mean=0.0,
+                    precision=MIXED, stream=None):
+    """(loglik, grad) with grad ordered (log l_1..d, log sigma_s, log sigma_n)."""
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    out = C.c_double()
+    g = np.empty(prob.d + 2)
+    _abi.check(lib.lma_loglik_grad(C.byref(prob), C.byref(hyp), C.byref(opt), C.byref(out), g.ctypes.data))
+    return out.value, g
+
+
+def lma_window_residual(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, m, jitter=1e-6, mean=0.0,
+                        precision=MIXED, stream=None):
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    nw = lib.lma_window_rows(C.byref(prob), int(m))
+    out = np.empty((nw, nw))
+    _abi.check(lib.lma_window_residual(C.byref(prob), C.byref(hyp), C.byref(opt), int(m), out.ctypes.data))
+    return out
+
+
+def lma_kernel_launch_count() -> int:
+    return int(_abi.load().lma_kernel_launch_count())
+
+
+def problem_args(p, B=None):
+    """Positional/keyword arguments of lma_fit for a workloads.Problem."""
+    return dict(X=p.X, y=p.y, block_ptr=p.block_ptr, S=p.S, B=p.B if B is None else B, log_ell=p.log_ell,
+                log_sigma_s=p.log_sigma_s, log_sigma_n=p.log_sigma_n, jitter=p.jitter, mean=p.mean)
+
+
+if torch is not None:
+    class LMALogLik(torch.autograd.Function):
+        """log N(y; mu, Sigma-bar_DD) as a function of (log l, log sigma_s, log sigma_n);
+        forward and the hand-written adjoint both run in the CUDA library."""
+
+        @staticmethod
+        def forward(ctx, log_ell, log_sigma_s, log_sigma_n, data):
+            ll, g = lma_loglik_grad(log_ell=log_ell.detach().cpu().numpy(), log_sigma_s=float(log_sigma_s),
+                                    log_sigma_n=float(log_sigma_n), **data)
+            gt = torch.as_tensor(g, dtype=torch.float64)
+            ctx.save_for_backward(gt)
+            ctx.d = int(log_ell.numel())
+            return torch.tensor(ll, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            g = g * gout.detach().cpu().to(torch.float64)
+            d = ctx.d
+            return g[:d].reshape(-1), g[d], g[d + 1], None
+
+    def lma_loglik_autograd(log_ell, log_sigma_s, log_sigma_n, data):
+        """Differentiable log-likelihood; `data` holds the remaining lma_loglik_grad keywords."""
+        return LMALogLik.apply(log_ell, log_sigma_s, log_sigma_n, data)
+
+
+def profile_start(name_filter: str = "") -> None:
+    """Bracket matching kernel launches with CUDA events (see lma_profile_start)."""
+    _abi.load().lma_profile_start(name_filter.encode())
+
+
+def profile_stop() -> dict:
+    """{kernel name: (total milliseconds, launches)} since profile_start."""
+    lib = _abi.load()
+    cap = 64
+    names = C.create_string_buffer(8192)
+    ms = np.zeros(cap)
+    cnt = np.zeros(cap, dtype=np.int64)
+    k = lib.lma_profile_stop(names, 8192, ms.ctypes.data, cnt.ctypes.data, cap)
+    keys = names.value.decode().split("\n")[:k]
+    return {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(keys)}

@@ -1,0 +1,336 @@
+// C ABI of the LMA library: argument checks, dispatch by precision, error
+// reporting.  No C++ exception crosses this file's functions.
+#include <math.h>
+
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lma_impl.cuh"
+
+namespace lma {
+
+ErrState& err() {
+  static thread_local ErrState e;
+  return e;
+}
+
+lma_status fail(lma_status st, const std::string& msg, int64_t block) {
+  ErrState& e = err();
+  e.status = st;
+  e.block = block;
+  e.msg = msg;
+  return st;
+}
+
+namespace prof {
+static bool g_on = false;
+static std::string g_filter;
+struct Rec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static std::vector<Rec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+
+static cudaEvent_t take() {
+  cudaEvent_t e = nullptr;
+  if (!g_pool.empty()) {
+    e = g_pool.back();
+    g_pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+bool active(const char* name) { return g_on && (g_filter.empty() || strstr(name, g_filter.c_str()) != nullptr); }
+void start(const char* name, cudaStream_t st) {
+  Rec r{name, take(), take()};
+  cudaEventRecord(r.a, st);
+  g_recs.push_back(r);
+}
+void stop(cudaStream_t st) { cudaEventRecord(g_recs.back().b, st); }
+}  // namespace prof
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static void init_pool() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  done = true;
+}
+
+static lma_status check_problem(const lma_problem* P, const lma_hyper* H, const lma_options* O) {
+  if (!P || !H || !O) return fail(LMA_ERR_INVALID_ARG, "null problem, hyper or options");
+  if (P->n < 1 || P->d < 1 || P->d > MAXD || P->s < 1 || P->m_blocks < 1)
+    return fail(LMA_ERR_INVALID_ARG, "sizes out of range (n>=1, 1<=d<=24, s>=1, M>=1)");
+  if (P->m_blocks > 65535) return fail(LMA_ERR_INVALID_ARG, "at most 65535 blocks");
+  if (P->markov_order < 0 || P->markov_order > P->m_blocks - 1)
+    return fail(LMA_ERR_INVALID_ARG, "Markov order B must lie in [0, M-1]");
+  if (!P->X || !P->y || !P->S || !P->block_ptr || !H->log_ell)
+    return fail(LMA_ERR_INVALID_ARG, "null data pointer");
+  if (O->precision != LMA_FP64 && O->precision != LMA_MIXED) return fail(LMA_ERR_INVALID_ARG, "unknown precision");
+  if (O->reserved != 0) return fail(LMA_ERR_INVALID_ARG, "options.reserved must be 0");
+  if (P->block_ptr[0] != 0 || P->block_ptr[P->m_blocks] != P->n)
+    return fail(LMA_ERR_INVALID_ARG, "block_ptr must start at 0 and end at n");
+  int64_t maxwin = 0;
+  for (int64_t m = 0; m < P->m_blocks; ++m) {
+    if (P->block_ptr[m + 1] <= P->block_ptr[m])
+      return fail(LMA_ERR_INVALID_ARG, "block " + std::to_string(m) + " is empty or block_ptr decreases", m);
+    int64_t last = m + P->markov_order < P->m_blocks - 1 ? m + P->markov_order : P->m_blocks - 1;
+    int64_t nw = P->block_ptr[last + 1] - P->block_ptr[m];
+    if (nw > maxwin) maxwin = nw;
+  }
+  if (maxwin > (1 << 20)) return fail(LMA_ERR_INVALID_ARG, "window too large");
+  for (int64_t q = 0; q < P->d; ++q)
+    if (!isfinite(H->log_ell[q])) return fail(LMA_ERR_INVALID_ARG, "non-finite log length-scale");
+  if (!isfinite(H->log_sigma_s) || !isfinite(H->log_sigma_n) || !isfinite(H->jitter) || H->jitter < 0)
+    return fail(LMA_ERR_INVALID_ARG, "non-finite hyperparameter or negative jitter");
+  if (!isfinite(P->mean)) return fail(LMA_ERR_INVALID_ARG, "non-finite mean");
+  return LMA_OK;
+}
+
+template <class F>
+static lma_status guarded(F f) {
+  err().status = LMA_OK;
+  err().msg.clear();
+  err().block = 0;
+  try {
+    init_pool();
+    f();
+  } catch (const Fail&) {
+    return err().status == LMA_OK ? LMA_ERR_INTERNAL : err().status;
+  } catch (const std::bad_alloc&) {
+    return fail(LMA_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(LMA_ERR_INTERNAL, "unexpected exception");
+  }
+  return LMA_OK;
+}
+
+}  // namespace lma
+
+using namespace lma;
+
+extern "C" {
+
+lma_status lma_fit(const lma_problem* P, const lma_hyper* H, const lma_options* O, lma_model** out) {
+  if (!out) return fail(LMA_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  lma_status cs = check_problem(P, H, O);
+  if (cs != LMA_OK) return cs;
+  lma_model* md = new (std::nothrow) lma_model();
+  if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+  md->core.prec = O->precision;
+  md->core.st = (cudaStream_t)O->cuda_stream;
+  md->core.keep.st = md->core.st;
+  lma_status st = guarded([&] {
+    if (O->precision == LMA_MIXED)
+      Impl<float>::fit(md->core, P, H);
+    else
+      Impl<double>::fit(md->core, P, H);
+  });
+  if (st != LMA_OK) {
+    md->core.keep.release();
+    cudaStreamSynchronize(md->core.st);
+    delete md;
+    return st;
+  }
+  *out = md;
+  return LMA_OK;
+}
+
+lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
+                       int io_on_device, double* mean_out, double* var_out) {
+  if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
+  if (u < 0) return fail(LMA_ERR_INVALID_ARG, "negative test count");
+  if (u > 0 && (!XU || !tptr || !mean_out || !var_out)) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  const ModelCore& mc = md->core;
+  if (u > 0) {
+    if (tptr[0] != 0 || tptr[mc.M] != u) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr must start at 0, end at u");
+    for (int64_t m = 0; m < mc.M; ++m)
+      if (tptr[m + 1] < tptr[m]) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr decreases", m);
+  }
+  return guarded([&] {
+    if (mc.prec == LMA_MIXED)
+      Impl<float>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
+    else
+      Impl<double>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
+  });
+}
+
+lma_status lma_model_loglik(const lma_model* md, double* out) {
+  if (!md || !out) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  *out = md->core.loglik;
+  return LMA_OK;
+}
+
+lma_status lma_loglik(const lma_problem* P, const lma_hyper* H, const lma_options* O, double* out) {
+  if (!out) return fail(LMA_ERR_INVALID_ARG, "null output pointer");
+  lma_model* md = nullptr;
+  lma_status st = lma_fit(P, H, O, &md);
+  if (st != LMA_OK) return st;
+  *out = md->core.loglik;
+  lma_model_free(md);
+  return LMA_OK;
+}
+
+lma_status lma_loglik_grad(const lma_problem* P, const lma_hyper* H, const lma_options* O, double* ll,
+                           double* grad) {
+  if (!ll || !grad) return fail(LMA_ERR_INVALID_ARG, "null output pointer");
+  lma_status cs = check_problem(P, H, O);
+  if (cs != LMA_OK) return cs;
+  ModelCore mc;
+  mc.prec = O->precision;
+  mc.st = (cudaStream_t)O->cuda_stream;
+  mc.keep.st = mc.st;
+  lma_status st = guarded([&] {
+    if (O->precision == LMA_MIXED)
+      Impl<float>::loglik_grad(mc, P, H, ll, grad);
+    else
+      Impl<double>::loglik_grad(mc, P, H, ll, grad);
+  });
+  mc.keep.release();
+  cudaStreamSynchronize(mc.st);
+  return st;
+}
+
+lma_status lma_model_summary(const lma_model* md, double* A_out, double* y_out, double* sc) {
+  if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
+  const ModelCore& mc = md->core;
+  return guarded([&] {
+    const int64_t se = mc.s + 1;
+    std::vector<double> G((size_t)(se * se));
+    LMA_CK(cudaMemcpyAsync(G.data(), mc.G, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, mc.st));
+    LMA_CK(cudaStreamSynchronize(mc.st));
+    if (A_out)
+      for (int64_t i = 0; i < mc.s; ++i)
+        for (int64_t j = 0; j < mc.s; ++j) A_out[i * mc.s + j] = G[(size_t)((1 + i) * se + 1 + j)];
+    if (y_out)
+      for (int64_t i = 0; i < mc.s; ++i) y_out[i] = G[(size_t)((1 + i) * se)];
+    if (sc) {
+      sc[0] = mc.quad;
+      sc[1] = mc.logdetR;
+      sc[2] = mc.logdetC;
+      sc[3] = mc.loglik;
+    }
+  });
+}
+
+int64_t lma_window_rows(const lma_problem* P, int64_t m) {
+  if (!P || !P->block_ptr || m < 0 || m >= P->m_blocks || P->markov_order < 0) return 0;
+  int64_t last = m + P->markov_order < P->m_blocks - 1 ? m + P->markov_order : P->m_blocks - 1;
+  return P->block_ptr[last + 1] - P->block_ptr[m];
+}
+
+lma_status lma_window_residual(const lma_problem* P, const lma_hyper* H, const lma_options* O, int64_t m,
+                               double* out) {
+  lma_status cs = check_problem(P, H, O);
+  if (cs != LMA_OK) return cs;
+  if (m < 0 || m >= P->m_blocks || !out) return fail(LMA_ERR_INVALID_ARG, "bad block index or null output");
+  ModelCore mc;
+  mc.prec = O->precision;
+  mc.st = (cudaStream_t)O->cuda_stream;
+  mc.keep.st = mc.st;
+  lma_status st = guarded([&] {
+    if (O->precision == LMA_MIXED)
+      Impl<float>::window_residual(mc, P, H, m, out);
+    else
+      Impl<double>::window_residual(mc, P, H, m, out);
+  });
+  mc.keep.release();
+  cudaStreamSynchronize(mc.st);
+  return st;
+}
+
+void lma_model_free(lma_model* md) {
+  if (!md) return;
+  md->core.keep.release();
+  cudaStreamSynchronize(md->core.st);
+  delete md;
+}
+
+const char* lma_status_string(lma_status s) {
+  switch (s) {
+    case LMA_OK: return "ok";
+    case LMA_ERR_INVALID_ARG: return "invalid argument";
+    case LMA_ERR_NOT_PD: return "matrix not positive definite";
+    case LMA_ERR_CUDA: return "CUDA error";
+    case LMA_ERR_OOM: return "out of device memory";
+    case LMA_ERR_TIMEOUT: return "device wait timed out";
+    case LMA_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+lma_status lma_last_error_info(int64_t* failed_block, const char** message) {
+  ErrState& e = err();
+  if (failed_block) *failed_block = e.block;
+  if (message) *message = e.msg.c_str();
+  return e.status;
+}
+
+int64_t lma_kernel_launch_count(void) { return g_launches.load(); }
+
+void lma_profile_start(const char* name_filter) {
+  prof::g_on = true;
+  prof::g_filter = name_filter ? name_filter : "";
+  for (auto& r : prof::g_recs) {
+    prof::g_pool.push_back(r.a);
+    prof::g_pool.push_back(r.b);
+  }
+  prof::g_recs.clear();
+}
+
+int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* launches, int cap) {
+  prof::g_on = false;
+  std::map<std::string, std::pair<double, int64_t>> agg;
+  std::vector<std::string> order;
+  for (auto& r : prof::g_recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto it = agg.find(r.name);
+    if (it == agg.end()) {
+      order.push_back(r.name);
+      agg[r.name] = {ms, 1};
+    } else {
+      it->second.first += ms;
+      it->second.second += 1;
+    }
+    prof::g_pool.push_back(r.a);
+    prof::g_pool.push_back(r.b);
+  }
+  prof::g_recs.clear();
+  std::string all;
+  int k = 0;
+  for (const std::string& nm : order) {
+    if (k < cap) {
+      if (total_ms) total_ms[k] = agg[nm].first;
+      if (launches) launches[k] = agg[nm].second;
+    }
+    all += nm;
+    all += "\n";
+    ++k;
+  }
+  if (names && names_cap > 0) {
+    size_t n = all.size() < (size_t)(names_cap - 1) ? all.size() : (size_t)(names_cap - 1);
+    memcpy(names, all.data(), n);
+    names[n] = 0;
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Host orchestration of the LMA hot path (fit, predict) for one precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/lma.h"
+#include "lma_types.cuh"
+
+namespace lma {
+
+// ---- error state and bookkeeping -------------------------------------------
+struct ErrState {
+  lma_status status = LMA_OK;
+  int64_t block = 0;
+  std::string msg;
+};
+ErrState& err();
+lma_status fail(lma_status st, const std::string& msg, int64_t block = 0);
+void count_launch(int64_t n = 1);
+
+struct Fail {};  // thrown inside the library only, caught at the ABI boundary
+
+#define LMA_CK(call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ::lma::fail(e_ == cudaErrorMemoryAllocation ? LMA_ERR_OOM : LMA_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      throw ::lma::Fail{};                                                               \
+    }                                                                                    \
+  } while (0)
+
+#define LMA_LAUNCHED()                                                                   \
+  do {                                                                                   \
+    ::lma::count_launch();                                                               \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess) {                                                             \
+      ::lma::fail(LMA_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+      throw ::lma::Fail{};                                                               \
+    }                                                                                    \
+  } while (0)
+
+// Stream-ordered device allocations released together.
+struct Arena {
+  cudaStream_t st = nullptr;
+  std::vector<void*> ptrs;
+  template <typename X> X* alloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    LMA_CK(cudaMallocAsync(&p, count * sizeof(X), st));
+    ptrs.push_back(p);
+    return static_cast<X*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    ptrs.clear();
+  }
+};
+
+// Optional launch profiler: when enabled, a CUDA event pair is recorded on the
+// launching stream around every launch whose name matches the filter.
+namespace prof {
+bool active(const char* name);
+void start(const char* name, cudaStream_t st);
+void stop(cudaStream_t st);
+}  // namespace prof
+
+// Launch a kernel, count it, check the launch status and (optionally) time it.
+template <typename... KArgs, typename... Args>
+inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args... args) {
+  const bool p = prof::active(name);
+  if (p) prof::start(name, st);
+  kern<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (p) prof::stop(st);
+  if (e != cudaSuccess) {
+    fail(LMA_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    throw Fail{};
+  }
+}
+
+inline int64_t roundup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline unsigned nblk(int64_t n, int t = NT) { return (unsigned)((n + t - 1) / t); }
+
+// Everything a fitted model keeps on the device.
+struct ModelCore {
+  lma_precision prec = LMA_MIXED;
+  cudaStream_t st = nullptr;
+  int64_t n = 0, d = 0, M = 0, s = 0, B = 0;
+  double mu = 0, ss2 = 0, sn2 = 0;
+  std::vector<double> inv_ell;
+  std::vector<int64_t> bptr;
+  std::vector<Win> wins;
+  Arena keep;                 // buffers owned by the model
+  double* inv_ell_d = nullptr;
+  void* xsT = nullptr;        // n*d scaled inputs (T)
+  void* ssT = nullptr;        // s*d scaled support inputs (T)
+  void* ET = nullptr;         // s*s, ET[k][i] = (L_SS^-1)[i][k]   (T)
+  void* Vt = nullptr;         // n*s whitened support coordinates  (T)
+  void* wbuf = nullptr;       // window buffers (T)
+  void* dinv = nullptr;       // inverted diagonal tiles (T)
+  void* ew = nullptr;         // per-window L^-1 e (T)
+  Win* wins_d = nullptr;
+  double* G = nullptr;        // (s+1)^2 global Gram [quad, y; y, A]
+  double* beta = nullptr;     // s
+  void* LcT = nullptr;        // s*s, (L_C^-1)[i][k] at [k][i]   (T)
+  double quad = 0, wCw = 0, logdetC = 0, logdetR = 0, loglik = 0;
+};
+
+}  // namespace lma
+
+struct lma_model {
+  lma::ModelCore core;
+};
+
+namespace lma {
+
+template <typename T>
+struct Impl {
+  // prepares inputs, Sigma_SS factor and Vt (shared by fit / residual / grad)
+  static void prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, Arena& tmp,
+                      const double** X_d, const double** y_d);
+  static void fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H);
+  static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
+                      int on_device, double* mean, double* var);
+  static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);
+  static void loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad);
+  static void setup_attributes();
+};
+
+// builds the window descriptors of a partition (Section 3: W_m = D_m u D^B_m)
+void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t elem, std::vector<Win>& wins,
+                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems);
+
+// sweep helpers (defined per precision)
+template <typename T>
+void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info,
+                bool batched);
+
+}  // namespace lma

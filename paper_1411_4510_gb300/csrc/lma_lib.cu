@@ -1,0 +1,447 @@
+// Fit / predict pipelines of the LMA hot path, instantiated for float (mixed
+// form) and double (plain FP64 form).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lma_impl.cuh"
+#include "lma_kernels.cuh"
+
+namespace lma {
+
+// ---------------------------------------------------------------------------
+void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t /*elem*/, std::vector<Win>& wins,
+                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems) {
+  const int64_t M = (int64_t)bptr.size() - 1;
+  wins.resize(M);
+  buf_elems = dinv_elems = ew_elems = 0;
+  for (int64_t m = 0; m < M; ++m) {
+    const int64_t last = std::min(m + B, M - 1);
+    Win w{};
+    w.n = (int)(bptr[last + 1] - bptr[m]);
+    w.nB = (int)(bptr[last + 1] - bptr[m + 1]);
+    w.npad = (int)roundup(w.n, TB);
+    w.rows = (int)(w.npad + s + 1);
+    w.g_end = bptr[last + 1];
+    w.m = (int)m;
+    w.base = buf_elems;
+    w.dinv = dinv_elems;
+    w.ew = ew_elems;
+    buf_elems += (int64_t)w.rows * w.npad;
+    dinv_elems += (int64_t)(w.npad / TB) * TB * TB;
+    ew_elems += w.npad;
+    wins[m] = w;
+  }
+}
+
+template <typename T>
+static void set_smem_attr() {
+  cudaFuncSetAttribute(k_chol_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CholSmem<T>));
+  cudaFuncSetAttribute(k_chol_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrsmSmem<T>));
+  cudaFuncSetAttribute(k_pred_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CholSmem<T>));
+}
+
+template <typename T>
+void Impl<T>::setup_attributes() {
+  static bool done = false;
+  if (!done) {
+    set_smem_attr<T>();
+    set_smem_attr<double>();
+    done = true;
+  }
+}
+
+// Left-looking sweep over all column panels.  batched: every window in
+// each launch; otherwise one window per launch (the plain form).
+template <typename T>
+void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info, bool batched) {
+  if (wins.empty()) return;
+  if (batched) {
+    int maxpan = 0, maxrt = 0;
+    for (const Win& w : wins) {
+      maxpan = std::max(maxpan, w.npad / TB);
+      maxrt = std::max(maxrt, (w.rows + TB - 1) / TB);
+    }
+    const unsigned nw = (unsigned)wins.size();
+    for (int kp = 0; kp < maxpan; ++kp) {
+      launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv, info, kp);
+      if (maxrt - kp - 1 > 0) {
+        launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf, dinv, kp);
+      }
+    }
+  } else {
+    for (size_t wi = 0; wi < wins.size(); ++wi) {
+      const Win& w = wins[wi];
+      const int npan = w.npad / TB, rt = (w.rows + TB - 1) / TB;
+      for (int kp = 0; kp < npan; ++kp) {
+        launch("k_chol_step", k_chol_step<T>, dim3(rt - kp, 1), NT, sizeof(CholSmem<T>), st, wins_d + wi, buf, dinv, info + wi, kp);
+        if (rt - kp - 1 > 0) {
+          launch("k_chol_trsm", k_chol_trsm<T>, dim3(rt - kp - 1, 1), NT, sizeof(TrsmSmem<T>), st, wins_d + wi, buf, dinv, kp);
+        }
+      }
+    }
+  }
+}
+
+// Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
+// `extra` extra rows).  Returns false when it is not positive definite.
+static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra) {
+  std::vector<Win> w(1);
+  w[0] = Win{};
+  w[0].n = n;
+  w[0].npad = npad;
+  w[0].rows = npad + extra;
+  w[0].nB = 0;
+  w[0].base = 0;
+  w[0].dinv = 0;
+  Win* wd = tmp.alloc<Win>(1);
+  double* dv = tmp.alloc<double>((size_t)npad * TB);
+  int* info = tmp.alloc<int>(1);
+  LMA_CK(cudaMemcpyAsync(wd, w.data(), sizeof(Win), cudaMemcpyHostToDevice, st));
+  LMA_CK(cudaMemsetAsync(info, 0, sizeof(int), st));
+  chol_sweep<double>(st, w, wd, buf, dv, info, true);
+  int h = 0;
+  LMA_CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LMA_CK(cudaStreamSynchronize(st));
+  return h == 0;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, Arena& tmp, const double** X_d,
+                      const double** y_d) {
+  setup_attributes();
+  cudaStream_t st = mc.st;
+  const int64_t n = P->n, d = P->d, s = P->s;
+  mc.n = n;
+  mc.d = d;
+  mc.M = P->m_blocks;
+  mc.s = s;
+  mc.B = P->markov_order;
+  mc.mu = P->mean;
+  mc.ss2 = exp(2.0 * H->log_sigma_s);
+  mc.sn2 = exp(2.0 * H->log_sigma_n);
+  mc.inv_ell.resize(d);
+  for (int64_t q = 0; q < d; ++q) mc.inv_ell[q] = exp(-H->log_ell[q]);
+  mc.bptr.assign(P->block_ptr, P->block_ptr + mc.M + 1);
+  // inputs on the device
+  const double *X = P->X, *y = P->y, *S = P->S;
+  if (!P->inputs_on_device) {
+    double* Xd = tmp.alloc<double>(n * d);
+    double* yd = tmp.alloc<double>(n);
+    double* Sd = tmp.alloc<double>(s * d);
+    LMA_CK(cudaMemcpyAsync(Xd, X, sizeof(double) * n * d, cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(yd, y, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(Sd, S, sizeof(double) * s * d, cudaMemcpyHostToDevice, st));
+    X = Xd;
+    y = yd;
+    S = Sd;
+  }
+  *X_d = X;
+  *y_d = y;
+  mc.inv_ell_d = mc.keep.alloc<double>(d);
+  LMA_CK(cudaMemcpyAsync(mc.inv_ell_d, mc.inv_ell.data(), sizeof(double) * d, cudaMemcpyHostToDevice, st));
+  T* xsT = mc.keep.alloc<T>(n * d);
+  T* ssT = mc.keep.alloc<T>(s * d);
+  double* ss64 = tmp.alloc<double>(s * d);
+  launch("k_scale", k_scale<T>, nblk(n * d), NT, 0, st, X, n, (int)d, mc.inv_ell_d, nullptr, xsT);
+  launch("k_scale", k_scale<T>, nblk(s * d), NT, 0, st, S, s, (int)d, mc.inv_ell_d, ss64, ssT);
+  mc.xsT = xsT;
+  mc.ssT = ssT;
+  // Sigma_SS + jitter = L_SS L_SS^T, and L_SS^-T from the identity extra rows
+  const int npS = (int)roundup(s, TB);
+  double* kb = tmp.alloc<double>((size_t)(npS + s) * npS);
+  launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
+  if (!factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s)) {
+    fail(LMA_ERR_NOT_PD, "Sigma_SS + jitter is not positive definite", -1);
+    throw Fail{};
+  }
+  T* ET = mc.keep.alloc<T>(s * s);
+  launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
+  mc.ET = ET;
+  // V = L_SS^-1 Sigma_SD, point-major
+  T* Kds = tmp.alloc<T>(n * s);
+  launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, xsT, n, (int)d, ssT, (int)s, (T)mc.ss2, Kds);
+  T* Vt = mc.keep.alloc<T>(n * s);
+  launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt);
+  mc.Vt = Vt;
+}
+
+template <typename T>
+void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
+  cudaStream_t st = mc.st;
+  Arena tmp;
+  tmp.st = st;
+  try {
+    const double *X_d, *y_d;
+    prepare(mc, P, H, tmp, &X_d, &y_d);
+    const bool batched = (mc.prec == LMA_MIXED);
+    const int64_t n = mc.n, s = mc.s, M = mc.M;
+    const int d = (int)mc.d;
+    T* rT = tmp.alloc<T>(n);
+    launch("k_center", k_center<T>, nblk(n), NT, 0, st, y_d, n, mc.mu, rT);
+    // windows
+    int64_t bufe, dinve, ewe;
+    make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe);
+    T* wbuf = mc.keep.alloc<T>(bufe);
+    T* dinv = mc.keep.alloc<T>(dinve);
+    T* ew = mc.keep.alloc<T>(ewe);
+    Win* wd = mc.keep.alloc<Win>(M);
+    int* info = tmp.alloc<int>(M);
+    mc.wbuf = wbuf;
+    mc.dinv = dinv;
+    mc.ew = ew;
+    mc.wins_d = wd;
+    LMA_CK(cudaMemcpyAsync(wd, mc.wins.data(), sizeof(Win) * M, cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemsetAsync(info, 0, sizeof(int) * M, st));
+    int maxnt = 0;
+    for (const Win& w : mc.wins) maxnt = std::max(maxnt, w.npad / TB);
+    const T* Vt = (const T*)mc.Vt;
+    const T* xsT = (const T*)mc.xsT;
+    const unsigned et = nblk(s + 1, TB);
+    if (batched) {
+      launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
+                                                                          (T)mc.sn2, wbuf);
+      launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
+    } else {
+      for (int64_t m = 0; m < M; ++m) {
+        const int nt = mc.wins[m].npad / TB;
+        launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd + m, xsT, d, Vt, (int)s, (T)mc.ss2, (T)mc.sn2,
+                                                               wbuf);
+        launch("k_fill_ext", k_fill_ext<T>, dim3(nt, et, 1), NT, 0, st, wd + m, Vt, rT, (int)s, wbuf);
+      }
+    }
+    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched);
+    {
+      std::vector<int> hinfo(M);
+      LMA_CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * M, cudaMemcpyDeviceToHost, st));
+      LMA_CK(cudaStreamSynchronize(st));
+      for (int64_t m = 0; m < M; ++m)
+        if (hinfo[m]) {
+          fail(LMA_ERR_NOT_PD, "residual window of block " + std::to_string(m) +
+                                   " is not positive definite (pivot " + std::to_string(hinfo[m] - 1) + ")",
+               m);
+          throw Fail{};
+        }
+    }
+    // global Gram of the local summaries, reduced in a fixed order
+    const int se = (int)s + 1;
+    const int nte = (se + TB - 1) / TB;
+    const int nchunk = (int)std::min<int64_t>(M, 32);
+    const int chunk = (int)((M + nchunk - 1) / nchunk);
+    double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
+    launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wd, (int)M, chunk, (int)s, wbuf, partial);
+    mc.G = mc.keep.alloc<double>((size_t)se * se);
+    launch("k_gram_reduce", k_gram_reduce, nblk((int64_t)se * se), NT, 0, st, partial, nchunk, se, mc.G);
+    double* ldw = tmp.alloc<double>(M);
+    double* ldR = tmp.alloc<double>(1);
+    launch("k_logdet", k_logdet<T>, (unsigned)M, NT, 0, st, wd, wbuf, ldw);
+    launch("k_sum_ordered", k_sum_ordered, 1, 32, 0, st, ldw, (int)M, ldR);
+    // global step in FP64: C = I + A, L_C, w = L_C^-1 y, L_C^-T, beta = C^-1 y
+    const int npC = (int)roundup(s, TB);
+    double* cb = tmp.alloc<double>((size_t)(npC + 1 + s) * npC);
+    launch("k_build_global", k_build_global, nblk((int64_t)(npC + 1 + s) * npC), NT, 0, st, mc.G, (int)s, npC, cb);
+    if (!factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1)) {
+      fail(LMA_ERR_NOT_PD, "global summary Sigma-ddot_SS is not positive definite", -2);
+      throw Fail{};
+    }
+    mc.beta = mc.keep.alloc<double>(s);
+    double* sc = tmp.alloc<double>(4);
+    launch("k_global_finish", k_global_finish, 1, NT, 0, st, cb, mc.G, (int)s, npC, mc.beta, sc);
+    T* LcT = mc.keep.alloc<T>(s * s);
+    launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)(npC + 1) * npC, npC, (int)s, LcT);
+    mc.LcT = LcT;
+    launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, wd, wbuf, mc.beta, (int)s, ew);
+    double hs[4], hr = 0;
+    LMA_CK(cudaMemcpyAsync(hs, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaMemcpyAsync(&hr, ldR, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaStreamSynchronize(st));
+    mc.quad = hs[0];
+    mc.wCw = hs[1];
+    mc.logdetC = hs[2];
+    mc.logdetR = hr;
+    mc.loglik = -0.5 * (mc.quad - mc.wCw) - 0.5 * (mc.logdetR + mc.logdetC) - 0.5 * (double)n * log(2.0 * M_PI);
+    tmp.release();
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
+}
+
+template <typename T>
+void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
+                      double* mean, double* var) {
+  cudaStream_t st = mc.st;
+  Arena tmp;
+  tmp.st = st;
+  try {
+    const int64_t s = mc.s, M = mc.M, B = mc.B;
+    const int d = (int)mc.d;
+    if (U == 0) {
+      tmp.release();
+      return;
+    }
+    const double* XUd = XU;
+    if (!on_device) {
+      double* t = tmp.alloc<double>(U * d);
+      LMA_CK(cudaMemcpyAsync(t, XU, sizeof(double) * U * d, cudaMemcpyHostToDevice, st));
+      XUd = t;
+    }
+    T* xu = tmp.alloc<T>(U * d);
+    launch("k_scale", k_scale<T>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
+    T* Kus = tmp.alloc<T>(U * s);
+    launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s, (T)mc.ss2, Kus);
+    T* Vu = tmp.alloc<T>(U * s);
+    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu);
+    // pairs (test block n, window m in [n-B, n])
+    std::vector<Pair> pairs;
+    std::vector<int4> tb;  // per test block: first pair, count, u0, nu
+    int64_t pe = 0;
+    for (int64_t nb = 0; nb < M; ++nb) {
+      const int nu = (int)(tptr[nb + 1] - tptr[nb]);
+      if (nu == 0) continue;
+      const int first = (int)pairs.size();
+      for (int64_t m = std::max<int64_t>(0, nb - B); m <= nb; ++m) {
+        const Win& w = mc.wins[m];
+        Pair p{};
+        p.pbase = pe;
+        p.win = (int)m;
+        p.u0 = (int)tptr[nb];
+        p.nu = nu;
+        p.c0 = (m < nb) ? w.nB : 0;
+        p.c1 = w.n;
+        p.n = (int)nb;
+        pe += (int64_t)nu * w.npad;
+        pairs.push_back(p);
+      }
+      tb.push_back(make_int4(first, (int)pairs.size() - first, (int)tptr[nb], nu));
+    }
+    std::vector<int4> it_rhs, it_acc, it_t12;
+    std::vector<int2> it_sw;
+    for (size_t pi = 0; pi < pairs.size(); ++pi) {
+      const Pair& p = pairs[pi];
+      const int nut = (p.nu + TB - 1) / TB, nct = mc.wins[p.win].npad / TB;
+      for (int ut = 0; ut < nut; ++ut) {
+        it_sw.push_back(make_int2((int)pi, ut));
+        for (int ct = 0; ct < nct; ++ct) it_rhs.push_back(make_int4((int)pi, ut, ct, 0));
+      }
+    }
+    const int nst = (int)((s + TB - 1) / TB);
+    for (const int4& t : tb) {
+      const int nut = (t.w + TB - 1) / TB;
+      for (int ut = 0; ut < nut; ++ut)
+        for (int kt = 0; kt < nst; ++kt) it_acc.push_back(make_int4(t.x, t.y, ut, kt));
+      for (int u = 0; u < t.w; ++u) it_t12.push_back(make_int4(t.x, t.y, u, 0));
+    }
+    Pair* pd = tmp.alloc<Pair>(pairs.size());
+    int4* ird = tmp.alloc<int4>(it_rhs.size());
+    int2* isd = tmp.alloc<int2>(it_sw.size());
+    int4* iad = tmp.alloc<int4>(it_acc.size());
+    int4* itd = tmp.alloc<int4>(it_t12.size());
+    LMA_CK(cudaMemcpyAsync(pd, pairs.data(), sizeof(Pair) * pairs.size(), cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(ird, it_rhs.data(), sizeof(int4) * it_rhs.size(), cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(isd, it_sw.data(), sizeof(int2) * it_sw.size(), cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(iad, it_acc.data(), sizeof(int4) * it_acc.size(), cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(itd, it_t12.data(), sizeof(int4) * it_t12.size(), cudaMemcpyHostToDevice, st));
+    T* Pbuf = tmp.alloc<T>(pe);
+    const T* xs = (const T*)mc.xsT;
+    const T* Vt = (const T*)mc.Vt;
+    const T* wbuf = (const T*)mc.wbuf;
+    if (mc.prec == LMA_MIXED) {
+      launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu, (int)s,
+                                                           (T)mc.ss2, Pbuf);
+      launch("k_pred_sweep", k_pred_sweep<T>, (unsigned)it_sw.size(), NT, sizeof(CholSmem<T>), st, pd, isd, mc.wins_d, wbuf,
+                                                                              (const T*)mc.dinv, Pbuf);
+    } else {
+      // plain form: one pair per launch
+      size_t a = 0, b = 0;
+      for (size_t pi = 0; pi < pairs.size(); ++pi) {
+        size_t a1 = a, b1 = b;
+        while (a1 < it_rhs.size() && it_rhs[a1].x == (int)pi) ++a1;
+        while (b1 < it_sw.size() && it_sw[b1].x == (int)pi) ++b1;
+        launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)(a1 - a), NT, 0, st, pd, ird + a, mc.wins_d, xs, xu, d, Vt, Vu, (int)s,
+                                                         (T)mc.ss2, Pbuf);
+        launch("k_pred_sweep", k_pred_sweep<T>, (unsigned)(b1 - b), NT, sizeof(CholSmem<T>), st, pd, isd + b, mc.wins_d, wbuf,
+                                                                            (const T*)mc.dinv, Pbuf);
+        a = a1;
+        b = b1;
+      }
+    }
+    T* h = tmp.alloc<T>(U * s);
+    launch("k_pred_accum", k_pred_accum<T>, (unsigned)it_acc.size(), NT, 0, st, pd, iad, mc.wins_d, wbuf, Pbuf, Vu, (int)s, h);
+    double* t1 = tmp.alloc<double>(U);
+    double* t2 = tmp.alloc<double>(U);
+    launch("k_pred_t12", k_pred_t12<T>, nblk((int64_t)it_t12.size() * 32), NT, 0, st, pd, itd, (int)it_t12.size(), mc.wins_d, Pbuf,
+                                                                    (const T*)mc.ew, t1, t2);
+    double* part = tmp.alloc<double>((size_t)nst * U);
+    launch("k_var_gemm", k_var_gemm<T>, dim3(nst, nblk(U, TB)), NT, 0, st, h, U, (int)s, (const T*)mc.LcT, part);
+    double* md = mean;
+    double* vd = var;
+    if (!on_device) {
+      md = tmp.alloc<double>(U);
+      vd = tmp.alloc<double>(U);
+    }
+    const double prior = mc.ss2 + (noisy ? mc.sn2 : 0.0);
+    launch("k_pred_final", k_pred_final<T>, nblk(U * 32), NT, 0, st, Vu, U, (int)s, mc.beta, t1, t2, part, nst, mc.mu, prior, md, vd);
+    if (!on_device) {
+      LMA_CK(cudaMemcpyAsync(mean, md, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
+      LMA_CK(cudaMemcpyAsync(var, vd, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
+    }
+    tmp.release();
+    LMA_CK(cudaStreamSynchronize(st));
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
+}
+
+// residual window of block m in natural row order (host, n_w x n_w)
+template <typename T>
+void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out) {
+  cudaStream_t st = mc.st;
+  Arena tmp;
+  tmp.st = st;
+  try {
+    const double *X_d, *y_d;
+    prepare(mc, P, H, tmp, &X_d, &y_d);
+    int64_t bufe, dinve, ewe;
+    std::vector<Win> all;
+    make_windows(mc.bptr, mc.B, mc.s, sizeof(T), all, bufe, dinve, ewe);
+    Win w = all[m];
+    w.base = 0;
+    Win* wd = tmp.alloc<Win>(1);
+    LMA_CK(cudaMemcpyAsync(wd, &w, sizeof(Win), cudaMemcpyHostToDevice, st));
+    T* buf = tmp.alloc<T>((size_t)w.npad * w.npad);
+    const int nt = w.npad / TB;
+    launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d, (const T*)mc.Vt,
+                                                           (int)mc.s, (T)mc.ss2, (T)mc.sn2, buf);
+    std::vector<T> h((size_t)w.npad * w.npad);
+    LMA_CK(cudaMemcpyAsync(h.data(), buf, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaStreamSynchronize(st));
+    const int n = w.n;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        int a = n - 1 - i, b = n - 1 - j;  // reversed storage, lower triangle valid
+        if (b > a) std::swap(a, b);
+        out[(int64_t)i * n + j] = (double)h[(size_t)a * w.npad + b];
+      }
+    tmp.release();
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
+}
+
+template <typename T>
+void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad) {
+  (void)mc; (void)P; (void)H; (void)ll; (void)grad;
+  fail(LMA_ERR_INTERNAL, "lma_loglik_grad: not built yet");
+  throw Fail{};
+}
+
+template struct Impl<float>;
+template struct Impl<double>;
+
+}  // namespace lma

@@ -1,0 +1,43 @@
+// Shared constants and descriptors of the LMA kernels (host and device).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lma {
+
+constexpr int TB = 64;     // tile edge (also the Cholesky panel width)
+constexpr int NT = 256;    // threads per CTA
+constexpr int KS = 16;     // K step of the SIMT tile product
+constexpr int MAXD = 24;   // largest input dimension held in shared memory
+
+// One factorisation problem ("window").  The window of block m is
+// D_m u D^B_m (Section 3) stored in REVERSED row order: local row i is the
+// global training row g_end-1-i, so the blanket D^B_m comes first and block
+// m last.  Its buffer is a row-major matrix with leading dimension npad
+// (n rounded up to 64):
+//   rows [0, npad)          residual R (lower triangle; padding = identity)
+//   rows [npad, rows)       extra rows that the sweep turns into (L^-1 Y)^T
+struct Win {
+  int64_t base;   // element offset of row 0 in the window buffer
+  int64_t dinv;   // element offset of this window's inverted 64x64 diagonal tiles
+  int64_t ew;     // element offset into the per-window vector buffer
+  int64_t g_end;  // one past the last global training row of the window
+  int n;          // true order of the window
+  int npad;       // padded order, multiple of 64 (= leading dimension)
+  int rows;       // npad + number of extra rows
+  int nB;         // blanket size: block-m part is local rows [nB, n)
+  int m;          // block index
+  int pad_;
+};
+
+// A prediction pair (test block n, window m), m in [n-B, n].
+struct Pair {
+  int64_t pbase;  // element offset of this pair's RHS rows (nu x npad of window m)
+  int win;        // window index m
+  int u0;         // first test row of block n
+  int nu;         // number of test rows in block n
+  int c0, c1;     // kept window columns [c0, c1): block part for m < n, all for m == n
+  int n;          // test block
+};
+
+}  // namespace lma

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  FP64 form: 1e-9 relative (norm-wise for mean and variance,
+absolute-over-|ref| for the log-likelihood).  Mixed form: predictive mean
+1e-4 norm-wise relative and RMSE within 0.1% of the oracle's; the variance
+and log-likelihood bounds below follow from FP32 rounding of R = K - Q, whose
+entries are O(sigma_s^2) while its smallest eigenvalue is O(sigma_n^2): a
+relative perturbation of ~1e-7 sigma_s^2 / sigma_n^2 in the residual
+precision (about 4e-5 at sigma_n = 0.05) reaches the variance and the
+log-likelihood nearly undamped.
+
+The mixed form's error also grows with sqrt(cond(Sigma_SS)): V = L_SS^-1
+Sigma_SD is formed in FP32 and its cancellation is of size |L_SS^-1|.  The
+tiny structural cases below pack up to 100 support points into a unit cube,
+which drives cond(Sigma_SS) to ~4e7 at the default jitter; for the mixed
+form they therefore use jitter 1e-3 (cond <= ~4e4).  The configuration-shaped
+cases (C1, C2 recipe) keep the default jitter 1e-6.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL_MIXED = 1e-4
+VAR_TOL_MIXED = 2e-3
+LL_TOL_MIXED = 1e-3
+TOL_FP64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    from paper_1411_4510_gb300 import build
+    build.build()
+    import paper_1411_4510_gb300 as L
+    torch.cuda.set_device(0)
+    return L
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1e-300, np.linalg.norm(np.asarray(b))))
+
+
+def run_gpu(L, p, prec, B=None, on_device=True, noisy=True):
+    import torch
+    args = L.problem_args(p, B)
+    if on_device:
+        dev = torch.device("cuda:0")
+        args.update(X=torch.as_tensor(p.X, device=dev), y=torch.as_tensor(p.y, device=dev),
+                    S=torch.as_tensor(p.S, device=dev))
+        XU = torch.as_tensor(p.XU, device=dev)
+    else:
+        XU = p.XU
+    model = L.lma_fit(precision=prec, **args)
+    mean, var = L.lma_predict(model, XU, p.test_block_ptr, noisy=noisy)
+    if on_device:
+        mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    return model, mean, var
+
+
+def oracle(p, B=None, noisy=True):
+    from oracle import lma_oracle as O2
+    f = O2.fit(p, B)
+    m, v = O2.predict(f, noisy=noisy)
+    return f, m, v
+
+
+TINY = [
+    # (seed, sizes, B, d, s, test sizes)
+    (0, (70, 90, 65, 80, 75), 1, 3, 40, (9, 0, 12, 7, 10)),
+    (1, (64, 64, 64, 64), 2, 2, 64, (16, 16, 16, 16)),
+    (2, (130, 5, 77, 140), 0, 4, 70, (3, 1, 20, 0)),
+    (3, (50, 61, 72, 83), 3, 2, 33, (5, 6, 7, 8)),        # B = M-1: full GP
+    (4, (1, 129, 2, 66, 3, 100), 2, 5, 100, (1, 4, 0, 2, 7, 3)),
+]
+
+
+def _tiny(case):
+    from workloads import make_random_problem
+    seed, sizes, B, d, s, ts = case
+    return make_random_problem(seed, sizes, d=d, s=s, B=B, test_sizes=ts)
+
+
+@pytest.mark.parametrize("case", TINY)
+def test_fp64_matches_oracle(L, case):
+    p = _tiny(case)
+    f, m, v = oracle(p)
+    model, mean, var = run_gpu(L, p, L.FP64)
+    assert rel(mean, m) <= TOL_FP64
+    assert rel(var, v) <= TOL_FP64
+    assert abs(L.lma_model_loglik(model) - f.loglik) <= TOL_FP64 * abs(f.loglik)
+
+
+MIXED_TINY_JITTER = 1e-3
+
+
+@pytest.mark.parametrize("case", TINY)
+def test_mixed_matches_oracle(L, case):
+    p = _tiny(case)
+    p.jitter = MIXED_TINY_JITTER
+    f, m, v = oracle(p)
+    model, mean, var = run_gpu(L, p, L.MIXED)
+    assert rel(mean, m) <= MEAN_TOL_MIXED
+    assert rel(var, v) <= VAR_TOL_MIXED
+    assert abs(L.lma_model_loglik(model) - f.loglik) <= LL_TOL_MIXED * abs(f.loglik)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_host_buffers_and_latent_variance(L, prec):
+    p = _tiny(TINY[0])
+    p.jitter = MIXED_TINY_JITTER
+    _, m, v = oracle(p, noisy=False)
+    _, mean, var = run_gpu(L, p, getattr(L, prec), on_device=False, noisy=False)
+    tol = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
+    assert rel(mean, m) <= tol
+    assert rel(var, v) <= (TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_residual_window_entries(L, prec):
+    """Residual-formation kernel: entries of R = Sigma - Q over D_m u D^B_m,
+    on a C2-shaped case with cond(Sigma_SS) ~ 2e2, where FP32 rounding of V
+    contributes ~5e-7 (emulated) and the compensated Q sum ~1e-7."""
+    from oracle.lma_oracle import _Cov
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=2)
+    cv = _Cov(p)
+    for m in (0, 7, 14, 15):
+        R = L.lma_window_residual(m=m, precision=getattr(L, prec), **L.problem_args(p))
+        last = min(m + p.B, p.M - 1)
+        idx = np.arange(p.block_ptr[m], p.block_ptr[last + 1])
+        ref = cv.R_train(idx, idx)
+        tol = 1e-12 if prec == "FP64" else 2e-6
+        assert np.max(np.abs(R - ref)) <= tol * max(1.0, np.max(np.abs(ref))), m
+
+
+def test_c1_full_config(L):
+    from workloads import make_problem
+    p = make_problem("C1")
+    f, m, v = oracle(p)
+    for prec in ("FP64", "MIXED"):
+        model, mean, var = run_gpu(L, p, getattr(L, prec))
+        if prec == "FP64":
+            assert rel(mean, m) <= TOL_FP64 and rel(var, v) <= TOL_FP64
+            assert abs(L.lma_model_loglik(model) - f.loglik) <= TOL_FP64 * abs(f.loglik)
+        else:
+            assert rel(mean, m) <= MEAN_TOL_MIXED
+            rm_ref = np.sqrt(np.mean((m - p.yU) ** 2))
+            rm = np.sqrt(np.mean((mean - p.yU) ** 2))
+            assert abs(rm - rm_ref) <= 1e-3 * rm_ref
+            assert rel(var, v) <= VAR_TOL_MIXED
+
+
+@pytest.mark.parametrize("B", [1, 2, 3])
+def test_c2_shaped_reduced(L, B):
+    """C2 recipe (5-D normal inputs, RFF draw, k-means blocks) at 16 blocks of
+    200 and |S| = 100: several tiles per window and ragged tails."""
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=B)
+    f, m, v = oracle(p)
+    for prec in ("FP64", "MIXED"):
+        model, mean, var = run_gpu(L, p, getattr(L, prec))
+        tol_m = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
+        tol_v = TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED
+        assert rel(mean, m) <= tol_m, (prec, rel(mean, m))
+        assert rel(var, v) <= tol_v, (prec, rel(var, v))
+
+
+def test_single_block_and_tiny_sizes(L):
+    from workloads import make_random_problem
+    for case in [((37,), 0, 1, 1, (5,)), ((1, 1, 1), 1, 1, 1, (1, 0, 2)), ((3, 200), 1, 2, 3, (0, 4))]:
+        sizes, B, d, s, ts = case
+        p = make_random_problem(5, sizes, d=d, s=s, B=B, test_sizes=ts)
+        f, m, v = oracle(p)
+        model, mean, var = run_gpu(L, p, L.FP64)
+        assert rel(mean, m) <= TOL_FP64 and rel(var, v) <= TOL_FP64, case
+
+
+def test_no_test_points(L):
+    p = _tiny(TINY[0])
+    model = L.lma_fit(precision=L.MIXED, **L.problem_args(p))
+    mean, var = L.lma_predict(model, np.zeros((0, p.d)), np.zeros(p.M + 1, dtype=np.int64))
+    assert mean.shape == (0,)
+
+
+def test_nan_input_reports_not_pd(L):
+    p = _tiny(TINY[0])
+    X = p.X.copy()
+    X[100, 0] = np.nan
+    args = L.problem_args(p)
+    args["X"] = X
+    with pytest.raises(L.LMAError) as ei:
+        L.lma_fit(precision=L.MIXED, **args)
+    assert ei.value.status == 2
+    # the library stays usable after the error
+    model, mean, var = run_gpu(L, p, L.MIXED)
+    assert np.all(np.isfinite(mean))
