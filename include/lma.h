@@ -160,6 +160,18 @@ lma_status lma_last_error_info(int64_t* failed_block, const char** message);
 /* Number of kernels this library has launched in the calling process.     */
 int64_t lma_kernel_launch_count(void);
 
+/* Diagnostic (not part of the paper's method): C = A B^T computed by this
+ * library's tensor-core tile product (tcgen05, FP32 operands split into TF32
+ * hi/lo halves, three MMAs per product, FP32 accumulation in tensor memory),
+ * for self-tests of that building block.  A is M x K, B is N x K, C is M x N,
+ * all row-major FP32 DEVICE pointers with leading dimensions lda, ldb, ldc;
+ * K must be a multiple of 32, lda and ldb multiples of 4, A and B 16-byte
+ * aligned; tile_n is the tile width (64 or 128).  Returns LMA_ERR_TIMEOUT if
+ * a bounded device wait gave up.                                         */
+lma_status lma_tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                             const float* B, int64_t ldb, float* C, int64_t ldc, int tile_n,
+                             void* cuda_stream);
+
 /* Launch profiler (a single-threaded diagnostic, off by default; not part of
  * the paper's method).  lma_profile_start clears earlier records and, until
  * lma_profile_stop, brackets every launch whose kernel name contains

@@ -284,6 +284,15 @@ lma_status lma_last_error_info(int64_t* failed_block, const char** message) {
 
 int64_t lma_kernel_launch_count(void) { return g_launches.load(); }
 
+lma_status lma_tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                             int64_t ldb, float* C, int64_t ldc, int tile_n, void* cuda_stream) {
+  if (M < 1 || N < 1 || K < 32 || K % 32 || !A || !B || !C || lda % 4 || ldb % 4 || lda < K || ldb < K || ldc < N ||
+      (tile_n != 64 && tile_n != 128) || M > (1ll << 30) || N > (1ll << 30) || K > (1ll << 30) ||
+      ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+    return fail(LMA_ERR_INVALID_ARG, "tc_gemm_check: bad sizes, strides or alignment");
+  return guarded([&] { tc_gemm_check(M, N, K, A, lda, B, ldb, C, ldc, tile_n, (cudaStream_t)cuda_stream); });
+}
+
 void lma_profile_start(const char* name_filter) {
   prof::g_on = true;
   prof::g_filter = name_filter ? name_filter : "";

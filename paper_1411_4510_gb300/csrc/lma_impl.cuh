@@ -111,6 +111,9 @@ struct ModelCore {
   double* beta = nullptr;     // s
   void* LcT = nullptr;        // s*s, (L_C^-1)[i][k] at [k][i]   (T)
   double quad = 0, wCw = 0, logdetC = 0, logdetR = 0, loglik = 0;
+  double* kss = nullptr;      // Sigma_SS factor buffer: L_SS (rows < npS) and L_SS^-T rows (FP64)
+  double* ss64 = nullptr;     // s*d scaled support inputs (FP64)
+  int npS = 0;
 };
 
 }  // namespace lma
@@ -133,6 +136,9 @@ struct Impl {
   static void loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad);
   static void setup_attributes();
 };
+
+void tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                   float* C, int64_t ldc, int tile_n, cudaStream_t st);
 
 // builds the window descriptors of a partition (Section 3: W_m = D_m u D^B_m)
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t elem, std::vector<Win>& wins,

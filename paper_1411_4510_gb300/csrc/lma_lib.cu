@@ -8,6 +8,8 @@
 
 #include "lma_impl.cuh"
 #include "lma_kernels.cuh"
+#include "lma_grad.cuh"
+#include "lma_tc.cuh"
 
 namespace lma {
 
@@ -145,14 +147,17 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   LMA_CK(cudaMemcpyAsync(mc.inv_ell_d, mc.inv_ell.data(), sizeof(double) * d, cudaMemcpyHostToDevice, st));
   T* xsT = mc.keep.alloc<T>(n * d);
   T* ssT = mc.keep.alloc<T>(s * d);
-  double* ss64 = tmp.alloc<double>(s * d);
+  double* ss64 = mc.keep.alloc<double>(s * d);
+  mc.ss64 = ss64;
   launch("k_scale", k_scale<T>, nblk(n * d), NT, 0, st, X, n, (int)d, mc.inv_ell_d, nullptr, xsT);
   launch("k_scale", k_scale<T>, nblk(s * d), NT, 0, st, S, s, (int)d, mc.inv_ell_d, ss64, ssT);
   mc.xsT = xsT;
   mc.ssT = ssT;
   // Sigma_SS + jitter = L_SS L_SS^T, and L_SS^-T from the identity extra rows
   const int npS = (int)roundup(s, TB);
-  double* kb = tmp.alloc<double>((size_t)(npS + s) * npS);
+  double* kb = mc.keep.alloc<double>((size_t)(npS + s) * npS);
+  mc.kss = kb;
+  mc.npS = npS;
   launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
   if (!factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s)) {
     fail(LMA_ERR_NOT_PD, "Sigma_SS + jitter is not positive definite", -1);
@@ -436,9 +441,153 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
 
 template <typename T>
 void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad) {
-  (void)mc; (void)P; (void)H; (void)ll; (void)grad;
-  fail(LMA_ERR_INTERNAL, "lma_loglik_grad: not built yet");
-  throw Fail{};
+  fit(mc, P, H);
+  cudaStream_t st = mc.st;
+  Arena tmp;
+  tmp.st = st;
+  try {
+    const int64_t n = mc.n, s = mc.s, M = mc.M;
+    const int d = (int)mc.d;
+    const int si = (int)s;
+    // per-window backward layout
+    std::vector<GWin> gw(M);
+    int64_t qe = 0, ge = 0, gve = 0;
+    int maxnt = 0, maxrows = 0;
+    for (int64_t m = 0; m < M; ++m) {
+      const Win& w = mc.wins[m];
+      GWin g{};
+      g.nrows = 2 * (si + 1) + (w.n - w.nB);
+      g.q = qe;
+      g.g = ge;
+      g.gv = gve;
+      qe += (int64_t)g.nrows * w.npad;
+      ge += (int64_t)w.npad * w.npad;
+      gve += s * w.npad;
+      gw[m] = g;
+      maxnt = std::max(maxnt, w.npad / TB);
+      maxrows = std::max(maxrows, g.nrows);
+    }
+    GWin* gwd = tmp.alloc<GWin>(M);
+    LMA_CK(cudaMemcpyAsync(gwd, gw.data(), sizeof(GWin) * M, cudaMemcpyHostToDevice, st));
+    T* Q = tmp.alloc<T>(qe);
+    T* Gb = tmp.alloc<T>(ge);
+    T* GV = tmp.alloc<T>(gve);
+    const T* wbuf = (const T*)mc.wbuf;
+    launch("k_grad_rhs", k_grad_rhs<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd, wbuf,
+           (const T*)mc.LcT, si, Q);
+    launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+           (const T*)mc.ew, si, Q);
+    std::vector<int2> it_sw, it_g;
+    for (int64_t m = 0; m < M; ++m) {
+      const int nrt = (gw[m].nrows + TB - 1) / TB;
+      for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
+      const int nt = mc.wins[m].npad / TB;
+      for (int t = 0; t < nt * (nt + 1) / 2; ++t) it_g.push_back(make_int2((int)m, t));
+    }
+    int2* isw = tmp.alloc<int2>(it_sw.size());
+    int2* ig = tmp.alloc<int2>(it_g.size());
+    LMA_CK(cudaMemcpyAsync(isw, it_sw.data(), sizeof(int2) * it_sw.size(), cudaMemcpyHostToDevice, st));
+    LMA_CK(cudaMemcpyAsync(ig, it_g.data(), sizeof(int2) * it_g.size(), cudaMemcpyHostToDevice, st));
+    launch("k_bwd_sweep", k_bwd_sweep<T>, dim3((unsigned)it_sw.size()), NT, sizeof(CholSmem<T>), st, isw,
+           mc.wins_d, gwd, wbuf, (const T*)mc.dinv, Q);
+    const int np2 = d + 2;
+    double* pG = tmp.alloc<double>(it_g.size() * np2);
+    launch("k_grad_G", k_grad_G<T>, dim3((unsigned)it_g.size()), NT, 0, st, ig, mc.wins_d, gwd, (const T*)Q,
+           (const T*)mc.xsT, d, si, mc.ss2, mc.sn2, Gb, pG);
+    launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+           (const T*)Gb, (const T*)mc.Vt, si, GV);
+    int64_t* bptr_d = tmp.alloc<int64_t>(M + 1);
+    LMA_CK(cudaMemcpyAsync(bptr_d, mc.bptr.data(), sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, st));
+    T* PsiT = tmp.alloc<T>((s + 1) * n);
+    T* GVT = tmp.alloc<T>(s * n);
+    launch("k_grad_gather", k_grad_gather<T>, dim3(nblk(n), (unsigned)(2 * s + 1)), NT, 0, st, mc.wins_d, gwd,
+           bptr_d, (int)M, (int)mc.B, n, si, (const T*)Q, (const T*)GV, PsiT, GVT);
+    T* VbT = tmp.alloc<T>(s * n);
+    launch("k_grad_vbar", k_grad_vbar<T>, dim3(nblk(n, TB), nblk(s, TB)), NT, 0, st, (const T*)PsiT,
+           (const T*)GVT, (const T*)mc.LcT, mc.beta, n, si, VbT);
+    const unsigned gx = nblk(n, TB), gy = nblk(s, TB);
+    double* pK = tmp.alloc<double>((size_t)gx * gy * np2);
+    launch("k_grad_kds", k_grad_kds<T>, dim3(gx, gy), NT, 0, st, (const T*)VbT, (const T*)mc.ET,
+           (const T*)mc.xsT, (const T*)mc.ssT, d, n, si, mc.ss2, pK);
+    // L_SS-bar = -L_SS^-T (Vt-bar^T Vt) and the Cholesky adjoint, in FP64
+    const int nch = (int)std::min<int64_t>(64, (n + 8191) / 8192);
+    const int64_t chunk = (n + nch - 1) / nch;
+    double* pM = tmp.alloc<double>((size_t)nch * s * s);
+    launch("k_grad_m1", k_grad_m1<T>, dim3(gy, gy, nch), NT, 0, st, (const T*)VbT, (const T*)mc.Vt, n, si, chunk,
+           pM);
+    double* M1 = tmp.alloc<double>(s * s);
+    launch("k_sum_chunks", k_sum_chunks, nblk(s * s), NT, 0, st, (const double*)pM, nch, (int64_t)(s * s), M1);
+    const double* ET64 = mc.kss + (int64_t)mc.npS * mc.npS;
+    double* Lm = tmp.alloc<double>(s * s);   // L_SS with its upper triangle zeroed
+    launch("k_copy_block", k_copy_block<double>, nblk(s * s), NT, 0, st, (const double*)mc.kss, (int64_t)mc.npS,
+           si, Lm);
+    launch("k_phi", k_phi, nblk(s * s), NT, 0, st, Lm, si);   // tril with halved diagonal ...
+    launch("k_tril_fix", k_tril_fix, nblk(s * s), NT, 0, st, Lm, si);  // ... restore the diagonal
+    double* Lbar = tmp.alloc<double>(s * s);
+    double* X = tmp.alloc<double>(s * s);
+    double* Y = tmp.alloc<double>(s * s);
+    double* Sb = tmp.alloc<double>(s * s);
+    const dim3 gg(gy, gy);
+    launch("k_dgemm", k_dgemm<false, false>, gg, NT, 0, st, ET64, (int64_t)mc.npS, (const double*)M1, s, Lbar, s,
+           si, -1.0);
+    launch("k_dgemm", k_dgemm<true, false>, gg, NT, 0, st, (const double*)Lm, s, (const double*)Lbar, s, X, s, si,
+           1.0);
+    launch("k_phi", k_phi, nblk(s * s), NT, 0, st, X, si);
+    launch("k_dgemm", k_dgemm<false, true>, gg, NT, 0, st, (const double*)X, s, ET64, (int64_t)mc.npS, Y, s, si,
+           1.0);
+    launch("k_dgemm", k_dgemm<false, false>, gg, NT, 0, st, ET64, (int64_t)mc.npS, (const double*)Y, s, Sb, s, si,
+           1.0);
+    double* pS = tmp.alloc<double>(s * np2);
+    launch("k_grad_kss", k_grad_kss, (unsigned)s, NT, 0, st, (const double*)Sb, (const double*)mc.ss64, si, d,
+           mc.ss2, pS);
+    // ordered reduction of the partial sums on the host
+    std::vector<double> h1(it_g.size() * np2), h2((size_t)gx * gy * np2), h3(s * np2);
+    LMA_CK(cudaMemcpyAsync(h1.data(), pG, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaMemcpyAsync(h2.data(), pK, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaMemcpyAsync(h3.data(), pS, sizeof(double) * h3.size(), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaStreamSynchronize(st));
+    for (int q = 0; q < np2; ++q) grad[q] = 0.0;
+    for (const auto* v : {&h1, &h2, &h3})
+      for (size_t i = 0; i < v->size(); i += np2)
+        for (int q = 0; q < np2; ++q) grad[q] += (*v)[i + q];
+    *ll = mc.loglik;
+    tmp.release();
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
+}
+
+// Tensor-core tile product self-check (see lma_tc_gemm_check in lma.h).
+void tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                   float* C, int64_t ldc, int tile_n, cudaStream_t st) {
+  Arena tmp;
+  tmp.st = st;
+  try {
+    int* err = tmp.alloc<int>(1);
+    LMA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    dim3 grid((unsigned)((N + tile_n - 1) / tile_n), (unsigned)((M + 127) / 128));
+    if (tile_n == 64) {
+      const size_t sm = sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack;
+      LMA_CK(cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      launch("k_tc_gemm", k_tc_gemm<64>, grid, 256, sm, st, A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, err);
+    } else {
+      const size_t sm = sizeof(tc::TcSmem<128>) + tc::kTcAlignSlack;
+      LMA_CK(cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      launch("k_tc_gemm", k_tc_gemm<128>, grid, 256, sm, st, A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, err);
+    }
+    int h = 0;
+    LMA_CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaStreamSynchronize(st));
+    if (h) {
+      fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+      throw Fail{};
+    }
+    tmp.release();
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
 }
 
 template struct Impl<float>;

@@ -1,0 +1,250 @@
+// 5th-generation tensor-core (tcgen05) building blocks for sm_103a, written
+// as inline PTX: tensor-memory allocation and loads, shared-memory matrix
+// descriptors (K-major, 128-byte swizzle), the TF32 MMA and mbarrier waits
+// with an iteration limit.
+//
+// FP32 operands are used as a 3-term TF32 split: x = hi + lo with hi the
+// TF32 rounding of x; a.b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b accumulated in
+// FP32 tensor memory (the published "3xTF32" technique), which keeps about
+// 22 bits of every product.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lma {
+namespace tc {
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // iterations before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier --------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---- fences ----------------------------------------------------------------
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ---- tensor memory ---------------------------------------------------------
+// whole warp; the allocated column base is written to *dst (shared memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns (lane = warp quadrant * 32 + laneid)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- descriptors -----------------------------------------------------------
+// K-major operand tile in shared memory with the 128-byte swizzle: rows of
+// 128 bytes (32 FP32/TF32 values of K), 8-row atoms 1024 bytes apart; the
+// tile base must be 1024-byte aligned.  Advancing K by 8 TF32 values inside
+// the atom advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // [0,14)  start address >> 4
+  d |= (uint64_t)1 << 16;                             // [16,30) leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                   // [32,46) stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                             // [46,49) fixed 0b001
+  d |= (uint64_t)2 << 61;                             // [61,64) 128-byte swizzle
+  return d;
+}
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+// byte offset of element (row, k) (k < 32) in a 128B-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {
+  return row * 128u + ((((k >> 2) ^ (row & 7u)) & 7u) << 4) + (k & 3u) * 4u;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on *bar once every previously issued MMA of this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// TF32 rounding (nearest, ties away) of an FP32 value; the result keeps the
+// FP32 encoding with the 13 low mantissa bits cleared.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+}  // namespace tc
+}  // namespace lma
+
+namespace lma {
+namespace tc {
+
+// Shared-memory stage of a 128 x BN tile product over 32 values of K:
+// TF32 hi/lo halves of both operands, each 128B-swizzled and 1024-aligned.
+template <int BN>
+struct alignas(1024) TcStage {
+  float a_hi[128 * 32];
+  float a_lo[128 * 32];
+  float b_hi[BN * 32];
+  float b_lo[BN * 32];
+};
+template <int BN>
+struct TcSmem {
+  TcStage<BN> st[2];
+  uint64_t bar[2];
+  uint32_t tmem;
+};
+constexpr size_t kTcAlignSlack = 1024;
+
+template <int BN>
+__device__ __forceinline__ TcSmem<BN>& tc_smem(unsigned char* raw) {
+  uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+  p = (p + 1023) & ~uintptr_t(1023);
+  return *reinterpret_cast<TcSmem<BN>*>(p);
+}
+
+// Split a float4 of K-consecutive values into TF32 hi/lo and store both at
+// (row, k..k+3) of a swizzled tile.
+__device__ __forceinline__ void store_split4(float* hi, float* lo, uint32_t row, uint32_t k, float4 v) {
+  float4 h, l;
+  h.x = tf32_round(v.x); l.x = v.x - h.x;
+  h.y = tf32_round(v.y); l.y = v.y - h.y;
+  h.z = tf32_round(v.z); l.z = v.z - h.z;
+  h.w = tf32_round(v.w); l.w = v.w - h.w;
+  const uint32_t off = sw128_offset(row, k) >> 2;
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+}  // namespace tc
+
+// Self-check kernel: C[M x N] = A[M x K] B[N x K]^T (row-major FP32, K % 32 == 0,
+// lda/ldb % 4 == 0), one CTA per 128 x BN output tile, 3xTF32 on tcgen05.
+template <int BN>
+__global__ void __launch_bounds__(256) k_tc_gemm(const float* __restrict__ A, int64_t lda,
+                                                 const float* __restrict__ Bm, int64_t ldb, float* __restrict__ C,
+                                                 int64_t ldc, int M, int N, int K, int* __restrict__ err) {
+  using namespace tc;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<BN>& sm = tc_smem<BN>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem, BN < 32 ? 32 : BN);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  const uint32_t idesc = idesc_tf32(128, BN);
+  const int nchunk = K / 32;
+  bool ok = true;
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = c & 1;
+    if (c >= 2) {
+      // every thread waits (bounded), then all agree on the outcome
+      const bool w = mbar_wait(&sm.bar[s], ((c >> 1) - 1) & 1);
+      ok = __syncthreads_and(w) != 0;
+      if (!ok) break;
+    }
+    TcStage<BN>& S = sm.st[s];
+    const int k0 = c * 32;
+    for (int i = tid; i < 128 * 8; i += 256) {
+      const int row = i >> 3, c4 = i & 7;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + row < M) v = *reinterpret_cast<const float4*>(A + (int64_t)(m0 + row) * lda + k0 + c4 * 4);
+      store_split4(S.a_hi, S.a_lo, row, c4 * 4, v);
+    }
+    for (int i = tid; i < BN * 8; i += 256) {
+      const int row = i >> 3, c4 = i & 7;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n0 + row < N) v = *reinterpret_cast<const float4*>(Bm + (int64_t)(n0 + row) * ldb + k0 + c4 * 4);
+      store_split4(S.b_hi, S.b_lo, row, c4 * 4, v);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t o = ks * 32;
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+      }
+      mma_commit(&sm.bar[s]);
+    }
+  }
+  if (ok && nchunk > 0) {
+    const bool w = mbar_wait(&sm.bar[(nchunk - 1) & 1], ((nchunk - 1) >> 1) & 1);
+    ok = __syncthreads_and(w) != 0;
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  fence_after_sync();
+  if (ok) {
+    const int q = warp & 3, half = warp >> 2;
+    const int row = m0 + q * 32 + (tid & 31);
+    for (int cb = half * (BN / 2); cb < (half + 1) * (BN / 2); cb += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + cb, v);
+      if (row < M)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + cb + j < N) C[(int64_t)row * ldc + n0 + cb + j] = v[j];
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
+}
+
+}  // namespace lma
