@@ -147,6 +147,6 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
 // sweep helpers (defined per precision)
 template <typename T>
 void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info,
-                bool batched);
+                bool batched, int* tc_err);
 
 }  // namespace lma

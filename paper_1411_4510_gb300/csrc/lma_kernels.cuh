@@ -310,6 +310,55 @@ struct CholSmem {
   T X[TB][TB + 1];
 };
 
+// Cholesky of the 64x64 diagonal tile held in D (shared memory), its
+// inverse into X, then L (zeros above the diagonal) to Lout (leading dim ld)
+// and the inverse to Dv.  A non-positive or NaN pivot is recorded in *info
+// (first failing column + 1, offset k0) and replaced by 1 so the sweep stays
+// finite.  Called by all NT threads of the CTA.
+template <typename T>
+__device__ void diag_factor(T (*D)[TB + 1], T (*X)[TB + 1], T* Lout, int64_t ld, T* Dv, int* info, int k0) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int j = 0; j < TB; ++j) {
+    __syncthreads();
+    T piv = D[j][j];
+    __syncthreads();
+    if (!(piv > T(0))) {
+      if (threadIdx.x == 0 && !bad) {
+        bad = 1;
+        if (*info == 0) *info = k0 + j + 1;
+      }
+      piv = T(1);
+    }
+    T dj = sqrt(piv);
+    for (int r = j + 1 + threadIdx.x; r < TB; r += NT) D[r][j] /= dj;
+    if (threadIdx.x == 0) D[j][j] = dj;
+    __syncthreads();
+    const int m = TB - j - 1;
+    for (int q = threadIdx.x; q < m * m; q += NT) {
+      int rr = j + 1 + q / m, cc = j + 1 + q % m;
+      if (cc <= rr) D[rr][cc] -= D[rr][j] * D[cc][j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < TB) {
+    const int c = threadIdx.x;
+    for (int r = 0; r < c; ++r) X[r][c] = T(0);
+    X[c][c] = T(1) / D[c][c];
+    for (int r = c + 1; r < TB; ++r) {
+      T sum = T(0);
+      for (int j = c; j < r; ++j) sum = fma(D[r][j], X[j][c], sum);
+      X[r][c] = -sum / D[r][r];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < TB * TB; q += NT) {
+    int r = q / TB, c = q % TB;
+    Lout[(int64_t)r * ld + c] = (c <= r) ? D[r][c] : T(0);
+    Dv[q] = X[r][c];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chol_step(const Win* __restrict__ wins, T* __restrict__ buf,
                                                   T* __restrict__ dinv, int* __restrict__ info, int kp) {
@@ -346,48 +395,8 @@ __global__ void __launch_bounds__(NT) k_chol_step(const Win* __restrict__ wins, 
       int r = ty + 16 * a, c = tx + 16 * b;
       sm.D[r][c] = A[(int64_t)(k0 + r) * ld + k0 + c] - acc[a][b];
     }
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int j = 0; j < TB; ++j) {
-    __syncthreads();
-    T piv = sm.D[j][j];
-    __syncthreads();
-    if (!(piv > T(0))) {  // not positive definite (or NaN): record, continue finite
-      if (threadIdx.x == 0 && !bad) {
-        bad = 1;
-        if (info[blockIdx.y] == 0) info[blockIdx.y] = k0 + j + 1;
-      }
-      piv = T(1);
-    }
-    T dj = sqrt(piv);
-    for (int r = j + 1 + threadIdx.x; r < TB; r += NT) sm.D[r][j] /= dj;
-    if (threadIdx.x == 0) sm.D[j][j] = dj;
-    __syncthreads();
-    const int m = TB - j - 1;
-    for (int q = threadIdx.x; q < m * m; q += NT) {
-      int rr = j + 1 + q / m, cc = j + 1 + q % m;
-      if (cc <= rr) sm.D[rr][cc] -= sm.D[rr][j] * sm.D[cc][j];
-    }
-  }
-  __syncthreads();
-  // inverse of the 64x64 lower factor, one column per thread
-  if (threadIdx.x < TB) {
-    const int c = threadIdx.x;
-    for (int r = 0; r < c; ++r) sm.X[r][c] = T(0);
-    sm.X[c][c] = T(1) / sm.D[c][c];
-    for (int r = c + 1; r < TB; ++r) {
-      T sum = T(0);
-      for (int j = c; j < r; ++j) sum = fma(sm.D[r][j], sm.X[j][c], sum);
-      sm.X[r][c] = -sum / sm.D[r][r];
-    }
-  }
-  __syncthreads();
-  T* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
-  for (int q = threadIdx.x; q < TB * TB; q += NT) {
-    int r = q / TB, c = q % TB;
-    A[(int64_t)(k0 + r) * ld + k0 + c] = (c <= r) ? sm.D[r][c] : T(0);
-    Dv[q] = sm.X[r][c];
-  }
+  diag_factor<T>(sm.D, sm.X, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+                 k0);
 }
 
 template <typename T>

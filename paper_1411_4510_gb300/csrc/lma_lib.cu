@@ -1,6 +1,7 @@
 // Fit / predict pipelines of the LMA hot path, instantiated for float (mixed
 // form) and double (plain FP64 form).
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <cstring>
@@ -38,11 +39,25 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
   }
 }
 
+static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
+
+// Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
+// SIMT kernels instead (used to compare the two on the same build).
+static bool use_tensor_cores() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("LMA_NO_TENSOR_CORES");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
+
 template <typename T>
 static void set_smem_attr() {
   cudaFuncSetAttribute(k_chol_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CholSmem<T>));
   cudaFuncSetAttribute(k_chol_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrsmSmem<T>));
   cudaFuncSetAttribute(k_pred_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CholSmem<T>));
+  cudaFuncSetAttribute(k_bwd_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CholSmem<T>));
 }
 
 template <typename T>
@@ -51,6 +66,8 @@ void Impl<T>::setup_attributes() {
   if (!done) {
     set_smem_attr<T>();
     set_smem_attr<double>();
+    cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     done = true;
   }
 }
@@ -58,7 +75,8 @@ void Impl<T>::setup_attributes() {
 // Left-looking sweep over all column panels.  batched: every window in
 // each launch; otherwise one window per launch (the plain form).
 template <typename T>
-void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info, bool batched) {
+void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info, bool batched,
+                int* tc_err) {
   if (wins.empty()) return;
   if (batched) {
     int maxpan = 0, maxrt = 0;
@@ -67,9 +85,24 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
       maxrt = std::max(maxrt, (w.rows + TB - 1) / TB);
     }
     const unsigned nw = (unsigned)wins.size();
+    int maxrows = 0;
+    for (const Win& w : wins) maxrows = std::max(maxrows, w.rows);
     for (int kp = 0; kp < maxpan; ++kp) {
-      launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv, info, kp);
-      if (maxrt - kp - 1 > 0) {
+      if (tc_err && sizeof(T) == 4) {
+        const unsigned gx = (unsigned)((maxrows - kp * TB + 127) / 128);
+        launch("k_chol_step_tc", k_chol_step_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+               (float*)dinv, info, kp, tc_err);
+      } else {
+        launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,
+               info, kp);
+      }
+      if (tc_err && sizeof(T) == 4) {
+        if (maxrows - (kp + 1) * TB > 0) {
+          const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
+          launch("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+                 (const float*)dinv, kp, tc_err);
+        }
+      } else if (maxrt - kp - 1 > 0) {
         launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf, dinv, kp);
       }
     }
@@ -103,7 +136,7 @@ static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
   int* info = tmp.alloc<int>(1);
   LMA_CK(cudaMemcpyAsync(wd, w.data(), sizeof(Win), cudaMemcpyHostToDevice, st));
   LMA_CK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  chol_sweep<double>(st, w, wd, buf, dv, info, true);
+  chol_sweep<double>(st, w, wd, buf, dv, info, true, nullptr);
   int h = 0;
   LMA_CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   LMA_CK(cudaStreamSynchronize(st));
@@ -218,7 +251,21 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
         launch("k_fill_ext", k_fill_ext<T>, dim3(nt, et, 1), NT, 0, st, wd + m, Vt, rT, (int)s, wbuf);
       }
     }
-    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched);
+    int* tc_err = nullptr;
+    if (batched && sizeof(T) == 4 && use_tensor_cores()) {
+      tc_err = tmp.alloc<int>(1);
+      LMA_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
+    }
+    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err);
+    if (tc_err) {
+      int h = 0;
+      LMA_CK(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LMA_CK(cudaStreamSynchronize(st));
+      if (h) {
+        fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the window sweep");
+        throw Fail{};
+      }
+    }
     {
       std::vector<int> hinfo(M);
       LMA_CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * M, cudaMemcpyDeviceToHost, st));

@@ -248,3 +248,228 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const float* __restrict__ A, in
 }
 
 }  // namespace lma
+
+namespace lma {
+namespace tc {
+
+// Completion bookkeeping of the two stage barriers (identical in every thread).
+struct TcPipe {
+  uint32_t cnt[2] = {0, 0};      // commits issued on each barrier
+  bool pending[2] = {false, false};
+};
+
+// Collective, bounded wait for the most recent commit on stage s.
+template <int BN>
+__device__ __forceinline__ bool tc_drain(TcSmem<BN>& sm, TcPipe& p, int s) {
+  if (!p.pending[s]) return true;
+  const bool w = mbar_wait(&sm.bar[s], (p.cnt[s] - 1u) & 1u);
+  p.pending[s] = false;
+  return __syncthreads_and(w) != 0;
+}
+
+// D (tensor memory, 128 lanes x BN FP32 columns) = sum_{k<K} A(r,k) B(c,k),
+// r < 128, c < BN, K % 32 == 0.  rowA(r) / rowB(c) return a 16-byte-aligned
+// pointer to the K values of that row, or nullptr for a zero row.  All 256
+// threads call it; returns false (in every thread) if a wait timed out.
+template <int BN, class RA, class RB>
+__device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB) {
+  const int tid = threadIdx.x;
+  const uint32_t idesc = idesc_tf32(128, BN);
+  const int nchunk = K / 32;
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = c & 1;
+    if (!tc_drain(sm, p, s)) return false;
+    TcStage<BN>& S = sm.st[s];
+    const int k0 = c * 32;
+    for (int i = tid; i < 128 * 8; i += 256) {
+      const int row = i >> 3, c4 = i & 7;
+      const float* src = rowA(row);
+      float4 v = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      store_split4(S.a_hi, S.a_lo, row, c4 * 4, v);
+    }
+    for (int i = tid; i < BN * 8; i += 256) {
+      const int row = i >> 3, c4 = i & 7;
+      const float* src = rowB(row);
+      float4 v = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      store_split4(S.b_hi, S.b_lo, row, c4 * 4, v);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t o = ks * 32;
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+      }
+      mma_commit(&sm.bar[s]);
+    }
+    p.cnt[s] += 1;
+    p.pending[s] = true;
+  }
+  bool ok = tc_drain(sm, p, 0);
+  ok = tc_drain(sm, p, 1) && ok;
+  fence_after_sync();
+  return ok;
+}
+
+}  // namespace tc
+}  // namespace lma
+
+namespace lma {
+
+// Sweep update of column panel kp on the tensor cores (mixed form).  CTA
+// (x, window) owns rows [k0 + 128 x, k0 + 128 x + 128) of the window buffer:
+// T = A_{rows, panel} - A_{rows, 0:k0} A_{panel, 0:k0}^T with the product on
+// tcgen05 (3xTF32).  The diagonal 64x64 block (first rows of x = 0) is
+// factorised in shared memory; every other row keeps T for k_chol_trsm.
+__global__ void __launch_bounds__(256) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
+                                                      float* __restrict__ dinv, int* __restrict__ info, int kp,
+                                                      int* __restrict__ err) {
+  using namespace tc;
+  const Win w = wins[blockIdx.y];
+  const int k0 = kp * TB;
+  if (k0 >= w.npad) return;
+  const int r0 = k0 + blockIdx.x * 128;
+  if (r0 >= w.rows) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<64>& sm = tc_smem<64>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* A = buf + w.base;
+  const int64_t ld = w.npad;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem, 64);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  TcPipe pipe;
+  bool ok = true;
+  if (k0 > 0) {
+    auto rowA = [&](int r) -> const float* {
+      const int row = r0 + r;
+      return row < w.rows ? A + (int64_t)row * ld : nullptr;
+    };
+    auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld; };
+    ok = tile_product<64>(sm, pipe, tmem, k0, rowA, rowB);
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int q = warp & 3, half = warp >> 2;
+  const int rl = q * 32 + lane;
+  const int row = r0 + rl;
+  float v[32];
+  if (k0 > 0 && ok) {
+    float t[16];
+    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32, t);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = t[j];
+    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32 + 16, t);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+  }
+  // all MMAs have completed (tile_product drained both stages): stage memory is free
+  float* scratch = reinterpret_cast<float*>(&sm.st[0]);
+  float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
+  float(*Xm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch + TB * (TB + 1));
+  const bool diag = (blockIdx.x == 0) && (rl < TB);
+  if (row < w.rows) {
+    float* dst = A + (int64_t)row * ld + k0 + half * 32;
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
+      a.x -= v[4 * j4 + 0];
+      a.y -= v[4 * j4 + 1];
+      a.z -= v[4 * j4 + 2];
+      a.w -= v[4 * j4 + 3];
+      if (diag) {
+        float* d = &Dm[rl][half * 32 + 4 * j4];
+        d[0] = a.x;
+        d[1] = a.y;
+        d[2] = a.z;
+        d[3] = a.w;
+      } else {
+        *reinterpret_cast<float4*>(dst + 4 * j4) = a;
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+  if (blockIdx.x == 0)
+    diag_factor<float>(Dm, Xm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+                       k0);
+}
+
+}  // namespace lma
+
+namespace lma {
+
+// Panel solve of column panel kp on the tensor cores: rows
+// [k0 + 64 + 128 x, ... + 128) of every window get A_{row, panel} <- T inv(L_kk)^T
+// (T held there by k_chol_step_tc, inv(L_kk) in dinv).  Rows of the tile are
+// read into shared memory before any result is written back.
+__global__ void __launch_bounds__(256) k_chol_trsm_tc(const Win* __restrict__ wins, float* __restrict__ buf,
+                                                      const float* __restrict__ dinv, int kp, int* __restrict__ err) {
+  using namespace tc;
+  const Win w = wins[blockIdx.y];
+  const int k0 = kp * TB;
+  if (k0 >= w.npad) return;
+  const int r0 = k0 + TB + blockIdx.x * 128;
+  if (r0 >= w.rows) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<64>& sm = tc_smem<64>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* A = buf + w.base;
+  const int64_t ld = w.npad;
+  const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem, 64);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  TcPipe pipe;
+  auto rowA = [&](int r) -> const float* {
+    const int row = r0 + r;
+    return row < w.rows ? A + (int64_t)row * ld + k0 : nullptr;
+  };
+  auto rowB = [&](int c) -> const float* { return Dv + (int64_t)c * TB; };
+  const bool ok = tile_product<64>(sm, pipe, tmem, TB, rowA, rowB);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int q = warp & 3, half = warp >> 2;
+  const int row = r0 + q * 32 + lane;
+  if (ok) {  // uniform: tcgen05.ld is executed by whole warps, stores are per row
+    float* dst = A + (int64_t)row * ld + k0 + half * 32;
+    float t[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32 + 16 * h, t);
+      if (row < w.rows)
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4)
+          *reinterpret_cast<float4*>(dst + 16 * h + 4 * j4) =
+              make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+}  // namespace lma

@@ -1,7 +1,9 @@
 """Tensor-core (tcgen05, 3xTF32) tile product against an FP64 product of the
-same FP32 operands.  Bound: each product keeps ~22 bits (2^-22 ~ 2.4e-7
-relative to |a||b|) and the FP32 accumulation over K adds ~K^(1/2) 2^-24;
-the error is measured against sum_k |a_ik||b_jk| and held to 1e-6."""
+same FP32 operands.  Bound, relative to sum_k |a_ik||b_jk|: each 3xTF32
+product keeps ~22 bits (2^-22 = 2.4e-7; the dropped lo*lo term is 2^-22 too)
+and the FP32 accumulation in tensor memory over K terms adds ~K^(1/2) 2^-24
+in expectation; the test allows 2^-21 + 4 K^(1/2) 2^-24 (8e-7 + 2.4e-7
+K^(1/2)), i.e. 6.2e-6 at K = 512."""
 import ctypes as C
 
 import numpy as np
@@ -38,4 +40,5 @@ def test_tc_gemm_3xtf32(lib, shape, tile_n):
     out = Cm.double().cpu().numpy()
     assert np.all(np.isfinite(out))
     err = np.max(np.abs(out - ref) / scale)
-    assert err <= 1e-6, err
+    bound = 2.0 ** -21 + 4.0 * np.sqrt(K) * 2.0 ** -24
+    assert err <= bound, (err, bound)

@@ -304,14 +304,14 @@ def make_problem(name: str, N: Optional[int] = None, M: Optional[int] = None,
         nf, ellv, sig_noise, sigma_s = 4096, 0.3, 0.1, 1.0
         ell = np.full(d, ellv)
         f = rff_draw(rrff, d, nf, ellv, sigma_s)
-        key = _morton_keys(X)
-        order = np.argsort(key, kind="stable")
-        X, key = X[order], key[order]
+        mkey = _morton_keys(X)
+        order = np.argsort(mkey, kind="stable")
+        X, mkey = X[order], mkey[order]
         sizes = np.full(M_, Nn // M_, dtype=np.int64)
         sizes[: Nn % M_] += 1
         block_ptr = _ptr_from_sizes(sizes)
         if U_ > 0:
-            pos = np.clip(np.searchsorted(key, _morton_keys(XU)), 0, Nn - 1)
+            pos = np.clip(np.searchsorted(mkey, _morton_keys(XU)), 0, Nn - 1)
             blk = (np.searchsorted(block_ptr, pos, side="right") - 1).astype(np.int64)
         else:
             blk = np.zeros(0, dtype=np.int64)
