@@ -854,3 +854,63 @@ __global__ void k_pred_final(const T* __restrict__ Vu, int64_t U, int s, const d
 }
 
 }  // namespace lma
+
+namespace lma {
+
+// ---------------------------------------------------------------------------
+// Right-looking blocked Cholesky of ONE matrix with appended rows (used in
+// FP64 for Sigma_SS and for I + A): for panel kp, factor the already-updated
+// diagonal tile, solve the panel below it (k_chol_trsm), then update every
+// trailing tile (i, j), kp < j <= i, and every appended-row tile against the
+// panel.  Same result as the left-looking sweep; far more CTAs per launch.
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_diag_factor(const Win* __restrict__ wins, T* __restrict__ buf,
+                                                    T* __restrict__ dinv, int* __restrict__ info, int kp) {
+  const Win w = wins[0];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CholSmem<T>& sm = *reinterpret_cast<CholSmem<T>*>(smraw);
+  T* A = buf + w.base;
+  const int64_t ld = w.npad;
+  const int k0 = kp * TB;
+  for (int q = threadIdx.x; q < TB * TB; q += NT) sm.D[q / TB][q % TB] = A[(int64_t)(k0 + q / TB) * ld + k0 + q % TB];
+  diag_factor<T>(sm.D, sm.X, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info, k0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_trail_update(const Win* __restrict__ wins, T* __restrict__ buf, int kp) {
+  const Win w = wins[0];
+  const int npan = w.npad / TB;
+  const int m = npan - kp - 1;  // trailing panels
+  const int t1 = m * (m + 1) / 2;
+  int i, j;
+  if ((int)blockIdx.x < t1) {
+    int I, J;
+    tri_index(blockIdx.x, I, J);
+    i = kp + 1 + I;
+    j = kp + 1 + J;
+  } else {
+    const int t = blockIdx.x - t1;
+    i = npan + t / m;
+    j = kp + 1 + t % m;
+  }
+  const int r0 = i * TB, c0 = j * TB, k0 = kp * TB;
+  if (r0 >= w.rows) return;
+  __shared__ GemmSmem<T> sm;
+  T* A = buf + w.base;
+  const int64_t ld = w.npad;
+  T acc[4][4] = {};
+  auto fa = [&](int r, int k) -> T { int row = r0 + r; return row < w.rows ? A[row * ld + k0 + k] : T(0); };
+  auto fb = [&](int r, int k) -> T { return A[(int64_t)(c0 + r) * ld + k0 + k]; };
+  tile_mma<T, true, true>(acc, TB, sm, fa, fb);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int row = r0 + ty + 16 * a;
+      if (row < w.rows) A[row * ld + c0 + tx + 16 * b] -= acc[a][b];
+    }
+}
+
+}  // namespace lma

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "lma_impl.cuh"
@@ -66,8 +68,11 @@ void Impl<T>::setup_attributes() {
   if (!done) {
     set_smem_attr<T>();
     set_smem_attr<double>();
+    cudaFuncSetAttribute(k_diag_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CholSmem<double>));
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     done = true;
   }
 }
@@ -120,6 +125,20 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
   }
 }
 
+// Right-looking factorisation of one FP64 matrix (see k_trail_update).
+static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info) {
+  const int npan = w.npad / TB, nrt = (w.rows + TB - 1) / TB;
+  for (int kp = 0; kp < npan; ++kp) {
+    launch("k_diag_factor", k_diag_factor<double>, 1, NT, sizeof(CholSmem<double>), st, wd, buf, dv, info, kp);
+    if (nrt - kp - 1 > 0)
+      launch("k_chol_trsm", k_chol_trsm<double>, dim3(nrt - kp - 1, 1), NT, sizeof(TrsmSmem<double>), st, wd, buf,
+             dv, kp);
+    const int m = npan - kp - 1;
+    const int tiles = m * (m + 1) / 2 + (nrt - npan) * m;
+    if (tiles > 0) launch("k_trail_update", k_trail_update<double>, tiles, NT, 0, st, wd, buf, kp);
+  }
+}
+
 // Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
 // `extra` extra rows).  Returns false when it is not positive definite.
 static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra) {
@@ -136,7 +155,7 @@ static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
   int* info = tmp.alloc<int>(1);
   LMA_CK(cudaMemcpyAsync(wd, w.data(), sizeof(Win), cudaMemcpyHostToDevice, st));
   LMA_CK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  chol_sweep<double>(st, w, wd, buf, dv, info, true, nullptr);
+  right_looking_fp64(st, w[0], wd, buf, dv, info);
   int h = 0;
   LMA_CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   LMA_CK(cudaStreamSynchronize(st));
@@ -404,8 +423,27 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     if (mc.prec == LMA_MIXED) {
       launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu, (int)s,
                                                            (T)mc.ss2, Pbuf);
-      launch("k_pred_sweep", k_pred_sweep<T>, (unsigned)it_sw.size(), NT, sizeof(CholSmem<T>), st, pd, isd, mc.wins_d, wbuf,
-                                                                              (const T*)mc.dinv, Pbuf);
+      if (sizeof(T) == 4 && use_tensor_cores()) {
+        std::vector<int2> it_tc;
+        for (size_t pi = 0; pi < pairs.size(); ++pi)
+          for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut) it_tc.push_back(make_int2((int)pi, ut));
+        int2* itc = tmp.alloc<int2>(it_tc.size());
+        int* terr = tmp.alloc<int>(1);
+        LMA_CK(cudaMemcpyAsync(itc, it_tc.data(), sizeof(int2) * it_tc.size(), cudaMemcpyHostToDevice, st));
+        LMA_CK(cudaMemsetAsync(terr, 0, sizeof(int), st));
+        launch("k_pred_sweep_tc", k_pred_sweep_tc, (unsigned)it_tc.size(), 256, tc_chol_smem(), st, pd,
+               (const int2*)itc, mc.wins_d, (const float*)wbuf, (const float*)mc.dinv, (float*)Pbuf, terr);
+        int h = 0;
+        LMA_CK(cudaMemcpyAsync(&h, terr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LMA_CK(cudaStreamSynchronize(st));
+        if (h) {
+          fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the prediction sweep");
+          throw Fail{};
+        }
+      } else {
+        launch("k_pred_sweep", k_pred_sweep<T>, (unsigned)it_sw.size(), NT, sizeof(CholSmem<T>), st, pd, isd,
+               mc.wins_d, wbuf, (const T*)mc.dinv, Pbuf);
+      }
     } else {
       // plain form: one pair per launch
       size_t a = 0, b = 0;

@@ -273,26 +273,45 @@ __device__ __forceinline__ bool tc_drain(TcSmem<BN>& sm, TcPipe& p, int s) {
 // threads call it; returns false (in every thread) if a wait timed out.
 template <int BN, class RA, class RB>
 __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB) {
+  constexpr int NA = 128 * 8 / 256;          // float4 of A per thread per chunk
+  constexpr int NB = (BN * 8 + 255) / 256;   // float4 of B per thread per chunk
   const int tid = threadIdx.x;
   const uint32_t idesc = idesc_tf32(128, BN);
   const int nchunk = K / 32;
+  // the chunk's global loads are issued one chunk ahead into registers, so
+  // their latency overlaps the barrier and the MMAs of the previous chunk
+  float4 ra[NA], rb[NB];
+  auto load = [&](int c) {
+    const int k0 = c * 32;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+      const float* src = rowA(row);
+      ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+      const float* src = (i < BN * 8) ? rowB(row) : nullptr;
+      rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (nchunk > 0) load(0);
   for (int c = 0; c < nchunk; ++c) {
     const int s = c & 1;
     if (!tc_drain(sm, p, s)) return false;
     TcStage<BN>& S = sm.st[s];
-    const int k0 = c * 32;
-    for (int i = tid; i < 128 * 8; i += 256) {
-      const int row = i >> 3, c4 = i & 7;
-      const float* src = rowA(row);
-      float4 v = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-      store_split4(S.a_hi, S.a_lo, row, c4 * 4, v);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int i = tid + 256 * j;
+      store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
     }
-    for (int i = tid; i < BN * 8; i += 256) {
-      const int row = i >> 3, c4 = i & 7;
-      const float* src = rowB(row);
-      float4 v = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-      store_split4(S.b_hi, S.b_lo, row, c4 * 4, v);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int i = tid + 256 * j;
+      if (i < BN * 8) store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
     }
+    if (c + 1 < nchunk) load(c + 1);
     fence_async_smem();
     fence_before_sync();
     __syncthreads();
@@ -467,6 +486,107 @@ __global__ void __launch_bounds__(256) k_chol_trsm_tc(const Win* __restrict__ wi
               make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
     }
   }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+}  // namespace lma
+
+namespace lma {
+
+// Forward solve of the prediction right-hand sides on the tensor cores: CTA
+// (pair, 128 test rows) sweeps the window's column panels left to right,
+//   T = P[:, panel] - P[:, 0:k0] L[panel, 0:k0]^T ;  P[:, panel] = T inv(L_kk)^T
+// with both products on tcgen05 (3xTF32).  items: x = pair, y = 128-row tile.
+__global__ void __launch_bounds__(256) k_pred_sweep_tc(const Pair* __restrict__ pairs, const int2* __restrict__ items,
+                                                       const Win* __restrict__ wins, const float* __restrict__ buf,
+                                                       const float* __restrict__ dinv, float* __restrict__ P,
+                                                       int* __restrict__ err) {
+  using namespace tc;
+  const int2 it = items[blockIdx.x];
+  const Pair pr = pairs[it.x];
+  const Win w = wins[pr.win];
+  const int u0 = it.y * 128;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<64>& sm = tc_smem<64>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* L = buf + w.base;
+  const int64_t ld = w.npad;
+  float* Pp = P + pr.pbase;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem, 64);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  TcPipe pipe;
+  const int q = warp & 3, half = warp >> 2;
+  const int rl = q * 32 + lane;
+  const bool live = (u0 + rl) < pr.nu;
+  float* myrow = Pp + (int64_t)(u0 + rl) * ld;
+  const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+  bool ok = true;
+  const int npan = w.npad / TB;
+  for (int kp = 0; kp < npan && ok; ++kp) {
+    const int k0 = kp * TB;
+    float v[32];
+    if (k0 > 0) {
+      auto rowA = [&](int r) -> const float* {
+        return (u0 + r) < pr.nu ? Pp + (int64_t)(u0 + r) * ld : nullptr;
+      };
+      auto rowB = [&](int c) -> const float* { return L + (int64_t)(k0 + c) * ld; };
+      ok = tile_product<64>(sm, pipe, tmem, k0, rowA, rowB);
+      if (!ok) break;
+      float t[16];
+      tmem_ld16(taddr, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = t[j];
+      tmem_ld16(taddr + 16, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0.f;
+    }
+    if (live) {
+      float* dst = myrow + k0 + half * 32;
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
+        a.x -= v[4 * j4 + 0];
+        a.y -= v[4 * j4 + 1];
+        a.z -= v[4 * j4 + 2];
+        a.w -= v[4 * j4 + 3];
+        *reinterpret_cast<float4*>(dst + 4 * j4) = a;
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+    const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
+    auto rowT = [&](int r) -> const float* { return (u0 + r) < pr.nu ? Pp + (int64_t)(u0 + r) * ld + k0 : nullptr; };
+    auto rowD = [&](int c) -> const float* { return Dv + (int64_t)c * TB; };
+    ok = tile_product<64>(sm, pipe, tmem, TB, rowT, rowD);
+    if (!ok) break;
+    float t[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tmem_ld16(taddr + 16 * h, t);
+      if (live) {
+        float* dst = myrow + k0 + half * 32 + 16 * h;
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4)
+          *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
