@@ -172,6 +172,33 @@ lma_status lma_tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, in
                              const float* B, int64_t ldb, float* C, int64_t ldc, int tile_n,
                              void* cuda_stream);
 
+/* Global step of the fit without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory on their call path (a serving runtime or framework that
+ * pre-provisions all device memory and forbids allocation while handling a
+ * request, or a caller whose device memory belongs to another allocator).
+ *
+ * From the whitened summaries of a fit (lma_model_summary: A is s x s, y has
+ * s entries, quad and log|R-bar_DD| are scalars; n = |D|) it factorises
+ * I + A in FP64 and returns beta = (I + A)^-1 y in beta_out (s doubles) and
+ * scalars_out = { y^T (I + A)^-1 y, log|I + A|, log N(y_D; mu, Sigma-bar_DD) }
+ * (3 doubles).  A, y, beta_out and scalars_out are DEVICE pointers owned by
+ * the caller; the work is ordered on cuda_stream and synchronised before the
+ * call returns.
+ *
+ * All scratch lives in one fixed device array inside the library, sized for
+ * s <= 1024 (about 17 MB, held by every GPU that loads the library until the
+ * process exits); larger s returns LMA_ERR_INVALID_ARG.  The call allocates
+ * nothing.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  LMA_ERR_NOT_PD (block -2) if I + A is not positive
+ * definite.                                                                */
+lma_status lma_global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y,
+                                   double quad, double logdet_R, double* beta_out,
+                                   double* scalars_out, void* cuda_stream);
+
 /* Launch profiler (a single-threaded diagnostic, off by default; not part of
  * the paper's method).  lma_profile_start clears earlier records and, until
  * lma_profile_stop, brackets every launch whose kernel name contains

@@ -293,6 +293,14 @@ lma_status lma_tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, in
   return guarded([&] { tc_gemm_check(M, N, K, A, lda, B, ldb, C, ldc, tile_n, (cudaStream_t)cuda_stream); });
 }
 
+lma_status lma_global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y, double quad,
+                                   double logdet_R, double* beta_out, double* scalars_out, void* cuda_stream) {
+  if (s < 1 || n < 1 || !A || !y || !beta_out || !scalars_out || !isfinite(quad) || !isfinite(logdet_R))
+    return fail(LMA_ERR_INVALID_ARG, "lma_global_step_noalloc: bad sizes or null pointer");
+  return guarded([&] { global_step_noalloc(s, n, A, y, quad, logdet_R, beta_out, scalars_out,
+                                           (cudaStream_t)cuda_stream); });
+}
+
 void lma_profile_start(const char* name_filter) {
   prof::g_on = true;
   prof::g_filter = name_filter ? name_filter : "";

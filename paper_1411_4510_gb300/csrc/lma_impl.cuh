@@ -140,6 +140,9 @@ struct Impl {
 void tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
                    float* C, int64_t ldc, int tile_n, cudaStream_t st);
 
+void global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y, double quad, double logdet_R,
+                         double* beta, double* scalars, cudaStream_t st);
+
 // builds the window descriptors of a partition (Section 3: W_m = D_m u D^B_m)
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t elem, std::vector<Win>& wins,
                   int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems);

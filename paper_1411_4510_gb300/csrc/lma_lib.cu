@@ -675,6 +675,146 @@ void tc_gemm_check(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the global step.
+//
+// For callers that cannot allocate device memory themselves on the call
+// path: a serving runtime or framework that pre-provisions all device memory
+// and forbids allocation while it handles a request, or a pipeline whose
+// device memory is owned by another allocator.  The kernels below need
+// scratch (the (npad + 1 + s) x npad factorisation buffer, the inverted
+// diagonal tiles, a window descriptor and a status flag); this variant keeps
+// all of it in one file-scope device array of fixed size, so the call itself
+// never allocates.  The array is part of the library's image: every GPU that
+// loads the library holds it (about 17 MB) until the process exits.
+constexpr int kNoAllocMaxS = 1024;
+constexpr int64_t kNoAllocBuf = (int64_t)(2 * kNoAllocMaxS + 1) * kNoAllocMaxS;  // doubles
+constexpr int64_t kNoAllocDinv = (int64_t)kNoAllocMaxS * TB;                      // doubles
+constexpr int64_t kNoAllocMeta = 64;                                               // Win + flag
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBuf + kNoAllocDinv + kNoAllocMeta];
+
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is fetched once
+// per device (with that device current) and cached.
+static double* noalloc_scratch() {
+  static std::mutex mu;
+  static double* addr[256] = {};
+  int dev = 0;
+  LMA_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    fail(LMA_ERR_INTERNAL, "device index out of range");
+    throw Fail{};
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      fail(LMA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      throw Fail{};
+    }
+    addr[dev] = static_cast<double*>(p);
+  }
+  return addr[dev];
+}
+
+static __global__ void k_noalloc_setup(Win* wslot, Win w, int* flag) {
+  *wslot = w;
+  *flag = 0;
+}
+
+// C = I + A (A: s x s, ld s), extra row y, then s identity rows (the layout of k_build_global)
+static __global__ void k_noalloc_build(const double* __restrict__ A, const double* __restrict__ y, int s, int npad,
+                                       double* __restrict__ buf) {
+  int64_t total = (int64_t)(npad + 1 + s) * npad;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int i = (int)(e / npad), j = (int)(e % npad);
+  double v;
+  if (i < npad) {
+    if (i < s && j < s) v = A[(int64_t)i * s + j] + (i == j ? 1.0 : 0.0);
+    else v = (i == j) ? 1.0 : 0.0;
+  } else if (i == npad) {
+    v = (j < s) ? y[j] : 0.0;
+  } else {
+    v = ((i - npad - 1) == j) ? 1.0 : 0.0;
+  }
+  buf[e] = v;
+}
+
+// out[0] = w^T w (w = L_C^-1 y), out[1] = log|I + A|, out[2] = loglik; beta = L_C^-T w
+static __global__ void k_noalloc_finish(const double* __restrict__ buf, int s, int npad, double quad,
+                                        double logdet_R, double n, double* __restrict__ beta,
+                                        double* __restrict__ out) {
+  const double* w = buf + (int64_t)npad * npad;
+  const double* E = w + npad;
+  __shared__ double red[NT];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < s; i += NT) {
+    a += w[i] * w[i];
+    b += log(buf[(int64_t)i * npad + i]);
+  }
+  for (int k = threadIdx.x; k < s; k += NT) {
+    double sum = 0.0;
+    const double* row = E + (int64_t)k * npad;
+    for (int i = 0; i < s; ++i) sum += row[i] * w[i];
+    beta[k] = sum;
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double wCw = red[0];
+  __syncthreads();
+  red[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double ldC = 2.0 * red[0];
+    out[0] = wCw;
+    out[1] = ldC;
+    out[2] = -0.5 * (quad - wCw) - 0.5 * (logdet_R + ldC) - 0.5 * n * log(2.0 * M_PI);
+  }
+}
+
+void global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y, double quad, double logdet_R,
+                         double* beta, double* scalars, cudaStream_t st) {
+  if (s < 1 || s > kNoAllocMaxS) {
+    fail(LMA_ERR_INVALID_ARG, "lma_global_step_noalloc: s must lie in [1, " + std::to_string(kNoAllocMaxS) +
+                                  "] (fixed size of its device scratch array)");
+    throw Fail{};
+  }
+  Impl<float>::setup_attributes();
+  double* base = noalloc_scratch();
+  double* buf = base;
+  double* dv = base + kNoAllocBuf;
+  Win* wslot = reinterpret_cast<Win*>(base + kNoAllocBuf + kNoAllocDinv);
+  int* flag = reinterpret_cast<int*>(base + kNoAllocBuf + kNoAllocDinv + 32);
+  const int npad = (int)roundup(s, TB);
+  Win w{};
+  w.n = (int)s;
+  w.npad = npad;
+  w.rows = npad + 1 + (int)s;
+  launch("k_noalloc_setup", k_noalloc_setup, 1, 1, 0, st, wslot, w, flag);
+  launch("k_noalloc_build", k_noalloc_build, nblk((int64_t)(npad + 1 + s) * npad), NT, 0, st, A, y, (int)s, npad,
+         buf);
+  right_looking_fp64(st, w, wslot, buf, dv, flag);
+  launch("k_noalloc_finish", k_noalloc_finish, 1, NT, 0, st, (const double*)buf, (int)s, npad, quad, logdet_R,
+         (double)n, beta, scalars);
+  int h = 0;
+  LMA_CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LMA_CK(cudaStreamSynchronize(st));
+  if (h) {
+    fail(LMA_ERR_NOT_PD, "I + A is not positive definite", -2);
+    throw Fail{};
+  }
+}
+
 template struct Impl<float>;
 template struct Impl<double>;
 
