@@ -32,7 +32,7 @@ loglik_grad()    Hand adjoint of the summary-form log-likelihood with respect
                  pinned by central finite differences of loglik and, at
                  B = M-1, by the closed-form full-GP gradient.
 
-Readings of the paper used here (all listed in the design doc):
+Readings of the paper used here:
   * noise sigma_n^2 on the D-D diagonal (and U-U when noisy) only;
   * Sigma_SS = K_SS + jitter I, the same matrix in Q and in Sigma-ddot_SS;
   * constant prior mean mu;
