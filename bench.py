@@ -80,12 +80,13 @@ def kernel_work(p, B):
             n = ws[m][0]
             psweep += nu * n * n
             prhs += 2.0 * nu * n * s
-    return {"k_chol_step_tc": upd, "k_chol_step": upd, "k_chol_trsm_tc": tri, "k_chol_trsm": tri,
-            "k_resid": resid, "k_gram": gram, "k_pred_sweep_tc": psweep, "k_pred_sweep": psweep,
-            "k_pred_rhs": prhs}
+    return {"k_chol_step_tc": upd, "k_chol_step_tma": upd, "k_chol_step": upd, "k_chol_trsm_tc": tri,
+            "k_resid": resid, "k_resid_tc": resid, "k_gram": gram, "k_pred_sweep_tc": psweep, "k_pred_sweep": psweep,
+            "k_pred_rhs": prhs, "k_pred_rhs_tc": prhs}
 
 
-TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_trsm_tc", "k_pred_sweep_tc"}
+TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_step_tma", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
+                  "k_pred_rhs_tc"}
 
 
 def predict_flops(p, B):

@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "../../include/lma.h"
+#include <cuda.h>
+
 #include "lma_types.cuh"
 
 namespace lma {
@@ -150,6 +152,6 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
 // sweep helpers (defined per precision)
 template <typename T>
 void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info,
-                bool batched, int* tc_err);
+                bool batched, int* tc_err, const CUtensorMap* maps);
 
 }  // namespace lma

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(NT) k_kds(const T* __restrict__ xs, int64_t n,
 // the whitened support coordinates V = L_SS^-1 Sigma_SD, stored point-major.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_proj(const T* __restrict__ Kds, int64_t n, int s, const T* __restrict__ ET,
-                                             T* __restrict__ Vt) {
+                                             T* __restrict__ Vt, int ldo) {
   __shared__ GemmSmem<T> sm;
   const int64_t p0 = (int64_t)blockIdx.y * TB;
   const int i0 = blockIdx.x * TB;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NT) k_proj(const T* __restrict__ Kds, int64_t 
     for (int j = 0; j < 4; ++j) {
       int64_t p = p0 + ty + 16 * i;
       int c = i0 + tx + 16 * j;
-      if (p < n && c < s) Vt[p * s + c] = acc[i][j];
+      if (p < n && c < s) Vt[p * ldo + c] = acc[i][j];
     }
 }
 
@@ -310,53 +310,91 @@ struct CholSmem {
   T X[TB][TB + 1];
 };
 
-// Cholesky of the 64x64 diagonal tile held in D (shared memory), its
-// inverse into X, then L (zeros above the diagonal) to Lout (leading dim ld)
-// and the inverse to Dv.  A non-positive or NaN pivot is recorded in *info
-// (first failing column + 1, offset k0) and replaced by 1 so the sweep stays
-// finite.  Called by all NT threads of the CTA.
-template <typename T>
-__device__ void diag_factor(T (*D)[TB + 1], T (*X)[TB + 1], T* Lout, int64_t ld, T* Dv, int* info, int k0) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int j = 0; j < TB; ++j) {
-    __syncthreads();
-    T piv = D[j][j];
-    __syncthreads();
-    if (!(piv > T(0))) {
-      if (threadIdx.x == 0 && !bad) {
-        bad = 1;
-        if (*info == 0) *info = k0 + j + 1;
+// Cholesky of the N x N diagonal tile held in D (shared memory, lower part
+// significant) together with the inverse of the factor; L (zeros above the
+// diagonal) goes to Lout (leading dim ld), inv(L) to Dv (N x N, row-major).
+// Called by all threads of the CTA, which must have at least 4N threads.
+//
+// Thread t < 4N keeps row t / 4 of the working matrix and of the inverse in
+// registers (columns congruent to t mod 4).  Step j: the owners publish
+// column j and the (unscaled) inverse row j to shared memory; after one
+// barrier every row below j applies the rank-1 update
+//   D_rc -= D_rj D_cj / D_jj,   Xt_rc -= D_rj / D_jj  Xt_jc,
+// which is the right-looking Cholesky and the right-looking solve of
+// L X = I in one sweep (X row j = Xt row j / L_jj).  The reciprocal square
+// root of pivot j is taken by the owner of the diagonal as soon as its last
+// update lands, overlapping the other rows' updates of the previous step.
+// A non-positive or NaN pivot is recorded in *info (first failing column +
+// 1, offset k0) and replaced by 1 so the sweep stays finite.
+template <typename T, int N = TB>
+__device__ void diag_factor(T (*D)[N + 1], T* Lout, int64_t ld, T* Dv, int* info, int k0) {
+  constexpr int NQ = N / 4;
+  __shared__ T colb[2][N];
+  __shared__ T xrow[2][N];
+  __shared__ T rjs[2];
+  const int t = threadIdx.x, rr = t >> 2, p = t & 3;
+  const bool act = t < 4 * N;
+  T d[NQ], x[NQ];
+  __syncthreads();  // the caller's stores to D are visible
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    d[q] = act ? D[rr][p + 4 * q] : T(0);
+    x[q] = (act && p + 4 * q == rr) ? T(1) : T(0);
+  }
+  __syncthreads();  // D is overwritten with L below
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const int qj = j >> 2, pj = j & 3;
+    T* cb = colb[j & 1];
+    T* xb = xrow[j & 1];
+    if (act && rr >= j) {
+      if (p == pj) cb[rr] = d[qj];
+      if (rr == j) {
+#pragma unroll
+        for (int q = 0; q <= qj; ++q)
+          if (p + 4 * q <= j) xb[p + 4 * q] = x[q];
+        if (p == pj) {
+          T piv = d[qj];
+          if (!(piv > T(0))) {
+            if (*info == 0) *info = k0 + j + 1;
+            piv = T(1);
+          }
+          const T r = rsqrt(piv);
+          rjs[j & 1] = r;
+          D[j][j] = piv * r;
+        }
       }
-      piv = T(1);
     }
-    T dj = sqrt(piv);
-    for (int r = j + 1 + threadIdx.x; r < TB; r += NT) D[r][j] /= dj;
-    if (threadIdx.x == 0) D[j][j] = dj;
     __syncthreads();
-    const int m = TB - j - 1;
-    for (int q = threadIdx.x; q < m * m; q += NT) {
-      int rr = j + 1 + q / m, cc = j + 1 + q % m;
-      if (cc <= rr) D[rr][cc] -= D[rr][j] * D[cc][j];
+    const T rj = rjs[j & 1];
+    if (act && rr == j) {
+#pragma unroll
+      for (int q = 0; q <= qj; ++q) x[q] *= rj;
+    } else if (act && rr > j) {
+      const T lr = cb[rr];
+      const T l = lr * rj;
+      const T a = l * rj;
+      if (p == pj) D[rr][j] = l;
+#pragma unroll
+      for (int q = qj; q < NQ; ++q) {
+        const int cc = p + 4 * q;
+        if (cc > j && cc <= rr) d[q] = fma(-a, cb[cc], d[q]);
+      }
+#pragma unroll
+      for (int q = 0; q <= qj; ++q) {
+        const int c = p + 4 * q;
+        if (c <= j) x[q] = fma(-a, xb[c], x[q]);
+      }
     }
   }
   __syncthreads();
-  if (threadIdx.x < TB) {
-    const int c = threadIdx.x;
-    for (int r = 0; r < c; ++r) X[r][c] = T(0);
-    X[c][c] = T(1) / D[c][c];
-    for (int r = c + 1; r < TB; ++r) {
-      T sum = T(0);
-      for (int j = c; j < r; ++j) sum = fma(D[r][j], X[j][c], sum);
-      X[r][c] = -sum / D[r][r];
-    }
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < TB * TB; q += NT) {
-    int r = q / TB, c = q % TB;
+  for (int q = t; q < N * N; q += blockDim.x) {
+    const int r = q / N, c = q % N;
     Lout[(int64_t)r * ld + c] = (c <= r) ? D[r][c] : T(0);
-    Dv[q] = X[r][c];
   }
+  if (act)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Dv[rr * N + p + 4 * q] = x[q];
 }
 
 template <typename T>
@@ -395,7 +433,7 @@ __global__ void __launch_bounds__(NT) k_chol_step(const Win* __restrict__ wins, 
       int r = ty + 16 * a, c = tx + 16 * b;
       sm.D[r][c] = A[(int64_t)(k0 + r) * ld + k0 + c] - acc[a][b];
     }
-  diag_factor<T>(sm.D, sm.X, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+  diag_factor<T>(sm.D, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
                  k0);
 }
 
@@ -406,14 +444,21 @@ struct TrsmSmem {
 };
 
 // A[i-tile][kp-panel] = T_ik inv(L_kk)^T for row tiles i > kp.
+// nid > 0: the first nid appended rows are identity rows (row k has its 1 in
+// column k), so an appended-row tile e whose rows all lie below nid is still
+// zero at panel kp < e and is skipped.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chol_trsm(const Win* __restrict__ wins, T* __restrict__ buf,
-                                                  const T* __restrict__ dinv, int kp) {
+                                                  const T* __restrict__ dinv, int kp, int nid) {
   const Win w = wins[blockIdx.y];
   if (kp * TB >= w.npad) return;
   const int i = kp + 1 + blockIdx.x;
   const int r0 = i * TB;
   if (r0 >= w.rows) return;
+  {
+    const int e = i - w.npad / TB;
+    if (e > kp && (e + 1) * TB <= nid) return;
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   TrsmSmem<T>& sm = *reinterpret_cast<TrsmSmem<T>*>(smraw);
   T* A = buf + w.base;
@@ -528,8 +573,9 @@ __global__ void k_sum_ordered(const double* __restrict__ v, int n, double* __res
   }
 }
 
-// Sigma-ddot_SS whitened: C = I + A, with extra rows [y; I] (the sweep then
-// yields L_C, L_C^-1 y and L_C^-T).
+// Sigma-ddot_SS whitened: C = I + A, with appended rows [I; y] (the sweep
+// then yields L_C, L_C^-T and L_C^-1 y; identity rows first so they stay
+// 64-aligned for the zero-tile skip).
 __global__ void k_build_global(const double* __restrict__ G, int s, int npad, double* __restrict__ buf) {
   const int se = s + 1;
   int64_t total = (int64_t)(npad + 1 + s) * npad;
@@ -540,10 +586,10 @@ __global__ void k_build_global(const double* __restrict__ G, int s, int npad, do
   if (i < npad) {
     if (i < s && j < s) v = G[(int64_t)(1 + i) * se + 1 + j] + (i == j ? 1.0 : 0.0);
     else v = (i == j) ? 1.0 : 0.0;
-  } else if (i == npad) {
-    v = (j < s) ? G[(int64_t)(1 + j) * se] : 0.0;
+  } else if (i < npad + s) {
+    v = ((i - npad) == j) ? 1.0 : 0.0;
   } else {
-    v = ((i - npad - 1) == j) ? 1.0 : 0.0;
+    v = (j < s) ? G[(int64_t)(1 + j) * se] : 0.0;
   }
   buf[e] = v;
 }
@@ -551,8 +597,8 @@ __global__ void k_build_global(const double* __restrict__ G, int s, int npad, do
 // scalars[0] = quad, [1] = w^T w (w = L_C^-1 y), [2] = log|C|; beta = L_C^-T w
 __global__ void k_global_finish(const double* __restrict__ buf, const double* __restrict__ G, int s, int npad,
                                 double* __restrict__ beta, double* __restrict__ scalars) {
-  const double* w = buf + (int64_t)npad * npad;
-  const double* E = w + npad;  // row k = (L_C^-T)[k][.]
+  const double* E = buf + (int64_t)npad * npad;  // row k = (L_C^-T)[k][.]
+  const double* w = E + (int64_t)s * npad;
   __shared__ double red[NT];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < s; i += NT) {
@@ -851,66 +897,6 @@ __global__ void k_pred_final(const T* __restrict__ Vu, int64_t U, int s, const d
     mean[warp] = mu + a + t1[warp];
     var[warp] = prior - b - t2[warp] + g;
   }
-}
-
-}  // namespace lma
-
-namespace lma {
-
-// ---------------------------------------------------------------------------
-// Right-looking blocked Cholesky of ONE matrix with appended rows (used in
-// FP64 for Sigma_SS and for I + A): for panel kp, factor the already-updated
-// diagonal tile, solve the panel below it (k_chol_trsm), then update every
-// trailing tile (i, j), kp < j <= i, and every appended-row tile against the
-// panel.  Same result as the left-looking sweep; far more CTAs per launch.
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_diag_factor(const Win* __restrict__ wins, T* __restrict__ buf,
-                                                    T* __restrict__ dinv, int* __restrict__ info, int kp) {
-  const Win w = wins[0];
-  extern __shared__ __align__(16) unsigned char smraw[];
-  CholSmem<T>& sm = *reinterpret_cast<CholSmem<T>*>(smraw);
-  T* A = buf + w.base;
-  const int64_t ld = w.npad;
-  const int k0 = kp * TB;
-  for (int q = threadIdx.x; q < TB * TB; q += NT) sm.D[q / TB][q % TB] = A[(int64_t)(k0 + q / TB) * ld + k0 + q % TB];
-  diag_factor<T>(sm.D, sm.X, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info, k0);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_trail_update(const Win* __restrict__ wins, T* __restrict__ buf, int kp) {
-  const Win w = wins[0];
-  const int npan = w.npad / TB;
-  const int m = npan - kp - 1;  // trailing panels
-  const int t1 = m * (m + 1) / 2;
-  int i, j;
-  if ((int)blockIdx.x < t1) {
-    int I, J;
-    tri_index(blockIdx.x, I, J);
-    i = kp + 1 + I;
-    j = kp + 1 + J;
-  } else {
-    const int t = blockIdx.x - t1;
-    i = npan + t / m;
-    j = kp + 1 + t % m;
-  }
-  const int r0 = i * TB, c0 = j * TB, k0 = kp * TB;
-  if (r0 >= w.rows) return;
-  __shared__ GemmSmem<T> sm;
-  T* A = buf + w.base;
-  const int64_t ld = w.npad;
-  T acc[4][4] = {};
-  auto fa = [&](int r, int k) -> T { int row = r0 + r; return row < w.rows ? A[row * ld + k0 + k] : T(0); };
-  auto fb = [&](int r, int k) -> T { return A[(int64_t)(c0 + r) * ld + k0 + k]; };
-  tile_mma<T, true, true>(acc, TB, sm, fa, fb);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int row = r0 + ty + 16 * a;
-      if (row < w.rows) A[row * ld + c0 + tx + 16 * b] -= acc[a][b];
-    }
 }
 
 }  // namespace lma

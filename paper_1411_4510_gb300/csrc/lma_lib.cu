@@ -13,6 +13,8 @@
 #include "lma_kernels.cuh"
 #include "lma_grad.cuh"
 #include "lma_tc.cuh"
+#include "lma_f64.cuh"
+#include <cudaTypedefs.h>
 
 namespace lma {
 
@@ -42,6 +44,58 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
 }
 
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
+constexpr int kTmaStages = 4;
+static size_t tma_chol_smem() { return sizeof(tc::TmaSmem<kTmaStages>) + tc::kTcAlignSlack; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library); nullptr if unavailable.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// One 2-D tensor map per window buffer (npad columns x rows rows, FP32,
+// 32 x 64 boxes with the 128-byte swizzle the MMA descriptors expect).
+static CUtensorMap* window_tensor_maps(const std::vector<Win>& wins, float* wbuf, Arena& tmp, cudaStream_t st) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return nullptr;
+  std::vector<CUtensorMap> maps(wins.size());
+  for (size_t m = 0; m < wins.size(); ++m) {
+    const Win& w = wins[m];
+    cuuint64_t gdim[2] = {(cuuint64_t)w.npad, (cuuint64_t)w.rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)w.npad * sizeof(float)};
+    cuuint32_t box[2] = {32, 64};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, wbuf + w.base, gdim, gstride, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+  }
+  CUtensorMap* d = tmp.alloc<CUtensorMap>(maps.size());
+  LMA_CK(cudaMemcpyAsync(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+// TMA-fed warp-specialised sweep update only when LMA_USE_TMA=1 (it measured
+// slower than the register-staged kernel on the configurations tried).
+static bool use_tma() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("LMA_USE_TMA");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+static size_t tc_resid_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
 // SIMT kernels instead (used to compare the two on the same build).
@@ -68,11 +122,13 @@ void Impl<T>::setup_attributes() {
   if (!done) {
     set_smem_attr<T>();
     set_smem_attr<double>();
-    cudaFuncSetAttribute(k_diag_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(CholSmem<double>));
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_chol_step_tma<kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tma_chol_smem());
     done = true;
   }
 }
@@ -81,7 +137,7 @@ void Impl<T>::setup_attributes() {
 // each launch; otherwise one window per launch (the plain form).
 template <typename T>
 void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info, bool batched,
-                int* tc_err) {
+                int* tc_err, const CUtensorMap* maps) {
   if (wins.empty()) return;
   if (batched) {
     int maxpan = 0, maxrt = 0;
@@ -93,7 +149,11 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
     int maxrows = 0;
     for (const Win& w : wins) maxrows = std::max(maxrows, w.rows);
     for (int kp = 0; kp < maxpan; ++kp) {
-      if (tc_err && sizeof(T) == 4) {
+      if (tc_err && sizeof(T) == 4 && maps) {
+        const unsigned gx = (unsigned)((maxrows - kp * TB + 127) / 128);
+        launch("k_chol_step_tma", k_chol_step_tma<kTmaStages>, dim3(gx, nw), 256, tma_chol_smem(), st, wins_d, maps,
+               (float*)buf, (float*)dinv, info, kp, tc_err);
+      } else if (tc_err && sizeof(T) == 4) {
         const unsigned gx = (unsigned)((maxrows - kp * TB + 127) / 128);
         launch("k_chol_step_tc", k_chol_step_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
                (float*)dinv, info, kp, tc_err);
@@ -108,7 +168,8 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
                  (const float*)dinv, kp, tc_err);
         }
       } else if (maxrt - kp - 1 > 0) {
-        launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf, dinv, kp);
+        launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf, dinv, kp,
+               0);
       }
     }
   } else {
@@ -118,30 +179,37 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
       for (int kp = 0; kp < npan; ++kp) {
         launch("k_chol_step", k_chol_step<T>, dim3(rt - kp, 1), NT, sizeof(CholSmem<T>), st, wins_d + wi, buf, dinv, info + wi, kp);
         if (rt - kp - 1 > 0) {
-          launch("k_chol_trsm", k_chol_trsm<T>, dim3(rt - kp - 1, 1), NT, sizeof(TrsmSmem<T>), st, wins_d + wi, buf, dinv, kp);
+          launch("k_chol_trsm", k_chol_trsm<T>, dim3(rt - kp - 1, 1), NT, sizeof(TrsmSmem<T>), st, wins_d + wi, buf, dinv, kp,
+                 0);
         }
       }
     }
   }
 }
 
-// Right-looking factorisation of one FP64 matrix (see k_trail_update).
-static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info) {
-  const int npan = w.npad / TB, nrt = (w.rows + TB - 1) / TB;
+// Right-looking factorisation of one FP64 matrix on 32 x 32 tiles (see
+// lma_f64.cuh).  nid: number of leading appended rows that are identity rows
+// (0 = none).  wd is unused (kept for the window form's signature).
+static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info,
+                               int nid = 0) {
+  (void)wd;
+  using namespace f64;
+  const int npan = w.npad / TS, nrt = (w.rows + TS - 1) / TS;
+  const int64_t ld = w.npad;
+  launch("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
   for (int kp = 0; kp < npan; ++kp) {
-    launch("k_diag_factor", k_diag_factor<double>, 1, NT, sizeof(CholSmem<double>), st, wd, buf, dv, info, kp);
     if (nrt - kp - 1 > 0)
-      launch("k_chol_trsm", k_chol_trsm<double>, dim3(nrt - kp - 1, 1), NT, sizeof(TrsmSmem<double>), st, wd, buf,
-             dv, kp);
+      launch("k_f64_trsm", k_f64_trsm, (unsigned)(nrt - kp - 1), NTH, 0, st, buf, ld, w.rows, npan, kp, nid,
+             (const double*)dv);
     const int m = npan - kp - 1;
     const int tiles = m * (m + 1) / 2 + (nrt - npan) * m;
-    if (tiles > 0) launch("k_trail_update", k_trail_update<double>, tiles, NT, 0, st, wd, buf, kp);
+    if (m > 0) launch("k_f64_trail", k_f64_trail, (unsigned)tiles, NTH, 0, st, buf, ld, w.rows, npan, kp, nid, dv, info);
   }
 }
 
 // Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
 // `extra` extra rows).  Returns false when it is not positive definite.
-static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra) {
+static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra, int nid) {
   std::vector<Win> w(1);
   w[0] = Win{};
   w[0].n = n;
@@ -155,7 +223,7 @@ static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
   int* info = tmp.alloc<int>(1);
   LMA_CK(cudaMemcpyAsync(wd, w.data(), sizeof(Win), cudaMemcpyHostToDevice, st));
   LMA_CK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  right_looking_fp64(st, w[0], wd, buf, dv, info);
+  right_looking_fp64(st, w[0], wd, buf, dv, info, nid);
   int h = 0;
   LMA_CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   LMA_CK(cudaStreamSynchronize(st));
@@ -211,7 +279,7 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   mc.kss = kb;
   mc.npS = npS;
   launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
-  if (!factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s)) {
+  if (!factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s)) {
     fail(LMA_ERR_NOT_PD, "Sigma_SS + jitter is not positive definite", -1);
     throw Fail{};
   }
@@ -222,7 +290,7 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   T* Kds = tmp.alloc<T>(n * s);
   launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, xsT, n, (int)d, ssT, (int)s, (T)mc.ss2, Kds);
   T* Vt = mc.keep.alloc<T>(n * s);
-  launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt);
+  launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt, (int)s);
   mc.Vt = Vt;
 }
 
@@ -258,7 +326,38 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
     const T* Vt = (const T*)mc.Vt;
     const T* xsT = (const T*)mc.xsT;
     const unsigned et = nblk(s + 1, TB);
-    if (batched) {
+    if (batched && sizeof(T) == 4 && use_tensor_cores()) {
+      // residual tiles on the tensor cores; V with a row stride padded to 32
+      const int sp = (int)roundup(s, 32);
+      const float* Vtp = (const float*)Vt;
+      if (sp != s) {
+        float* pad = tmp.alloc<float>((size_t)n * sp);
+        LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * sp, st));
+        LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * sp, Vt, sizeof(float) * s, sizeof(float) * s, n,
+                                 cudaMemcpyDeviceToDevice, st));
+        Vtp = pad;
+      }
+      std::vector<int4> items;
+      for (int64_t m = 0; m < M; ++m) {
+        const int np = mc.wins[m].npad;
+        for (int I = 0; I * 128 < np; ++I)
+          for (int J = 0; J * TB < np && J <= 2 * I + 1; ++J) items.push_back(make_int4((int)m, I, J, 0));
+      }
+      int4* itd = tmp.alloc<int4>(items.size());
+      int* rerr = tmp.alloc<int>(1);
+      LMA_CK(cudaMemcpyAsync(itd, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
+      LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
+             (const float*)xsT, d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
+      launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
+      int h = 0;
+      LMA_CK(cudaMemcpyAsync(&h, rerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LMA_CK(cudaStreamSynchronize(st));
+      if (h) {
+        fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the residual kernel");
+        throw Fail{};
+      }
+    } else if (batched) {
       launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
                                                                           (T)mc.sn2, wbuf);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
@@ -275,7 +374,9 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
       tc_err = tmp.alloc<int>(1);
       LMA_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
     }
-    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err);
+    const CUtensorMap* maps = nullptr;
+    if (tc_err && use_tma()) maps = window_tensor_maps(mc.wins, (float*)wbuf, tmp, st);
+    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err, maps);
     if (tc_err) {
       int h = 0;
       LMA_CK(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -314,7 +415,7 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
     const int npC = (int)roundup(s, TB);
     double* cb = tmp.alloc<double>((size_t)(npC + 1 + s) * npC);
     launch("k_build_global", k_build_global, nblk((int64_t)(npC + 1 + s) * npC), NT, 0, st, mc.G, (int)s, npC, cb);
-    if (!factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1)) {
+    if (!factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1, (int)s)) {
       fail(LMA_ERR_NOT_PD, "global summary Sigma-ddot_SS is not positive definite", -2);
       throw Fail{};
     }
@@ -322,7 +423,7 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
     double* sc = tmp.alloc<double>(4);
     launch("k_global_finish", k_global_finish, 1, NT, 0, st, cb, mc.G, (int)s, npC, mc.beta, sc);
     T* LcT = mc.keep.alloc<T>(s * s);
-    launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)(npC + 1) * npC, npC, (int)s, LcT);
+    launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)npC * npC, npC, (int)s, LcT);
     mc.LcT = LcT;
     launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, wd, wbuf, mc.beta, (int)s, ew);
     double hs[4], hr = 0;
@@ -365,7 +466,8 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     T* Kus = tmp.alloc<T>(U * s);
     launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s, (T)mc.ss2, Kus);
     T* Vu = tmp.alloc<T>(U * s);
-    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu);
+    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
+           (int)s);
     // pairs (test block n, window m in [n-B, n])
     std::vector<Pair> pairs;
     std::vector<int4> tb;  // per test block: first pair, count, u0, nu
@@ -421,9 +523,48 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     const T* Vt = (const T*)mc.Vt;
     const T* wbuf = (const T*)mc.wbuf;
     if (mc.prec == LMA_MIXED) {
-      launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu, (int)s,
-                                                           (T)mc.ss2, Pbuf);
-      if (sizeof(T) == 4 && use_tensor_cores()) {
+      const bool tc = (sizeof(T) == 4 && use_tensor_cores());
+      if (tc) {
+        // right-hand sides on the tensor cores; V rows with a stride padded to 32
+        const int sp = (int)roundup(s, 32);
+        const float* Vtp = (const float*)Vt;
+        const float* Vup = (const float*)Vu;
+        if (sp != s) {
+          float* a = tmp.alloc<float>((size_t)mc.n * sp);
+          float* b = tmp.alloc<float>((size_t)U * sp);
+          LMA_CK(cudaMemsetAsync(a, 0, sizeof(float) * mc.n * sp, st));
+          LMA_CK(cudaMemsetAsync(b, 0, sizeof(float) * U * sp, st));
+          LMA_CK(cudaMemcpy2DAsync(a, sizeof(float) * sp, Vt, sizeof(float) * s, sizeof(float) * s, mc.n,
+                                   cudaMemcpyDeviceToDevice, st));
+          LMA_CK(cudaMemcpy2DAsync(b, sizeof(float) * sp, Vu, sizeof(float) * s, sizeof(float) * s, U,
+                                   cudaMemcpyDeviceToDevice, st));
+          Vtp = a;
+          Vup = b;
+        }
+        std::vector<int4> it_r;
+        for (size_t pi = 0; pi < pairs.size(); ++pi) {
+          const int nct = mc.wins[pairs[pi].win].npad / TB;
+          for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut)
+            for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
+        }
+        int4* irr = tmp.alloc<int4>(it_r.size());
+        int* rerr = tmp.alloc<int>(1);
+        LMA_CK(cudaMemcpyAsync(irr, it_r.data(), sizeof(int4) * it_r.size(), cudaMemcpyHostToDevice, st));
+        LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), 256, tc_resid_smem(), st, pd, (const int4*)irr,
+               mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, rerr);
+        int hh = 0;
+        LMA_CK(cudaMemcpyAsync(&hh, rerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LMA_CK(cudaStreamSynchronize(st));
+        if (hh) {
+          fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the prediction right-hand sides");
+          throw Fail{};
+        }
+      } else {
+        launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
+               (int)s, (T)mc.ss2, Pbuf);
+      }
+      if (tc) {
         std::vector<int2> it_tc;
         for (size_t pi = 0; pi < pairs.size(); ++pi)
           for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut) it_tc.push_back(make_int2((int)pi, ut));
@@ -505,8 +646,30 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
     LMA_CK(cudaMemcpyAsync(wd, &w, sizeof(Win), cudaMemcpyHostToDevice, st));
     T* buf = tmp.alloc<T>((size_t)w.npad * w.npad);
     const int nt = w.npad / TB;
-    launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d, (const T*)mc.Vt,
-                                                           (int)mc.s, (T)mc.ss2, (T)mc.sn2, buf);
+    if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
+      const int64_t s = mc.s, n = mc.n;
+      const int sp = (int)roundup(s, 32);
+      const float* Vtp = (const float*)mc.Vt;
+      if (sp != s) {
+        float* pad = tmp.alloc<float>((size_t)n * sp);
+        LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * sp, st));
+        LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * sp, mc.Vt, sizeof(float) * s, sizeof(float) * s, n,
+                                 cudaMemcpyDeviceToDevice, st));
+        Vtp = pad;
+      }
+      std::vector<int4> items;
+      for (int I = 0; I * 128 < w.npad; ++I)
+        for (int J = 0; J * TB < w.npad && J <= 2 * I + 1; ++J) items.push_back(make_int4(0, I, J, 0));
+      int4* itd = tmp.alloc<int4>(items.size());
+      int* rerr = tmp.alloc<int>(1);
+      LMA_CK(cudaMemcpyAsync(itd, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
+      LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
+             (const float*)mc.xsT, (int)mc.d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)buf, rerr);
+    } else {
+      launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,
+             (const T*)mc.Vt, (int)mc.s, (T)mc.ss2, (T)mc.sn2, buf);
+    }
     std::vector<T> h((size_t)w.npad * w.npad);
     LMA_CK(cudaMemcpyAsync(h.data(), buf, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, st));
     LMA_CK(cudaStreamSynchronize(st));

@@ -271,65 +271,80 @@ __device__ __forceinline__ bool tc_drain(TcSmem<BN>& sm, TcPipe& p, int s) {
 // r < 128, c < BN, K % 32 == 0.  rowA(r) / rowB(c) return a 16-byte-aligned
 // pointer to the K values of that row, or nullptr for a zero row.  All 256
 // threads call it; returns false (in every thread) if a wait timed out.
-template <int BN, class RA, class RB>
-__device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB) {
+//
+// The global loads of a 32-wide K chunk are issued DEPTH chunks ahead into
+// a register ring (DEPTH x 24 KB per CTA for BN = 64), so with two CTAs per
+// SM several chunks are in flight while the current one is split into TF32
+// hi/lo, stored to the swizzled stage and multiplied.
+template <int BN, int DEPTH = 3, class RA, class RB>
+__device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB, int nacc = 1) {
   constexpr int NA = 128 * 8 / 256;          // float4 of A per thread per chunk
   constexpr int NB = (BN * 8 + 255) / 256;   // float4 of B per thread per chunk
   const int tid = threadIdx.x;
   const uint32_t idesc = idesc_tf32(128, BN);
   const int nchunk = K / 32;
-  // the chunk's global loads are issued one chunk ahead into registers, so
-  // their latency overlaps the barrier and the MMAs of the previous chunk
-  float4 ra[NA], rb[NB];
-  auto load = [&](int c) {
+  float4 ra[DEPTH][NA], rb[DEPTH][NB];
+  auto load = [&](int c, float4 (&xa)[NA], float4 (&xb)[NB]) {
     const int k0 = c * 32;
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
       const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
       const float* src = rowA(row);
-      ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xa[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
       const float* src = (i < BN * 8) ? rowB(row) : nullptr;
-      rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  if (nchunk > 0) load(0);
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
-    if (!tc_drain(sm, p, s)) return false;
-    TcStage<BN>& S = sm.st[s];
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const int i = tid + 256 * j;
-      store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
-    }
+  for (int d = 0; d < DEPTH; ++d)
+    if (d < nchunk) load(d, ra[d], rb[d]);
+  for (int cb = 0; cb < nchunk; cb += DEPTH) {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int i = tid + 256 * j;
-      if (i < BN * 8) store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
-    }
-    if (c + 1 < nchunk) load(c + 1);
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (tid == 0) {
-      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+    for (int d = 0; d < DEPTH; ++d) {
+      const int c = cb + d;
+      if (c >= nchunk) break;
+      const int s = c & 1;
+      if (!tc_drain(sm, p, s)) return false;
+      TcStage<BN>& S = sm.st[s];
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t o = ks * 32;
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+      for (int j = 0; j < NA; ++j) {
+        const int i = tid + 256 * j;
+        store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[d][j]);
       }
-      mma_commit(&sm.bar[s]);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int i = tid + 256 * j;
+        if (i < BN * 8) store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[d][j]);
+      }
+      if (c + DEPTH < nchunk) load(c + DEPTH, ra[d], rb[d]);
+      fence_async_smem();
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      if (tid == 0) {
+        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+        // split-K: chunk c accumulates into accumulator c mod nacc (columns
+        // [BN a, BN a + BN)); accumulators 0 .. min(nacc, nchunk) - 1 are written
+        const int a = c % nacc;
+        const bool first = c < nacc;
+        const uint32_t dd = tmem + (uint32_t)(BN * a);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (!first || ks > 0) ? 1u : 0u);
+          mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+          mma_tf32(dd, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        }
+        mma_commit(&sm.bar[s]);
+      }
+      p.cnt[s] += 1;
+      p.pending[s] = true;
     }
-    p.cnt[s] += 1;
-    p.pending[s] = true;
   }
   bool ok = tc_drain(sm, p, 0);
   ok = tc_drain(sm, p, 1) && ok;
@@ -347,7 +362,7 @@ namespace lma {
 // T = A_{rows, panel} - A_{rows, 0:k0} A_{panel, 0:k0}^T with the product on
 // tcgen05 (3xTF32).  The diagonal 64x64 block (first rows of x = 0) is
 // factorised in shared memory; every other row keeps T for k_chol_trsm.
-__global__ void __launch_bounds__(256) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
+__global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
                                                       int* __restrict__ err) {
   using namespace tc;
@@ -401,7 +416,6 @@ __global__ void __launch_bounds__(256) k_chol_step_tc(const Win* __restrict__ wi
   // all MMAs have completed (tile_product drained both stages): stage memory is free
   float* scratch = reinterpret_cast<float*>(&sm.st[0]);
   float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
-  float(*Xm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch + TB * (TB + 1));
   const bool diag = (blockIdx.x == 0) && (rl < TB);
   if (row < w.rows) {
     float* dst = A + (int64_t)row * ld + k0 + half * 32;
@@ -427,7 +441,7 @@ __global__ void __launch_bounds__(256) k_chol_step_tc(const Win* __restrict__ wi
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
   if (blockIdx.x == 0)
-    diag_factor<float>(Dm, Xm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+    diag_factor<float>(Dm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
                        k0);
 }
 
@@ -439,7 +453,7 @@ namespace lma {
 // [k0 + 64 + 128 x, ... + 128) of every window get A_{row, panel} <- T inv(L_kk)^T
 // (T held there by k_chol_step_tc, inv(L_kk) in dinv).  Rows of the tile are
 // read into shared memory before any result is written back.
-__global__ void __launch_bounds__(256) k_chol_trsm_tc(const Win* __restrict__ wins, float* __restrict__ buf,
+__global__ void __launch_bounds__(256, 2) k_chol_trsm_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       const float* __restrict__ dinv, int kp, int* __restrict__ err) {
   using namespace tc;
   const Win w = wins[blockIdx.y];
@@ -499,7 +513,7 @@ namespace lma {
 // (pair, 128 test rows) sweeps the window's column panels left to right,
 //   T = P[:, panel] - P[:, 0:k0] L[panel, 0:k0]^T ;  P[:, panel] = T inv(L_kk)^T
 // with both products on tcgen05 (3xTF32).  items: x = pair, y = 128-row tile.
-__global__ void __launch_bounds__(256) k_pred_sweep_tc(const Pair* __restrict__ pairs, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256, 2) k_pred_sweep_tc(const Pair* __restrict__ pairs, const int2* __restrict__ items,
                                                        const Win* __restrict__ wins, const float* __restrict__ buf,
                                                        const float* __restrict__ dinv, float* __restrict__ P,
                                                        int* __restrict__ err) {
@@ -590,6 +604,465 @@ __global__ void __launch_bounds__(256) k_pred_sweep_tc(const Pair* __restrict__ 
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+}  // namespace lma
+
+namespace lma {
+
+// Compensated tile product on the tensor cores: hi + lo = sum_{k<K} A(r,k) B(c,k)
+// for the calling thread's row r = 32 (warp mod 4) + lane and its 32 columns
+// c = 32 (warp / 4) + j of a 128 x 64 tile.  Each 32-wide K chunk goes into
+// one of two tensor-memory slots (columns [0,64) and [64,128) of tmem); as
+// soon as its MMAs complete, the chunk's partial sums are drained into
+// registers and added with TwoSum.  The tensor core's FP32 accumulation is
+// thus only 12 MMA steps deep and the cross-chunk sum is compensated.
+template <class RA, class RB>
+__device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, RB rowB, float (&hi)[32],
+                             float (&lo)[32]) {
+  using namespace tc;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int q = warp & 3, half = warp >> 2;
+  const uint32_t tlane = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  auto drain = [&](int slot) {
+    float t[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tmem_ld16(tlane + 64 * slot + 16 * h, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
+    }
+  };
+  const uint32_t idesc = idesc_tf32(128, 64);
+  const int nchunk = K / 32;
+  TcPipe p;
+  bool ok = true;
+  float4 ra[4], rb[2];
+  auto load = [&](int c) {
+    const int k0 = c * 32;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+      const float* src = rowA(row);
+      ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+      const float* src = rowB(row);
+      rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (nchunk > 0) load(0);
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = c & 1;
+    if (p.pending[s]) {  // chunk c-2 used stage s and slot s: wait for it, then drain the slot
+      ok = tc_drain(sm, p, s);
+      if (!ok) break;
+      fence_after_sync();
+      drain(s);
+      fence_before_sync();
+    }
+    TcStage<64>& S = sm.st[s];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = tid + 256 * j;
+      store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = tid + 256 * j;
+      store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
+    }
+    if (c + 1 < nchunk) load(c + 1);
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+      const uint32_t dcol = tmem + 64 * s;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t o = ks * 32;
+        mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
+        mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+        mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+      }
+      mma_commit(&sm.bar[s]);
+    }
+    p.cnt[s] += 1;
+    p.pending[s] = true;
+  }
+  for (int k = 0; k < 2 && ok; ++k) {  // the last one or two chunks, in order
+    const int c = nchunk - 2 + k;
+    if (c < 0) continue;
+    const int s = c & 1;
+    if (p.pending[s]) {
+      ok = tc_drain(sm, p, s);
+      if (!ok) break;
+      fence_after_sync();
+      drain(s);
+      fence_before_sync();
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ void tc_setup(tc::TcSmem<64>& sm, uint32_t ncols) {
+  using namespace tc;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sm.tmem, ncols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+
+__device__ __forceinline__ void tc_teardown(tc::TcSmem<64>& sm, uint32_t ncols) {
+  using namespace tc;
+  fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(sm.tmem, ncols);
+}
+
+// Residual tiles on the tensor cores (mixed form).  Item (window, I, J): rows
+// [128 I, 128 I + 128) x columns [64 J, 64 J + 64) of the window's residual
+// R = K + sigma_n^2 I - Vt Vt^T, blanket-first, with the Vt Vt^T sum of
+// comp_product.  Vtp: point-major V with leading dimension ldv (a multiple
+// of 32, zero pad).
+__global__ void __launch_bounds__(256, 2) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
+                                                  const float* __restrict__ xs, int d, const float* __restrict__ Vtp,
+                                                  int ldv, float ss2, float sn2, float* __restrict__ buf,
+                                                  int* __restrict__ err) {
+  using namespace tc;
+  const int4 it = items[blockIdx.x];
+  const Win w = wins[it.x];
+  const int r0 = it.y * 128, c0 = it.z * TB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<64>& sm = tc_smem<64>(smraw);
+  __shared__ float xc[TB][MAXD + 1];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < TB * d; e += 256) {
+    const int r = e / d, q = e % d;
+    xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
+  }
+  tc_setup(sm, 128);
+  auto rowA = [&](int r) -> const float* {
+    const int i = r0 + r;
+    return (i < w.n) ? Vtp + (w.g_end - 1 - i) * (int64_t)ldv : nullptr;
+  };
+  auto rowB = [&](int c) -> const float* {
+    const int j = c0 + c;
+    return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
+  };
+  float hi[32], lo[32];
+  const bool ok = comp_product(sm, sm.tmem, ldv, rowA, rowB, hi, lo);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int q = warp & 3, half = warp >> 2;
+  const int i = r0 + q * 32 + lane;
+  if (ok && i < w.npad) {
+    float xr[MAXD];
+    for (int t = 0; t < d; ++t) xr[t] = (i < w.n) ? xs[(w.g_end - 1 - i) * d + t] : 0.f;
+    float* dst = buf + w.base + (int64_t)i * w.npad + c0 + half * 32;
+    float out[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int cl = half * 32 + j;
+      const int jj = c0 + cl;
+      float v;
+      if (i < w.n && jj < w.n) {
+        float d2 = 0.f;
+        for (int t2 = 0; t2 < d; ++t2) {
+          const float u = xr[t2] - xc[cl][t2];
+          d2 = fmaf(u, u, d2);
+        }
+        v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
+        if (i == jj) v += sn2;
+      } else {
+        v = (i == jj) ? 1.f : 0.f;
+      }
+      out[j] = v;
+    }
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4)
+      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
+  }
+  tc_teardown(sm, 128);
+}
+
+// Prediction right-hand sides on the tensor cores: item (pair, u tile of
+// 128, column tile of 64): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
+// the window of the pair, with the compensated product (the same cancellation
+// as the residual).  Vup / Vtp: leading dimension ldv (multiple of 32).
+__global__ void __launch_bounds__(256, 2) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
+                                                     const Win* __restrict__ wins, const float* __restrict__ xs,
+                                                     const float* __restrict__ xu, int d, const float* __restrict__ Vtp,
+                                                     const float* __restrict__ Vup, int ldv, float ss2,
+                                                     float* __restrict__ P, int* __restrict__ err) {
+  using namespace tc;
+  const int4 it = items[blockIdx.x];
+  const Pair pr = pairs[it.x];
+  const Win w = wins[pr.win];
+  const int u0 = it.y * 128, c0 = it.z * TB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcSmem<64>& sm = tc_smem<64>(smraw);
+  __shared__ float xc[TB][MAXD + 1];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < TB * d; e += 256) {
+    const int r = e / d, q = e % d;
+    xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
+  }
+  tc_setup(sm, 128);
+  auto rowA = [&](int r) -> const float* {
+    const int uu = u0 + r;
+    return (uu < pr.nu) ? Vup + (int64_t)(pr.u0 + uu) * ldv : nullptr;
+  };
+  auto rowB = [&](int c) -> const float* {
+    const int j = c0 + c;
+    return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
+  };
+  float hi[32], lo[32];
+  const bool ok = comp_product(sm, sm.tmem, ldv, rowA, rowB, hi, lo);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int q = warp & 3, half = warp >> 2;
+  const int uu = u0 + q * 32 + lane;
+  if (ok && uu < pr.nu) {
+    float xr[MAXD];
+    for (int t = 0; t < d; ++t) xr[t] = xu[(int64_t)(pr.u0 + uu) * d + t];
+    float* dst = P + pr.pbase + (int64_t)uu * w.npad + c0 + half * 32;
+    float out[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int cl = half * 32 + j;
+      float v = 0.f;
+      if (c0 + cl < w.n) {
+        float d2 = 0.f;
+        for (int t2 = 0; t2 < d; ++t2) {
+          const float u = xr[t2] - xc[cl][t2];
+          d2 = fmaf(u, u, d2);
+        }
+        v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
+      }
+      out[j] = v;
+    }
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4)
+      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
+  }
+  tc_teardown(sm, 128);
+}
+
+}  // namespace lma
+
+#include <cuda.h>
+
+namespace lma {
+namespace tc {
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// 2-D tiled TMA load of box (x = column, y = row) into shared memory,
+// completion signalled on *bar (complete_tx)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Ring of shared-memory stages for a 128 x 64 tile product over 32 values of
+// K: raw FP32 tiles land by TMA in a/b and are rounded there to TF32 (hi),
+// the remainders go to a_lo/b_lo.
+struct alignas(1024) TmaStage {
+  float a[128 * 32];
+  float a_lo[128 * 32];
+  float b[64 * 32];
+  float b_lo[64 * 32];
+};
+template <int ST>
+struct TmaSmem {
+  TmaStage st[ST];
+  uint64_t full[ST], conv[ST], empty[ST];
+  uint64_t done;
+  uint32_t tmem;
+  int abort;
+};
+
+}  // namespace tc
+
+// Sweep update of column panel kp (mixed form) with a TMA-fed, warp-
+// specialised tensor-core pipeline.  Warp 0 (one lane) loads 32-column slices
+// of the row tile (128 rows) and of the panel rows (64) through the window's
+// tensor map into an ST-stage ring; warps 2-7 split each slice into TF32
+// hi/lo; warp 1 (one lane) issues the three MMAs per 8-wide K step and frees
+// the stage with tcgen05.commit.  The epilogue (T = A - D, diagonal
+// factorisation) is that of k_chol_step_tc.
+template <int ST>
+__global__ void __launch_bounds__(256) k_chol_step_tma(const Win* __restrict__ wins,
+                                                       const CUtensorMap* __restrict__ maps, float* __restrict__ buf,
+                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
+                                                       int* __restrict__ err) {
+  using namespace tc;
+  const Win w = wins[blockIdx.y];
+  const int k0 = kp * TB;
+  if (k0 >= w.npad) return;
+  const int r0 = k0 + blockIdx.x * 128;
+  if (r0 >= w.rows) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uintptr_t pbase = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023);
+  TmaSmem<ST>& sm = *reinterpret_cast<TmaSmem<ST>*>(pbase);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const CUtensorMap* map = maps + blockIdx.y;
+  float* A = buf + w.base;
+  const int64_t ld = w.npad;
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.conv[s], 6);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(&sm.done, 1);
+    sm.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&sm.tmem, 64);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  const int nchunk = k0 / 32;
+  bool ok = true;
+  if (nchunk > 0) {
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int c = 0; c < nchunk; ++c) {
+          const int s = c % ST, j = c / ST;
+          if (*(volatile int*)&sm.abort) break;
+          if (c >= ST && !mbar_wait(&sm.empty[s], (j - 1) & 1)) {
+            sm.abort = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&sm.full[s], (128 + 64) * 32 * 4);
+          tma_load_2d(sm.st[s].a, map, c * 32, r0, &sm.full[s]);
+          tma_load_2d(sm.st[s].a + 64 * 32, map, c * 32, r0 + 64, &sm.full[s]);
+          tma_load_2d(sm.st[s].b, map, c * 32, k0, &sm.full[s]);
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        const uint32_t idesc = idesc_tf32(128, 64);
+        for (int c = 0; c < nchunk; ++c) {
+          const int s = c % ST, j = c / ST;
+          if (*(volatile int*)&sm.abort) break;
+          if (!mbar_wait(&sm.conv[s], j & 1)) {
+            sm.abort = 1;
+            break;
+          }
+          fence_after_sync();
+          TmaStage& S = sm.st[s];
+          const uint32_t ah = smem_addr(S.a), al = smem_addr(S.a_lo);
+          const uint32_t bh = smem_addr(S.b), bl = smem_addr(S.b_lo);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+            mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+          }
+          mma_commit(&sm.empty[s]);
+        }
+        mma_commit(&sm.done);
+      }
+    } else {
+      const int ct = tid - 64;  // 192 converter threads
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c % ST, j = c / ST;
+        if (*(volatile int*)&sm.abort) break;
+        if (!mbar_wait(&sm.full[s], j & 1)) {
+          sm.abort = 1;
+          break;
+        }
+        TmaStage& S = sm.st[s];
+        for (int i = ct; i < (128 + 64) * 8; i += 192) {
+          float4* hp = (i < 128 * 8) ? reinterpret_cast<float4*>(S.a) + i : reinterpret_cast<float4*>(S.b) + (i - 1024);
+          float4* lp =
+              (i < 128 * 8) ? reinterpret_cast<float4*>(S.a_lo) + i : reinterpret_cast<float4*>(S.b_lo) + (i - 1024);
+          float4 v = *hp, h, l;
+          h.x = tf32_round(v.x); l.x = v.x - h.x;
+          h.y = tf32_round(v.y); l.y = v.y - h.y;
+          h.z = tf32_round(v.z); l.z = v.z - h.z;
+          h.w = tf32_round(v.w); l.w = v.w - h.w;
+          *hp = h;
+          *lp = l;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.conv[s]);
+      }
+    }
+    // everybody waits for the last MMA (bounded), then agrees on the outcome
+    const bool w_ok = mbar_wait(&sm.done, 0);
+    ok = __syncthreads_and(w_ok && !sm.abort) != 0;
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  fence_after_sync();
+  const int q = warp & 3, half = warp >> 2;
+  const int rl = q * 32 + lane;
+  const int row = r0 + rl;
+  float v[32];
+  if (nchunk > 0 && ok) {
+    float t[16];
+    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32, t);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = t[j];
+    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32 + 16, t);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+  }
+  float* scratch = reinterpret_cast<float*>(&sm.st[0]);
+  float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
+  const bool diag = (blockIdx.x == 0) && (rl < TB);
+  if (row < w.rows) {
+    float* dst = A + (int64_t)row * ld + k0 + half * 32;
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
+      a.x -= v[4 * j4 + 0];
+      a.y -= v[4 * j4 + 1];
+      a.z -= v[4 * j4 + 2];
+      a.w -= v[4 * j4 + 3];
+      if (diag) {
+        float* dd = &Dm[rl][half * 32 + 4 * j4];
+        dd[0] = a.x;
+        dd[1] = a.y;
+        dd[2] = a.z;
+        dd[3] = a.w;
+      } else {
+        *reinterpret_cast<float4*>(dst + 4 * j4) = a;
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 64);
+  if (blockIdx.x == 0)
+    diag_factor<float>(Dm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+                       k0);
 }
 
 }  // namespace lma
