@@ -8,7 +8,6 @@
 #include <vector>
 
 #include "../../include/lma.h"
-#include <cuda.h>
 
 #include "lma_types.cuh"
 
@@ -152,6 +151,6 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
 // sweep helpers (defined per precision)
 template <typename T>
 void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info,
-                bool batched, int* tc_err, const CUtensorMap* maps);
+                bool batched, int* tc_err);
 
 }  // namespace lma

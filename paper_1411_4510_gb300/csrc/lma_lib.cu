@@ -14,7 +14,6 @@
 #include "lma_grad.cuh"
 #include "lma_tc.cuh"
 #include "lma_f64.cuh"
-#include <cudaTypedefs.h>
 
 namespace lma {
 
@@ -44,57 +43,7 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
 }
 
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
-constexpr int kTmaStages = 4;
-static size_t tma_chol_smem() { return sizeof(tc::TmaSmem<kTmaStages>) + tc::kTcAlignSlack; }
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// dependency on the driver library); nullptr if unavailable.
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// One 2-D tensor map per window buffer (npad columns x rows rows, FP32,
-// 32 x 64 boxes with the 128-byte swizzle the MMA descriptors expect).
-static CUtensorMap* window_tensor_maps(const std::vector<Win>& wins, float* wbuf, Arena& tmp, cudaStream_t st) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return nullptr;
-  std::vector<CUtensorMap> maps(wins.size());
-  for (size_t m = 0; m < wins.size(); ++m) {
-    const Win& w = wins[m];
-    cuuint64_t gdim[2] = {(cuuint64_t)w.npad, (cuuint64_t)w.rows};
-    cuuint64_t gstride[1] = {(cuuint64_t)w.npad * sizeof(float)};
-    cuuint32_t box[2] = {32, 64};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, wbuf + w.base, gdim, gstride, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return nullptr;
-  }
-  CUtensorMap* d = tmp.alloc<CUtensorMap>(maps.size());
-  LMA_CK(cudaMemcpyAsync(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
-  return d;
-}
-
-// TMA-fed warp-specialised sweep update only when LMA_USE_TMA=1 (it measured
-// slower than the register-staged kernel on the configurations tried).
-static bool use_tma() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("LMA_USE_TMA");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
-}
+static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
@@ -127,17 +76,19 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
-    cudaFuncSetAttribute(k_chol_step_tma<kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tma_chol_smem());
+    cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
     done = true;
   }
 }
 
 // Left-looking sweep over all column panels.  batched: every window in
-// each launch; otherwise one window per launch (the plain form).
+// each launch; otherwise one window per launch (the plain form).  With the
+// tensor cores (tc_err != nullptr) the panels are grouped in super-panels of
+// 256 columns: one wide update applies all columns left of the super-panel
+// (N = 256 tiles), the 64-wide panel steps add the rest.
 template <typename T>
 void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* buf, T* dinv, int* info, bool batched,
-                int* tc_err, const CUtensorMap* maps) {
+                int* tc_err) {
   if (wins.empty()) return;
   if (batched) {
     int maxpan = 0, maxrt = 0;
@@ -148,28 +99,31 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
     const unsigned nw = (unsigned)wins.size();
     int maxrows = 0;
     for (const Win& w : wins) maxrows = std::max(maxrows, w.rows);
+    const bool tc = tc_err && sizeof(T) == 4;
+    constexpr int SP = 256;
     for (int kp = 0; kp < maxpan; ++kp) {
-      if (tc_err && sizeof(T) == 4 && maps) {
-        const unsigned gx = (unsigned)((maxrows - kp * TB + 127) / 128);
-        launch("k_chol_step_tma", k_chol_step_tma<kTmaStages>, dim3(gx, nw), 256, tma_chol_smem(), st, wins_d, maps,
-               (float*)buf, (float*)dinv, info, kp, tc_err);
-      } else if (tc_err && sizeof(T) == 4) {
-        const unsigned gx = (unsigned)((maxrows - kp * TB + 127) / 128);
-        launch("k_chol_step_tc", k_chol_step_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-               (float*)dinv, info, kp, tc_err);
-      } else {
-        launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,
-               info, kp);
-      }
-      if (tc_err && sizeof(T) == 4) {
+      const int k0 = kp * TB;
+      if (tc) {
+        const int kb = (k0 / SP) * SP;
+        if (k0 == kb && kb > 0) {
+          const unsigned gy = (unsigned)((maxrows - kb + 127) / 128);
+          launch("k_chol_wide", k_chol_wide, dim3(nw, gy), tc::kWsThreads, wide_smem(), st, wins_d, (float*)buf, kb,
+                 tc_err);
+        }
+        const unsigned gy = (unsigned)((maxrows - k0 + 127) / 128);
+        launch("k_chol_step_tc", k_chol_step_tc, dim3(nw, gy), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+               (float*)dinv, info, kp, kb, tc_err);
         if (maxrows - (kp + 1) * TB > 0) {
           const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
           launch("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
                  (const float*)dinv, kp, tc_err);
         }
-      } else if (maxrt - kp - 1 > 0) {
-        launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf, dinv, kp,
-               0);
+      } else {
+        launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,
+               info, kp);
+        if (maxrt - kp - 1 > 0)
+          launch("k_chol_trsm", k_chol_trsm<T>, dim3(maxrt - kp - 1, nw), NT, sizeof(TrsmSmem<T>), st, wins_d, buf,
+                 dinv, kp, 0);
       }
     }
   } else {
@@ -374,9 +328,7 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
       tc_err = tmp.alloc<int>(1);
       LMA_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
     }
-    const CUtensorMap* maps = nullptr;
-    if (tc_err && use_tma()) maps = window_tensor_maps(mc.wins, (float*)wbuf, tmp, st);
-    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err, maps);
+    chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err);
     if (tc_err) {
       int h = 0;
       LMA_CK(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -43,6 +43,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // ---- fences ----------------------------------------------------------------
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -358,18 +362,21 @@ __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA
 namespace lma {
 
 // Sweep update of column panel kp on the tensor cores (mixed form).  CTA
-// (x, window) owns rows [k0 + 128 x, k0 + 128 x + 128) of the window buffer:
-// T = A_{rows, panel} - A_{rows, 0:k0} A_{panel, 0:k0}^T with the product on
-// tcgen05 (3xTF32).  The diagonal 64x64 block (first rows of x = 0) is
-// factorised in shared memory; every other row keeps T for k_chol_trsm.
+// (window x, row tile y) owns rows [k0 + 128 y, k0 + 128 y + 128) of the
+// window buffer: T = A_{rows, panel} - A_{rows, kb:k0} A_{panel, kb:k0}^T with
+// the product on tcgen05 (3xTF32); columns [0, kb) were applied by the
+// super-panel update (kb = 0 without one).  The diagonal 64x64 block (first
+// rows of y = 0) is factorised in shared memory; every other row keeps T
+// for k_chol_trsm_tc.  Row tile 0 of every window comes first in launch
+// order, so the diagonal factorisations start in the first wave.
 __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
-                                                      int* __restrict__ err) {
+                                                      int kb, int* __restrict__ err) {
   using namespace tc;
-  const Win w = wins[blockIdx.y];
+  const Win w = wins[blockIdx.x];
   const int k0 = kp * TB;
   if (k0 >= w.npad) return;
-  const int r0 = k0 + blockIdx.x * 128;
+  const int r0 = k0 + blockIdx.y * 128;
   if (r0 >= w.rows) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   TcSmem<64>& sm = tc_smem<64>(smraw);
@@ -388,20 +395,21 @@ __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__
   const uint32_t tmem = sm.tmem;
   TcPipe pipe;
   bool ok = true;
-  if (k0 > 0) {
+  const int K = k0 - kb;
+  if (K > 0) {
     auto rowA = [&](int r) -> const float* {
       const int row = r0 + r;
-      return row < w.rows ? A + (int64_t)row * ld : nullptr;
+      return row < w.rows ? A + (int64_t)row * ld + kb : nullptr;
     };
-    auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld; };
-    ok = tile_product<64>(sm, pipe, tmem, k0, rowA, rowB);
+    auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld + kb; };
+    ok = tile_product<64>(sm, pipe, tmem, K, rowA, rowB);
   }
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int rl = q * 32 + lane;
   const int row = r0 + rl;
   float v[32];
-  if (k0 > 0 && ok) {
+  if (K > 0 && ok) {
     float t[16];
     tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32, t);
 #pragma unroll
@@ -416,12 +424,15 @@ __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__
   // all MMAs have completed (tile_product drained both stages): stage memory is free
   float* scratch = reinterpret_cast<float*>(&sm.st[0]);
   float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
-  const bool diag = (blockIdx.x == 0) && (rl < TB);
+  const bool diag = (blockIdx.y == 0) && (rl < TB);
   if (row < w.rows) {
     float* dst = A + (int64_t)row * ld + k0 + half * 32;
+    float4 av[8];  // all loads first: they are independent of the stores below
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(dst + 4 * j4);
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
-      float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
+      float4 a = av[j4];
       a.x -= v[4 * j4 + 0];
       a.y -= v[4 * j4 + 1];
       a.z -= v[4 * j4 + 2];
@@ -440,9 +451,224 @@ __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
-  if (blockIdx.x == 0)
-    diag_factor<float>(Dm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
+  if (blockIdx.y == 0)
+    diag_factor<float>(Dm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.x,
                        k0);
+}
+
+}  // namespace lma
+
+namespace lma {
+namespace tc {
+
+// Warp-specialised tile product over a 128 x BN output tile: kWsProducers
+// warps load 32-wide K chunks (two chunks ahead, in registers), split them
+// into TF32 hi/lo and store them into an NS-stage ring; one thread of the
+// last warp issues the MMAs of a stage as soon as its producers have
+// arrived on full[s] and frees the stage with tcgen05.commit on empty[s].
+// A kind::tf32 MMA instruction occupies the tensor pipe for the same time
+// whatever its N up to 256, so wide tiles (BN = 256) are the efficient ones.
+constexpr int kWsProducers = 8;
+constexpr int kWsThreads = 32 * (kWsProducers + 1);
+
+template <int NS, int BN>
+struct WsSmem {
+  TcStage<BN> st[NS];
+  uint64_t full[NS], empty[NS], done;
+  uint32_t tmem;
+  int abort;
+};
+
+template <int NS, int BN>
+__device__ __forceinline__ WsSmem<NS, BN>& ws_smem(unsigned char* raw) {
+  uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+  p = (p + 1023) & ~uintptr_t(1023);
+  return *reinterpret_cast<WsSmem<NS, BN>*>(p);
+}
+
+// Barrier set-up and tensor-memory allocation (BN columns, by the MMA warp).
+template <int NS, int BN>
+__device__ __forceinline__ void ws_setup(WsSmem<NS, BN>& sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&sm.full[s], kWsProducers);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(&sm.done, 1);
+    sm.abort = 0;
+    mbar_fence_init();
+  }
+  if ((tid >> 5) == kWsProducers) tmem_alloc(&sm.tmem, BN);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+
+template <int NS, int BN>
+__device__ __forceinline__ void ws_teardown(WsSmem<NS, BN>& sm) {
+  fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == kWsProducers) tmem_dealloc(sm.tmem, BN);
+}
+
+// D (tensor memory, 128 lanes x BN FP32 columns) = sum_{k<K} A(r,k) B(c,k)
+// (3xTF32), r < 128, c < BN, K % 32 == 0; rowA(r) / rowB(c) return a
+// 16-byte-aligned pointer to the K values of that row or nullptr for a zero
+// row.  Called by all kWsThreads threads; returns false (in every thread)
+// when a wait timed out.  On return every MMA has completed.
+template <int NS, int BN, class RA, class RB>
+__device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
+  constexpr int NA = 128 * 8 / 256, NB = BN * 8 / 256;  // float4 per producer thread per chunk
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nchunk = K / 32;
+  volatile int* abort_flag = &sm.abort;
+  if (warp < kWsProducers) {
+    float4 ra[2][NA], rb[2][NB];
+    auto load = [&](int c, float4 (&xa)[NA], float4 (&xb)[NB]) {
+      const int k0 = c * 32;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+        const float* src = rowA(row);
+        xa[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+        const float* src = rowB(row);
+        xb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    if (nchunk > 0) load(0, ra[0], rb[0]);
+    if (nchunk > 1) load(1, ra[1], rb[1]);
+    bool run = true;
+    for (int cb = 0; cb < nchunk && run; cb += 2) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const int c = cb + d;
+        if (c >= nchunk || !run) break;
+        const int s = c % NS, j = c / NS;
+        if (c >= NS) {  // the MMAs that last read stage s have completed
+          int okw = 1;
+          if (lane == 0) okw = mbar_wait(&sm.empty[s], (j - 1) & 1) ? 1 : 0;
+          okw = __shfl_sync(0xffffffffu, okw, 0);
+          if (!okw) *abort_flag = 1;
+        }
+        if (*abort_flag) {
+          run = false;
+          break;
+        }
+        TcStage<BN>& S = sm.st[s];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          const int i = tid + 256 * q;
+          store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[d][q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int i = tid + 256 * q;
+          store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[d][q]);
+        }
+        if (c + 2 < nchunk) load(c + 2, ra[d], rb[d]);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.full[s]);
+      }
+    }
+  } else if (lane == 0) {
+    const uint32_t idesc = idesc_tf32(128, BN);
+    const uint32_t tmem = sm.tmem;
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % NS, j = c / NS;
+      if (*abort_flag) break;
+      if (!mbar_wait(&sm.full[s], j & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after_sync();
+      TcStage<BN>& S = sm.st[s];
+      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t o = ks * 32;
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+      }
+      mma_commit(&sm.empty[s]);
+    }
+    mma_commit(&sm.done);  // arrives once every MMA issued above has completed
+  }
+  const bool w = mbar_wait(&sm.done, 0);
+  const bool ok = __syncthreads_and(w && !*abort_flag) != 0;
+  fence_after_sync();
+  return ok;
+}
+
+}  // namespace tc
+
+// Super-panel update of the left-looking sweep (mixed form): for the 256
+// columns [s0, s0 + 256) of every window (clipped to its order), every row
+// r >= s0 gets A_{r,c} -= sum_{k < s0} L_{r,k} L_{c,k}, the contribution of
+// all columns left of the super-panel, as one 128 x 256 tensor-core tile per
+// CTA (grid: x = window, y = 128-row tile).  Only the lower triangle
+// (c <= r) is written.  The 64-wide panel steps inside the super-panel then
+// only add the contributions of columns [s0, k0).
+__global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __restrict__ wins,
+                                                                float* __restrict__ buf, int s0,
+                                                                int* __restrict__ err) {
+  using namespace tc;
+  const Win w = wins[blockIdx.x];
+  if (s0 >= w.npad) return;
+  const int r0 = s0 + blockIdx.y * 128;
+  if (r0 >= w.rows) return;
+  const int ncol = min(256, w.npad - s0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  WsSmem<2, 256>& sm = ws_smem<2, 256>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* A = buf + w.base;
+  const int64_t ld = w.npad;
+  ws_setup(sm);
+  auto rowA = [&](int r) -> const float* {
+    const int row = r0 + r;
+    return row < w.rows ? A + (int64_t)row * ld : nullptr;
+  };
+  auto rowB = [&](int c) -> const float* { return c < ncol ? A + (int64_t)(s0 + c) * ld : nullptr; };
+  const bool ok = ws_product(sm, s0, rowA, rowB);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  if (ok && warp < kWsProducers) {
+    const int q = warp & 3, half = warp >> 2;
+    const int row = r0 + q * 32 + lane;
+    float* dst = A + (int64_t)row * ld + s0;
+    for (int g = 0; g < 8; ++g) {
+      const int c0 = half * 128 + 16 * g;
+      if (c0 >= ncol) break;  // warp-uniform
+      float t[16];
+      tmem_ld16(sm.tmem + ((uint32_t)(q * 32) << 16) + c0, t);
+      if (row < w.rows) {
+        float4 a[4];
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) a[j4] = *reinterpret_cast<const float4*>(dst + c0 + 4 * j4);
+        if (s0 + c0 + 15 <= row) {
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4) {
+            a[j4].x -= t[4 * j4];
+            a[j4].y -= t[4 * j4 + 1];
+            a[j4].z -= t[4 * j4 + 2];
+            a[j4].w -= t[4 * j4 + 3];
+            *reinterpret_cast<float4*>(dst + c0 + 4 * j4) = a[j4];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (s0 + c0 + j <= row) dst[c0 + j] = reinterpret_cast<float*>(a)[j] - t[j];
+        }
+      }
+    }
+  }
+  ws_teardown(sm);
 }
 
 }  // namespace lma
@@ -857,212 +1083,6 @@ __global__ void __launch_bounds__(256, 2) k_pred_rhs_tc(const Pair* __restrict__
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
   tc_teardown(sm, 128);
-}
-
-}  // namespace lma
-
-#include <cuda.h>
-
-namespace lma {
-namespace tc {
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// 2-D tiled TMA load of box (x = column, y = row) into shared memory,
-// completion signalled on *bar (complete_tx)
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Ring of shared-memory stages for a 128 x 64 tile product over 32 values of
-// K: raw FP32 tiles land by TMA in a/b and are rounded there to TF32 (hi),
-// the remainders go to a_lo/b_lo.
-struct alignas(1024) TmaStage {
-  float a[128 * 32];
-  float a_lo[128 * 32];
-  float b[64 * 32];
-  float b_lo[64 * 32];
-};
-template <int ST>
-struct TmaSmem {
-  TmaStage st[ST];
-  uint64_t full[ST], conv[ST], empty[ST];
-  uint64_t done;
-  uint32_t tmem;
-  int abort;
-};
-
-}  // namespace tc
-
-// Sweep update of column panel kp (mixed form) with a TMA-fed, warp-
-// specialised tensor-core pipeline.  Warp 0 (one lane) loads 32-column slices
-// of the row tile (128 rows) and of the panel rows (64) through the window's
-// tensor map into an ST-stage ring; warps 2-7 split each slice into TF32
-// hi/lo; warp 1 (one lane) issues the three MMAs per 8-wide K step and frees
-// the stage with tcgen05.commit.  The epilogue (T = A - D, diagonal
-// factorisation) is that of k_chol_step_tc.
-template <int ST>
-__global__ void __launch_bounds__(256) k_chol_step_tma(const Win* __restrict__ wins,
-                                                       const CUtensorMap* __restrict__ maps, float* __restrict__ buf,
-                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
-                                                       int* __restrict__ err) {
-  using namespace tc;
-  const Win w = wins[blockIdx.y];
-  const int k0 = kp * TB;
-  if (k0 >= w.npad) return;
-  const int r0 = k0 + blockIdx.x * 128;
-  if (r0 >= w.rows) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  uintptr_t pbase = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023);
-  TmaSmem<ST>& sm = *reinterpret_cast<TmaSmem<ST>*>(pbase);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const CUtensorMap* map = maps + blockIdx.y;
-  float* A = buf + w.base;
-  const int64_t ld = w.npad;
-  if (tid == 0) {
-    for (int s = 0; s < ST; ++s) {
-      mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.conv[s], 6);
-      mbar_init(&sm.empty[s], 1);
-    }
-    mbar_init(&sm.done, 1);
-    sm.abort = 0;
-    mbar_fence_init();
-  }
-  if (warp == 1) tmem_alloc(&sm.tmem, 64);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = sm.tmem;
-  const int nchunk = k0 / 32;
-  bool ok = true;
-  if (nchunk > 0) {
-    if (warp == 0) {
-      if (lane == 0) {
-        for (int c = 0; c < nchunk; ++c) {
-          const int s = c % ST, j = c / ST;
-          if (*(volatile int*)&sm.abort) break;
-          if (c >= ST && !mbar_wait(&sm.empty[s], (j - 1) & 1)) {
-            sm.abort = 1;
-            break;
-          }
-          mbar_arrive_expect_tx(&sm.full[s], (128 + 64) * 32 * 4);
-          tma_load_2d(sm.st[s].a, map, c * 32, r0, &sm.full[s]);
-          tma_load_2d(sm.st[s].a + 64 * 32, map, c * 32, r0 + 64, &sm.full[s]);
-          tma_load_2d(sm.st[s].b, map, c * 32, k0, &sm.full[s]);
-        }
-      }
-    } else if (warp == 1) {
-      if (lane == 0) {
-        const uint32_t idesc = idesc_tf32(128, 64);
-        for (int c = 0; c < nchunk; ++c) {
-          const int s = c % ST, j = c / ST;
-          if (*(volatile int*)&sm.abort) break;
-          if (!mbar_wait(&sm.conv[s], j & 1)) {
-            sm.abort = 1;
-            break;
-          }
-          fence_after_sync();
-          TmaStage& S = sm.st[s];
-          const uint32_t ah = smem_addr(S.a), al = smem_addr(S.a_lo);
-          const uint32_t bh = smem_addr(S.b), bl = smem_addr(S.b_lo);
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-            mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
-          }
-          mma_commit(&sm.empty[s]);
-        }
-        mma_commit(&sm.done);
-      }
-    } else {
-      const int ct = tid - 64;  // 192 converter threads
-      for (int c = 0; c < nchunk; ++c) {
-        const int s = c % ST, j = c / ST;
-        if (*(volatile int*)&sm.abort) break;
-        if (!mbar_wait(&sm.full[s], j & 1)) {
-          sm.abort = 1;
-          break;
-        }
-        TmaStage& S = sm.st[s];
-        for (int i = ct; i < (128 + 64) * 8; i += 192) {
-          float4* hp = (i < 128 * 8) ? reinterpret_cast<float4*>(S.a) + i : reinterpret_cast<float4*>(S.b) + (i - 1024);
-          float4* lp =
-              (i < 128 * 8) ? reinterpret_cast<float4*>(S.a_lo) + i : reinterpret_cast<float4*>(S.b_lo) + (i - 1024);
-          float4 v = *hp, h, l;
-          h.x = tf32_round(v.x); l.x = v.x - h.x;
-          h.y = tf32_round(v.y); l.y = v.y - h.y;
-          h.z = tf32_round(v.z); l.z = v.z - h.z;
-          h.w = tf32_round(v.w); l.w = v.w - h.w;
-          *hp = h;
-          *lp = l;
-        }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.conv[s]);
-      }
-    }
-    // everybody waits for the last MMA (bounded), then agrees on the outcome
-    const bool w_ok = mbar_wait(&sm.done, 0);
-    ok = __syncthreads_and(w_ok && !sm.abort) != 0;
-  }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  fence_after_sync();
-  const int q = warp & 3, half = warp >> 2;
-  const int rl = q * 32 + lane;
-  const int row = r0 + rl;
-  float v[32];
-  if (nchunk > 0 && ok) {
-    float t[16];
-    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32, t);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = t[j];
-    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32 + 16, t);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
-  } else {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = 0.f;
-  }
-  float* scratch = reinterpret_cast<float*>(&sm.st[0]);
-  float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
-  const bool diag = (blockIdx.x == 0) && (rl < TB);
-  if (row < w.rows) {
-    float* dst = A + (int64_t)row * ld + k0 + half * 32;
-#pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
-      float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
-      a.x -= v[4 * j4 + 0];
-      a.y -= v[4 * j4 + 1];
-      a.z -= v[4 * j4 + 2];
-      a.w -= v[4 * j4 + 3];
-      if (diag) {
-        float* dd = &Dm[rl][half * 32 + 4 * j4];
-        dd[0] = a.x;
-        dd[1] = a.y;
-        dd[2] = a.z;
-        dd[3] = a.w;
-      } else {
-        *reinterpret_cast<float4*>(dst + 4 * j4) = a;
-      }
-    }
-  }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, 64);
-  if (blockIdx.x == 0)
-    diag_factor<float>(Dm, A + (int64_t)k0 * ld + k0, ld, dinv + w.dinv + (int64_t)kp * TB * TB, info + blockIdx.y,
-                       k0);
 }
 
 }  // namespace lma
