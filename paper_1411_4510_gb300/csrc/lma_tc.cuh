@@ -215,17 +215,20 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const float* __restrict__ A, in
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (tid == 0) {
-      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+    if (tid < 32) {
+      if (tid == 0) {
+        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t o = ks * 32;
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+          mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        }
+        mma_commit(&sm.bar[s]);
       }
-      mma_commit(&sm.bar[s]);
+      __syncwarp();  // lanes 1-31 wait here, so no divergent wait stalls the issuing lane
     }
   }
   if (ok && nchunk > 0) {
@@ -329,22 +332,25 @@ __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA
       fence_before_sync();
       __syncthreads();
       fence_after_sync();
-      if (tid == 0) {
-        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-        // split-K: chunk c accumulates into accumulator c mod nacc (columns
-        // [BN a, BN a + BN)); accumulators 0 .. min(nacc, nchunk) - 1 are written
-        const int a = c % nacc;
-        const bool first = c < nacc;
-        const uint32_t dd = tmem + (uint32_t)(BN * a);
+      if (tid < 32) {
+        if (tid == 0) {
+          const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+          const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+          // split-K: chunk c accumulates into accumulator c mod nacc (columns
+          // [BN a, BN a + BN)); accumulators 0 .. min(nacc, nchunk) - 1 are written
+          const int a = c % nacc;
+          const bool first = c < nacc;
+          const uint32_t dd = tmem + (uint32_t)(BN * a);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t o = ks * 32;
-          mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (!first || ks > 0) ? 1u : 0u);
-          mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-          mma_tf32(dd, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (!first || ks > 0) ? 1u : 0u);
+            mma_tf32(dd, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+            mma_tf32(dd, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+          }
+          mma_commit(&sm.bar[s]);
         }
-        mma_commit(&sm.bar[s]);
+        __syncwarp();  // lanes 1-31 wait here, so no divergent wait stalls the issuing lane
       }
       p.cnt[s] += 1;
       p.pending[s] = true;
@@ -576,30 +582,39 @@ __device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
         if (lane == 0) mbar_arrive(&sm.full[s]);
       }
     }
-  } else if (lane == 0) {
+  } else {
+    // the whole MMA warp runs this loop (a lane spinning on a barrier on a
+    // divergent path would hold up the issuing lane); lane 0 issues
     const uint32_t idesc = idesc_tf32(128, BN);
     const uint32_t tmem = sm.tmem;
     for (int c = 0; c < nchunk; ++c) {
       const int s = c % NS, j = c / NS;
       if (*abort_flag) break;
-      if (!mbar_wait(&sm.full[s], j & 1)) {
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&sm.full[s], j & 1) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
         *abort_flag = 1;
         break;
       }
       fence_after_sync();
-      TcStage<BN>& S = sm.st[s];
-      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+      if (lane == 0) {
+        TcStage<BN>& S = sm.st[s];
+        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t o = ks * 32;
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-        mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+          mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        }
+        mma_commit(&sm.empty[s]);
       }
-      mma_commit(&sm.empty[s]);
+      __syncwarp();
     }
-    mma_commit(&sm.done);  // arrives once every MMA issued above has completed
+    if (lane == 0) mma_commit(&sm.done);  // arrives once every MMA issued above has completed
+    __syncwarp();
   }
   const bool w = mbar_wait(&sm.done, 0);
   const bool ok = __syncthreads_and(w && !*abort_flag) != 0;
@@ -907,18 +922,21 @@ __device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, 
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (tid == 0) {
-      const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-      const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-      const uint32_t dcol = tmem + 64 * s;
+    if (tid < 32) {
+      if (tid == 0) {
+        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+        const uint32_t dcol = tmem + 64 * s;
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t o = ks * 32;
-        mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
-        mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-        mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
+          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+          mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        }
+        mma_commit(&sm.bar[s]);
       }
-      mma_commit(&sm.bar[s]);
+      __syncwarp();  // lanes 1-31 wait here, so no divergent wait stalls the issuing lane
     }
     p.cnt[s] += 1;
     p.pending[s] = true;
