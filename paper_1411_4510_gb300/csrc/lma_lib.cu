@@ -141,7 +141,7 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
   }
 }
 
-// Right-looking factorisation of one FP64 matrix on 32 x 32 tiles (see
+// Right-looking factorisation of one FP64 matrix on 16 x 16 tiles (see
 // lma_f64.cuh).  nid: number of leading appended rows that are identity rows
 // (0 = none).  wd is unused (kept for the window form's signature).
 static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info,
@@ -151,13 +151,13 @@ static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* b
   const int npan = w.npad / TS, nrt = (w.rows + TS - 1) / TS;
   const int64_t ld = w.npad;
   launch("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
-  for (int kp = 0; kp < npan; ++kp) {
-    if (nrt - kp - 1 > 0)
-      launch("k_f64_trsm", k_f64_trsm, (unsigned)(nrt - kp - 1), NTH, 0, st, buf, ld, w.rows, npan, kp, nid,
-             (const double*)dv);
+  for (int kp = 0; kp <= npan; ++kp) {
     const int m = npan - kp - 1;
-    const int tiles = m * (m + 1) / 2 + (nrt - npan) * m;
-    if (m > 0) launch("k_f64_trail", k_f64_trail, (unsigned)tiles, NTH, 0, st, buf, ld, w.rows, npan, kp, nid, dv, info);
+    const int trail = m > 0 ? m * (m + 1) / 2 + (nrt - npan) * m : 0;
+    const int solve = kp >= 1 ? nrt - kp : 0;
+    if (trail + solve > 0)
+      launch("k_f64_panel", k_f64_panel, (unsigned)(trail + solve), NTH, 0, st, buf, ld, w.rows, npan, kp, nid, dv,
+             info);
   }
 }
 
