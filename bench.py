@@ -210,17 +210,23 @@ def run_reference(args, p):
     out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": workload_config(p, args.B),
+           "data": "synthetic", "config": workload_config(p, args.B, world),
            "cpu_baseline": dict(last, value=value),
            "e2e": {"value": value, "unit": "train-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def workload_config(p, B):
-    return {"workload": f"C2: N={p.N} d={p.d} |S|={p.s} M={p.M} blocks of {p.N // p.M} (k-means order) "
-                        f"B={B} U={p.U} (RFF SE draw, synthetic)",
-            "N": p.N, "d": p.d, "s": p.s, "M": p.M, "B": B, "U": p.U,
-            "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+def workload_config(p, B, world=1):
+    c = {"workload": f"C2: N={p.N} d={p.d} |S|={p.s} M={p.M} blocks of {p.N // p.M} (k-means order) "
+                     f"B={B} U={p.U} (RFF SE draw, synthetic)",
+         "N": p.N, "d": p.d, "s": p.s, "M": p.M, "B": B, "U": p.U,
+         "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+    if world > 1:
+        c["workload"] = (f"{world} draws of C2 joined (N={p.N}, M={p.M}, |S|={p.s}, B={B}, U={p.U}); rank r owns "
+                         f"draw r's blocks plus B-block halos; local summaries, one all-reduce of the "
+                         f"(|S|+1)^2 FP64 summary Gram, global step on every rank")
+        c["parallelism"] = f"block-sharded x{world}"
+    return c
 
 
 # ----------------------------------------------------------------------------
@@ -238,47 +244,61 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "lma" else args.warmup
 
-    from workloads import make_problem
-    p = make_problem("C2", B=args.B)
+    from workloads import make_problem, make_replicated
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # one C2 problem per GPU: N = 1 runs C2 itself; N > 1 runs N draws of C2
+    # joined into one problem, each rank owning one draw's blocks (weak scaling)
+    p = make_problem("C2", B=args.B) if world == 1 else make_replicated("C2", world, B=args.B)
     if args.impl == "reference":
-        run_reference(args, p)
+        run_reference(args, make_problem("C2", B=args.B))
         return
 
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1411_4510_gb300 import build
     build.build()
     import paper_1411_4510_gb300 as L
+    from paper_1411_4510_gb300 import api, shard
 
     dev = torch.device("cuda", local)
-    X = torch.as_tensor(p.X, device=dev)
-    y = torch.as_tensor(p.y, device=dev)
-    S = torch.as_tensor(p.S, device=dev)
-    XU = torch.as_tensor(p.XU, device=dev)
-    kw = dict(block_ptr=p.block_ptr, B=args.B, log_ell=p.log_ell, log_sigma_s=p.log_sigma_s,
-              log_sigma_n=p.log_sigma_n, jitter=p.jitter, mean=p.mean)
+    full = L.problem_args(p, B=args.B)
+    if world == 1:
+        sh, sub, u0, u1, tptr = None, full, 0, p.U, p.test_block_ptr
+    else:
+        sh = shard.plan(p.block_ptr, args.B, world, rank)
+        sub = shard.sub_problem(full, sh)
+        u0, u1, tptr = shard.test_rows(p.test_block_ptr, sh)
+    hostsrc = dict(X=sub["X"], y=sub["y"], S=sub["S"], XU=p.XU[u0:u1])
+    dsrc = {k: torch.as_tensor(v, device=dev) for k, v in hostsrc.items()}
+    kw = {k: v for k, v in sub.items() if k not in ("X", "y", "S")}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
     def step(prec=L.MIXED, host=None):
-        if host is None:
-            m = L.lma_fit(X, y, S=S, precision=prec, **kw)
-            return m, L.lma_predict(m, XU, p.test_block_ptr)
-        m = L.lma_fit(host["X"], host["y"], S=host["S"], precision=prec, **kw)
-        return m, L.lma_predict(m, host["XU"], p.test_block_ptr)
+        src = dsrc if host is None else host
+        if sh is None:
+            m = L.lma_fit(src["X"], src["y"], S=src["S"], precision=prec, **kw)
+        else:  # local summaries, one all-reduce of the summary Gram, global step
+            m = api.lma_fit_local(src["X"], src["y"], S=src["S"], win_begin=0, own_begin=sh.own_begin,
+                                  own_end=sh.own_end, precision=prec, **kw)
+            G, ld = api.lma_model_local_summary(m, device=dev)
+            G, ld = shard.allreduce_sum(G, ld)
+            api.lma_model_set_global(m, G, ld, p.N)
+        return m, L.lma_predict(m, src["XU"], tptr)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     work = kernel_work(p, args.B)
+    if world > 1:  # equal shards: each rank does one draw's share
+        work = {k: v / world for k, v in work.items()}
 
     def timed(nsteps, prec=L.MIXED, host=None, profile=None):
         evs = []
@@ -319,19 +339,25 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
     fit_f, pred_f = fit_flops(p, args.B), predict_flops(p, args.B)
-    value = world * p.N / (step_ms / 1e3)
+    value = p.N / (step_ms / 1e3)
     mean_mixed = mean.cpu().numpy()
 
     # end to end through the C ABI with pinned host buffers (copies inside)
-    host = {k: torch.as_tensor(v).pin_memory() for k, v in dict(X=p.X, y=p.y, S=p.S, XU=p.XU).items()}
+    host = {k: torch.as_tensor(v).pin_memory() for k, v in hostsrc.items()}
     ems, _, _, _ = timed(max(3, args.steps // 2), host=host)
-    h2d = 8 * (p.N * p.d + p.N + p.s * p.d + p.U * p.d) + 8 * (p.M + 1) * 2
-    e2e = {"value": world * p.N / (statistics.mean(ems) / 1e3), "unit": "train-points/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * p.U}
+    e2e_ms = statistics.mean(ems)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nsub, Msub = len(hostsrc["y"]), len(kw["block_ptr"]) - 1
+    h2d = 8 * (nsub * p.d + nsub + p.s * p.d + (u1 - u0) * p.d) + 8 * (Msub + 1) * 2
+    e2e = {"value": p.N / (e2e_ms / 1e3), "unit": "train-points/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * (u1 - u0)}
 
     # plain FP64 GPU form (per-window launches) and the mixed form's error against it
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and world == 1:
         step(L.FP64)
         fms, _, _, (_, (m64, v64)) = timed(2, prec=L.FP64)
         m64 = m64.cpu().numpy()
@@ -369,12 +395,12 @@ def main():
                     "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived, not measured)"}
         roof["work_per_step_gflop"] = work[dominant] / 1e9
     cpu = None
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and rank == 0 and world == 1:
         cpu, _ = cpu_baseline(p, args.B)
     out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic", "config": workload_config(p, args.B),
+           "data": "synthetic", "config": workload_config(p, args.B, world),
            "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
            "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,

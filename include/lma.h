@@ -137,6 +137,41 @@ lma_status lma_loglik_grad(const lma_problem* problem, const lma_hyper* hyper,
 lma_status lma_model_summary(const lma_model* model, double* A_out, double* y_out,
                              double* scalars_out);
 
+/* Partitioned fit (Remark 1: machines compute the local summaries of their
+ * own blocks, Definition 1, and a master sums them into the global summary,
+ * Definition 2).  Three calls per shard:
+ *
+ * lma_fit_local: windows D_m u D^B_m of blocks [win_begin, own_end) of
+ *   `problem` are formed and factorised, and the local summaries of blocks
+ *   [own_begin, own_end) are summed.  `problem` is normally a sub-problem
+ *   holding the shard's blocks plus the B blocks after them (the blankets of
+ *   its last blocks) and, for prediction, the B blocks before them (win_begin
+ *   = own_begin - B, so that every window a test block of the shard needs is
+ *   present).  0 <= win_begin <= own_begin < own_end <= m_blocks.  The model
+ *   cannot predict or report a log-likelihood before lma_model_set_global.
+ *
+ * lma_model_local_summary: the shard's (s+1) x (s+1) FP64 Gram G, row-major,
+ *   G[0][0] = sum y-dot_m^T R-dot_m y-dot_m, G[0][1+i] = G[1+i][0] =
+ *   (L_SS^-1 y-ddot)_i, G[1+i][1+j] = A_ij (whitened, as in
+ *   lma_model_summary), into G_out (device memory if on_device, else host),
+ *   and the shard's sum of log|R-dot_m^-1| into *logdet_out (host).  The sum
+ *   over shards of both is the whole fit's.
+ *
+ * lma_model_set_global: given the summed G (device or host) and log-det sum,
+ *   and the total number of training points n_total, performs the global
+ *   step (Definition 2, Eq. pitck) on this shard's model; afterwards
+ *   lma_predict works for test blocks whose windows m in [n - B, n] lie in
+ *   [win_begin, own_end), and lma_model_loglik returns the whole problem's
+ *   log-likelihood.  Errors: LMA_ERR_INVALID_ARG for bad ranges or sizes,
+ *   LMA_ERR_NOT_PD as in lma_fit.                                           */
+lma_status lma_fit_local(const lma_problem* problem, const lma_hyper* hyper,
+                         const lma_options* options, int64_t win_begin, int64_t own_begin,
+                         int64_t own_end, lma_model** out);
+lma_status lma_model_local_summary(const lma_model* model, double* G_out, double* logdet_out,
+                                   int on_device);
+lma_status lma_model_set_global(lma_model* model, const double* G, double logdet_R,
+                                int64_t n_total, int on_device);
+
 /* The residual R = Sigma - Q over the window D_m u D^B_m of block m, as an
  * n_w x n_w matrix in natural row order (host memory, n_w = number of rows
  * of D_m u D^B_m), evaluated by the selected precision's kernels before any

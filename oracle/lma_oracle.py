@@ -106,6 +106,59 @@ class _Cov:
         return out + self.sn2 * same
 
 
+def _local_terms(cv: _Cov, r, m: int, B: int):
+    """Definition 1 for block m (whitened support coordinates): the rows I of
+    D_m and Bk of D^B_m, R' = R_{D_m D^B_m} R_{D^B_m D^B_m}^-1, y-dot_m,
+    R-dot_m^-1, Sigma-dot^m_S L^-T and the Cholesky factor of R-dot_m^-1."""
+    prob = cv.p
+    ptr = prob.block_ptr
+    M = len(ptr) - 1
+    I = _rows(ptr, m)
+    last = min(m + B, M - 1)
+    Bk = np.arange(ptr[m + 1], ptr[last + 1]) if last > m else np.zeros(0, dtype=np.int64)
+    R_II = cv.R_train(I, I)
+    W_I = cv.W(prob.X[I]).T                                             # Sigma_{D_m S} L^-T
+    if Bk.size:
+        R_IB = cv.R_train(I, Bk)
+        R_BB = cv.R_train(Bk, Bk)
+        Rp = sla.cho_solve(sla.cho_factor(R_BB, lower=True), R_IB.T).T      # R' = R_IB R_BB^-1
+        ydot = r[I] - Rp @ r[Bk]
+        Rdot_inv = R_II - Rp @ R_IB.T
+        Sdot = W_I - Rp @ cv.W(prob.X[Bk]).T
+    else:
+        Rp = np.zeros((I.size, 0))
+        ydot = r[I].copy()
+        Rdot_inv = R_II
+        Sdot = W_I
+    cf = sla.cho_factor(Rdot_inv, lower=True)
+    return I, Bk, Rp, ydot, Rdot_inv, Sdot, cf
+
+
+def local_summaries(prob, blocks, B: int | None = None):
+    """Sums of the local summaries (Definition 1) over the given blocks, in the
+    whitened support coordinates: (A, y-ddot, quad, log|R-bar|) with
+    A = sum Sigma-dot^T R-dot Sigma-dot, y-ddot = sum Sigma-dot^T R-dot y-dot,
+    quad = sum y-dot^T R-dot y-dot and the sum of log|R-dot_m^-1|.  Over all
+    blocks these are the global sums of Definition 2; over a machine's own
+    blocks they are what that machine contributes (Remark 1)."""
+    B = prob.B if B is None else int(B)
+    cv = _Cov(prob)
+    s = prob.S.shape[0]
+    r = prob.y - prob.mean
+    ydd = np.zeros(s)
+    A = np.zeros((s, s))
+    quad = 0.0
+    logdet_R = 0.0
+    for m in blocks:
+        _, _, _, ydot, _, Sdot, cf = _local_terms(cv, r, m, B)
+        t = sla.cho_solve(cf, np.column_stack([ydot, Sdot]))                 # R-dot [y-dot, Sigma-dot]
+        ydd += Sdot.T @ t[:, 0]
+        A += Sdot.T @ t[:, 1:]
+        quad += float(ydot @ t[:, 0])
+        logdet_R += _logdet_chol(np.tril(cf[0]))
+    return A, ydd, quad, logdet_R
+
+
 def fit(prob, B: int | None = None, keep_blocks: bool = False) -> LMAFit:
     """Definition 1 per block, Definition 2 sums, alpha, summary-form loglik.
 
@@ -129,24 +182,7 @@ def fit(prob, B: int | None = None, keep_blocks: bool = False) -> LMAFit:
     logdet_R = 0.0
     blocks = []
     for m in range(M):
-        I = _rows(ptr, m)
-        last = min(m + B, M - 1)
-        Bk = np.arange(ptr[m + 1], ptr[last + 1]) if last > m else np.zeros(0, dtype=np.int64)
-        R_II = cv.R_train(I, I)
-        W_I = cv.W(prob.X[I]).T                                             # Sigma_{D_m S} L^-T
-        if Bk.size:
-            R_IB = cv.R_train(I, Bk)
-            R_BB = cv.R_train(Bk, Bk)
-            Rp = sla.cho_solve(sla.cho_factor(R_BB, lower=True), R_IB.T).T      # R' = R_IB R_BB^-1
-            ydot = r[I] - Rp @ r[Bk]
-            Rdot_inv = R_II - Rp @ R_IB.T
-            Sdot = W_I - Rp @ cv.W(prob.X[Bk]).T
-        else:
-            Rp = np.zeros((I.size, 0))
-            ydot = r[I].copy()
-            Rdot_inv = R_II
-            Sdot = W_I
-        cf = sla.cho_factor(Rdot_inv, lower=True)
+        I, Bk, Rp, ydot, Rdot_inv, Sdot, cf = _local_terms(cv, r, m, B)
         t = sla.cho_solve(cf, np.column_stack([ydot, Sdot]))                 # R-dot [y-dot, Sigma-dot]
         ydd += Sdot.T @ t[:, 0]
         A += Sdot.T @ t[:, 1:]

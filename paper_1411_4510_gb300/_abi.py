@@ -14,7 +14,7 @@ EXPORTED = (
     "lma_fit", "lma_predict", "lma_model_loglik", "lma_loglik", "lma_loglik_grad", "lma_model_summary",
     "lma_window_residual", "lma_window_rows", "lma_model_free", "lma_status_string", "lma_last_error_info",
     "lma_kernel_launch_count", "lma_profile_start", "lma_profile_stop", "lma_tc_gemm_check",
-    "lma_global_step_noalloc",
+    "lma_global_step_noalloc", "lma_fit_local", "lma_model_local_summary", "lma_model_set_global",
 )
 
 
@@ -85,6 +85,12 @@ def load(path: str | None = None):
     lib.lma_tc_gemm_check.restype = C.c_int
     lib.lma_global_step_noalloc.argtypes = [C.c_int64, C.c_int64, vp, vp, C.c_double, C.c_double, vp, vp, vp]
     lib.lma_global_step_noalloc.restype = C.c_int
+    lib.lma_fit_local.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, C.c_int64, C.POINTER(vp)]
+    lib.lma_fit_local.restype = C.c_int
+    lib.lma_model_local_summary.argtypes = [vp, vp, C.POINTER(C.c_double), C.c_int]
+    lib.lma_model_local_summary.restype = C.c_int
+    lib.lma_model_set_global.argtypes = [vp, vp, C.c_double, C.c_int64, C.c_int]
+    lib.lma_model_set_global.restype = C.c_int
     lib.lma_profile_start.argtypes = [C.c_char_p]
     lib.lma_profile_start.restype = None
     lib.lma_profile_stop.argtypes = [C.c_char_p, C.c_int, vp, vp, C.c_int]

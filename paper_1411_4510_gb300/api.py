@@ -135,6 +135,42 @@ def lma_model_summary(model: Model):
     return dict(A=A, y=yv, quad=sc[0], logdet_R=sc[1], logdet_C=sc[2], loglik=sc[3])
 
 
+def lma_fit_local(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, win_begin, own_begin, own_end,
+                  jitter=1e-6, mean=0.0, precision=MIXED, stream=None) -> Model:
+    """Shard part of a partitioned fit (windows of blocks [win_begin, own_end),
+    local summaries of blocks [own_begin, own_end)); see lma_model_set_global."""
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    h = C.c_void_p()
+    _abi.check(lib.lma_fit_local(C.byref(prob), C.byref(hyp), C.byref(opt), int(win_begin), int(own_begin),
+                                 int(own_end), C.byref(h)))
+    return Model(h.value, prob.m_blocks, prob.s)
+
+
+def lma_model_local_summary(model: Model, device=None):
+    """(G, logdet): the shard's (s+1) x (s+1) Gram of local summaries and its
+    log-determinant sum.  G is a CUDA tensor on `device` if given, else numpy."""
+    lib = _abi.load()
+    se = model.s + 1
+    ld = C.c_double()
+    if device is not None:
+        G = torch.empty((se, se), dtype=torch.float64, device=device)
+        _abi.check(lib.lma_model_local_summary(model.handle, G.data_ptr(), C.byref(ld), 1))
+    else:
+        G = np.empty((se, se))
+        _abi.check(lib.lma_model_local_summary(model.handle, G.ctypes.data, C.byref(ld), 0))
+    return G, ld.value
+
+
+def lma_model_set_global(model: Model, G, logdet_R: float, n_total: int) -> None:
+    """Global step of a partitioned fit from the summed Gram and log-det sum."""
+    keep = []
+    gp, dev = _f64(G, keep)
+    _abi.check(_abi.load().lma_model_set_global(model.handle, gp, float(logdet_R), int(n_total), int(dev)))
+
+
 def lma_loglik(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter=1e-6, mean=0.0,
                precision=MIXED, stream=None) -> float:
     lib = _abi.load()

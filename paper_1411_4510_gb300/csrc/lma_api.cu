@@ -152,16 +152,78 @@ lma_status lma_fit(const lma_problem* P, const lma_hyper* H, const lma_options* 
   return LMA_OK;
 }
 
+lma_status lma_fit_local(const lma_problem* P, const lma_hyper* H, const lma_options* O, int64_t win_begin,
+                         int64_t own_begin, int64_t own_end, lma_model** out) {
+  if (!out) return fail(LMA_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  lma_status cs = check_problem(P, H, O);
+  if (cs != LMA_OK) return cs;
+  if (win_begin < 0 || win_begin > own_begin || own_begin >= own_end || own_end > P->m_blocks)
+    return fail(LMA_ERR_INVALID_ARG, "need 0 <= win_begin <= own_begin < own_end <= m_blocks");
+  lma_model* md = new (std::nothrow) lma_model();
+  if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+  md->core.prec = O->precision;
+  md->core.st = (cudaStream_t)O->cuda_stream;
+  md->core.keep.st = md->core.st;
+  lma_status st = guarded([&] {
+    if (O->precision == LMA_MIXED)
+      Impl<float>::fit_local(md->core, P, H, win_begin, own_begin, own_end);
+    else
+      Impl<double>::fit_local(md->core, P, H, win_begin, own_begin, own_end);
+  });
+  if (st != LMA_OK) {
+    md->core.keep.release();
+    cudaStreamSynchronize(md->core.st);
+    delete md;
+    return st;
+  }
+  *out = md;
+  return LMA_OK;
+}
+
+lma_status lma_model_local_summary(const lma_model* md, double* G_out, double* logdet_out, int on_device) {
+  if (!md || !G_out || !logdet_out) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  const ModelCore& mc = md->core;
+  return guarded([&] {
+    const int64_t se = mc.s + 1;
+    LMA_CK(cudaMemcpyAsync(G_out, mc.G, sizeof(double) * se * se,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, mc.st));
+    LMA_CK(cudaStreamSynchronize(mc.st));
+    *logdet_out = mc.logdetR;
+  });
+}
+
+lma_status lma_model_set_global(lma_model* md, const double* G, double logdet_R, int64_t n_total, int on_device) {
+  if (!md || !G) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  if (n_total < md->core.n || !isfinite(logdet_R)) return fail(LMA_ERR_INVALID_ARG, "bad n_total or logdet_R");
+  ModelCore& mc = md->core;
+  return guarded([&] {
+    const int64_t se = mc.s + 1;
+    LMA_CK(cudaMemcpyAsync(mc.G, G, sizeof(double) * se * se,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, mc.st));
+    mc.logdetR = logdet_R;
+    if (mc.prec == LMA_MIXED)
+      Impl<float>::fit_global(mc, n_total);
+    else
+      Impl<double>::fit_global(mc, n_total);
+  });
+}
+
 lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
                        int io_on_device, double* mean_out, double* var_out) {
   if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
   if (u < 0) return fail(LMA_ERR_INVALID_ARG, "negative test count");
   if (u > 0 && (!XU || !tptr || !mean_out || !var_out)) return fail(LMA_ERR_INVALID_ARG, "null pointer");
   const ModelCore& mc = md->core;
+  if (!mc.have_global) return fail(LMA_ERR_INVALID_ARG, "model has no global step yet (lma_model_set_global)");
   if (u > 0) {
     if (tptr[0] != 0 || tptr[mc.M] != u) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr must start at 0, end at u");
-    for (int64_t m = 0; m < mc.M; ++m)
+    const int64_t w1 = mc.w0 + (int64_t)mc.wins.size();
+    for (int64_t m = 0; m < mc.M; ++m) {
       if (tptr[m + 1] < tptr[m]) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr decreases", m);
+      if (tptr[m + 1] > tptr[m] && (std::max<int64_t>(0, m - mc.B) < mc.w0 || m >= w1))
+        return fail(LMA_ERR_INVALID_ARG, "test block outside the windows of this model", m);
+    }
   }
   return guarded([&] {
     if (mc.prec == LMA_MIXED)
@@ -173,6 +235,7 @@ lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const i
 
 lma_status lma_model_loglik(const lma_model* md, double* out) {
   if (!md || !out) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  if (!md->core.have_global) return fail(LMA_ERR_INVALID_ARG, "model has no global step yet (lma_model_set_global)");
   *out = md->core.loglik;
   return LMA_OK;
 }

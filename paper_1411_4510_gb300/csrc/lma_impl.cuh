@@ -115,6 +115,8 @@ struct ModelCore {
   double* kss = nullptr;      // Sigma_SS factor buffer: L_SS (rows < npS) and L_SS^-T rows (FP64)
   double* ss64 = nullptr;     // s*d scaled support inputs (FP64)
   int npS = 0;
+  int64_t w0 = 0;             // block index of the first window (partitioned fits)
+  bool have_global = false;   // global step done (prediction possible)
 };
 
 }  // namespace lma
@@ -131,6 +133,9 @@ struct Impl {
   static void prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, Arena& tmp,
                       const double** X_d, const double** y_d);
   static void fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H);
+  static void fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin, int64_t own_begin,
+                        int64_t own_end);
+  static void fit_global(ModelCore& mc, int64_t n_total);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
                       int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);
@@ -145,8 +150,10 @@ void global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y,
                          double* beta, double* scalars, cudaStream_t st);
 
 // builds the window descriptors of a partition (Section 3: W_m = D_m u D^B_m)
+// for blocks [m_begin, m_end) (m_end < 0: all)
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t elem, std::vector<Win>& wins,
-                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems);
+                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems, int64_t m_begin = 0,
+                  int64_t m_end = -1);
 
 // sweep helpers (defined per precision)
 template <typename T>

@@ -19,11 +19,12 @@ namespace lma {
 
 // ---------------------------------------------------------------------------
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t /*elem*/, std::vector<Win>& wins,
-                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems) {
+                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems, int64_t m_begin, int64_t m_end) {
   const int64_t M = (int64_t)bptr.size() - 1;
-  wins.resize(M);
+  if (m_end < 0) m_end = M;
+  wins.resize(m_end - m_begin);
   buf_elems = dinv_elems = ew_elems = 0;
-  for (int64_t m = 0; m < M; ++m) {
+  for (int64_t m = m_begin; m < m_end; ++m) {
     const int64_t last = std::min(m + B, M - 1);
     Win w{};
     w.n = (int)(bptr[last + 1] - bptr[m]);
@@ -38,7 +39,7 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
     buf_elems += (int64_t)w.rows * w.npad;
     dinv_elems += (int64_t)(w.npad / TB) * TB * TB;
     ew_elems += w.npad;
-    wins[m] = w;
+    wins[m - m_begin] = w;
   }
 }
 
@@ -248,8 +249,13 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   mc.Vt = Vt;
 }
 
+// Local part of a fit: windows of blocks [w_begin, own_end) are formed and
+// factorised, and the Gram of the local summaries (Definition 1) of blocks
+// [own_begin, own_end) goes to mc.G with their log-determinant sum in
+// mc.logdetR.  A whole fit has w_begin = own_begin = 0, own_end = M.
 template <typename T>
-void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
+void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin,
+                        int64_t own_begin, int64_t own_end) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -257,13 +263,15 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
     const double *X_d, *y_d;
     prepare(mc, P, H, tmp, &X_d, &y_d);
     const bool batched = (mc.prec == LMA_MIXED);
-    const int64_t n = mc.n, s = mc.s, M = mc.M;
+    const int64_t n = mc.n, s = mc.s;
     const int d = (int)mc.d;
     T* rT = tmp.alloc<T>(n);
     launch("k_center", k_center<T>, nblk(n), NT, 0, st, y_d, n, mc.mu, rT);
     // windows
     int64_t bufe, dinve, ewe;
-    make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe);
+    make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe, w_begin, own_end);
+    mc.w0 = w_begin;
+    const int64_t M = (int64_t)mc.wins.size();  // windows of this fit
     T* wbuf = mc.keep.alloc<T>(bufe);
     T* dinv = mc.keep.alloc<T>(dinve);
     T* ew = mc.keep.alloc<T>(ewe);
@@ -344,25 +352,52 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
       LMA_CK(cudaStreamSynchronize(st));
       for (int64_t m = 0; m < M; ++m)
         if (hinfo[m]) {
-          fail(LMA_ERR_NOT_PD, "residual window of block " + std::to_string(m) +
+          fail(LMA_ERR_NOT_PD, "residual window of block " + std::to_string(mc.wins[m].m) +
                                    " is not positive definite (pivot " + std::to_string(hinfo[m] - 1) + ")",
-               m);
+               mc.wins[m].m);
           throw Fail{};
         }
     }
-    // global Gram of the local summaries, reduced in a fixed order
+    // Gram of the local summaries of the owned windows, reduced in a fixed order
     const int se = (int)s + 1;
     const int nte = (se + TB - 1) / TB;
-    const int nchunk = (int)std::min<int64_t>(M, 32);
-    const int chunk = (int)((M + nchunk - 1) / nchunk);
+    const int64_t nown = own_end - own_begin;
+    const Win* wown = wd + (own_begin - w_begin);
+    const int nchunk = (int)std::min<int64_t>(nown, 32);
+    const int chunk = (int)((nown + nchunk - 1) / nchunk);
     double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
-    launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wd, (int)M, chunk, (int)s, wbuf, partial);
+    launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wown, (int)nown, chunk, (int)s, wbuf,
+           partial);
     mc.G = mc.keep.alloc<double>((size_t)se * se);
     launch("k_gram_reduce", k_gram_reduce, nblk((int64_t)se * se), NT, 0, st, partial, nchunk, se, mc.G);
-    double* ldw = tmp.alloc<double>(M);
+    double* ldw = tmp.alloc<double>(nown);
     double* ldR = tmp.alloc<double>(1);
-    launch("k_logdet", k_logdet<T>, (unsigned)M, NT, 0, st, wd, wbuf, ldw);
-    launch("k_sum_ordered", k_sum_ordered, 1, 32, 0, st, ldw, (int)M, ldR);
+    launch("k_logdet", k_logdet<T>, (unsigned)nown, NT, 0, st, wown, wbuf, ldw);
+    launch("k_sum_ordered", k_sum_ordered, 1, 32, 0, st, ldw, (int)nown, ldR);
+    double hr = 0;
+    LMA_CK(cudaMemcpyAsync(&hr, ldR, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaStreamSynchronize(st));
+    mc.logdetR = hr;
+    tmp.release();
+  } catch (...) {
+    tmp.release();
+    throw;
+  }
+}
+
+// Global part of a fit (Definition 2 and Eq. (pitck)) from the Gram in mc.G
+// and mc.logdetR (local, or summed over the shards of a partitioned fit):
+// C = I + A, L_C, beta = C^-1 y-ddot, L_C^-T, the per-window L^-1 e and the
+// log-likelihood of n_total training points.
+template <typename T>
+void Impl<T>::fit_global(ModelCore& mc, int64_t n_total) {
+  cudaStream_t st = mc.st;
+  Arena tmp;
+  tmp.st = st;
+  try {
+    const int64_t s = mc.s, M = (int64_t)mc.wins.size();
+    int maxnt = 0;
+    for (const Win& w : mc.wins) maxnt = std::max(maxnt, w.npad / TB);
     // global step in FP64: C = I + A, L_C, w = L_C^-1 y, L_C^-T, beta = C^-1 y
     const int npC = (int)roundup(s, TB);
     double* cb = tmp.alloc<double>((size_t)(npC + 1 + s) * npC);
@@ -377,21 +412,27 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
     T* LcT = mc.keep.alloc<T>(s * s);
     launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)npC * npC, npC, (int)s, LcT);
     mc.LcT = LcT;
-    launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, wd, wbuf, mc.beta, (int)s, ew);
-    double hs[4], hr = 0;
+    launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, mc.wins_d, (const T*)mc.wbuf, mc.beta,
+           (int)s, (T*)mc.ew);
+    double hs[4];
     LMA_CK(cudaMemcpyAsync(hs, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
-    LMA_CK(cudaMemcpyAsync(&hr, ldR, sizeof(double), cudaMemcpyDeviceToHost, st));
     LMA_CK(cudaStreamSynchronize(st));
     mc.quad = hs[0];
     mc.wCw = hs[1];
     mc.logdetC = hs[2];
-    mc.logdetR = hr;
-    mc.loglik = -0.5 * (mc.quad - mc.wCw) - 0.5 * (mc.logdetR + mc.logdetC) - 0.5 * (double)n * log(2.0 * M_PI);
+    mc.loglik = -0.5 * (mc.quad - mc.wCw) - 0.5 * (mc.logdetR + mc.logdetC) - 0.5 * (double)n_total * log(2.0 * M_PI);
+    mc.have_global = true;
     tmp.release();
   } catch (...) {
     tmp.release();
     throw;
   }
+}
+
+template <typename T>
+void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
+  fit_local(mc, P, H, 0, 0, P->m_blocks);
+  fit_global(mc, mc.n);
 }
 
 template <typename T>
@@ -429,10 +470,10 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       if (nu == 0) continue;
       const int first = (int)pairs.size();
       for (int64_t m = std::max<int64_t>(0, nb - B); m <= nb; ++m) {
-        const Win& w = mc.wins[m];
+        const Win& w = mc.wins[m - mc.w0];
         Pair p{};
         p.pbase = pe;
-        p.win = (int)m;
+        p.win = (int)(m - mc.w0);
         p.u0 = (int)tptr[nb];
         p.nu = nu;
         p.c0 = (m < nb) ? w.nB : 0;

@@ -1,0 +1,76 @@
+"""GPU side of the partitioned fit: two shards run one after the other on
+one GPU (lma_fit_local on each sub-problem, the Grams summed on the device,
+lma_model_set_global on each) must reproduce the whole fit's log-likelihood
+and, shard by shard, its predictions of the test blocks each shard owns."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    from paper_1411_4510_gb300 import build
+    build.build()
+    import paper_1411_4510_gb300 as L
+    torch.cuda.set_device(0)
+    return L
+
+
+@pytest.mark.parametrize("prec,tol_ll,tol_mean", [("FP64", 1e-11, 1e-11), ("MIXED", 1e-6, 2e-5)])
+@pytest.mark.parametrize("B,world", [(1, 2), (2, 2), (2, 3)])
+def test_sharded_equals_whole(L, prec, tol_ll, tol_mean, B, world):
+    import torch
+    from paper_1411_4510_gb300 import api, shard
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=B)
+    args = L.problem_args(p)
+    precision = getattr(L, prec)
+    whole = L.lma_fit(precision=precision, **args)
+    ll_whole = L.lma_model_loglik(whole)
+    mean_w, var_w = L.lma_predict(whole, p.XU, p.test_block_ptr)
+    shards = [shard.plan(p.block_ptr, B, world, r) for r in range(world)]
+    models, G, ld = [], None, 0.0
+    for sh in shards:
+        sub = shard.sub_problem(args, sh)
+        m = api.lma_fit_local(**sub, win_begin=0, own_begin=sh.own_begin, own_end=sh.own_end, precision=precision)
+        g, l = api.lma_model_local_summary(m, device=torch.device("cuda:0"))
+        G = g if G is None else G + g
+        ld += l
+        models.append(m)
+    for sh, m in zip(shards, models):
+        api.lma_model_set_global(m, G, ld, p.block_ptr[-1])
+        ll = L.lma_model_loglik(m)
+        assert abs(ll - ll_whole) <= tol_ll * abs(ll_whole), (ll, ll_whole)
+        u0, u1, tp = shard.test_rows(p.test_block_ptr, sh)
+        mean, var = L.lma_predict(m, p.XU[u0:u1], tp)
+        assert np.linalg.norm(mean - mean_w[u0:u1]) <= tol_mean * np.linalg.norm(mean_w[u0:u1])
+        assert np.linalg.norm(var - var_w[u0:u1]) <= 10 * tol_mean * np.linalg.norm(var_w[u0:u1])
+
+
+def test_fit_local_rejects_bad_ranges(L):
+    from paper_1411_4510_gb300 import api
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=1)
+    args = L.problem_args(p)
+    for wb, ob, oe in ((0, 3, 3), (4, 3, 6), (0, 0, 17), (-1, 0, 4)):
+        with pytest.raises(L.LMAError):
+            api.lma_fit_local(**args, win_begin=wb, own_begin=ob, own_end=oe)
+
+
+def test_predict_needs_global_and_windows(L):
+    from paper_1411_4510_gb300 import api
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=1)
+    args = L.problem_args(p)
+    m = api.lma_fit_local(**args, win_begin=4, own_begin=4, own_end=8)
+    with pytest.raises(L.LMAError):
+        L.lma_model_loglik(m)
+    G, ld = api.lma_model_local_summary(m)
+    api.lma_model_set_global(m, G, ld, p.block_ptr[-1])
+    # test block 2 needs window 1, which this model does not hold
+    tp = np.zeros(17, dtype=np.int64)
+    tp[3:] = 1
+    with pytest.raises(L.LMAError):
+        L.lma_predict(m, p.XU[:1], tp)

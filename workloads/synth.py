@@ -234,20 +234,24 @@ _cache: dict = {}
 
 def make_problem(name: str, N: Optional[int] = None, M: Optional[int] = None,
                  s: Optional[int] = None, B: Optional[int] = None,
-                 U: Optional[int] = None, jitter: float = 1e-6) -> Problem:
+                 U: Optional[int] = None, jitter: float = 1e-6, draw: int = 0) -> Problem:
     """Build configuration `name` (C1..C5); keyword overrides shrink it for
-    parity tests while keeping its distribution and partition recipe."""
+    parity tests while keeping its distribution and partition recipe.
+    draw > 0 gives another sample of inputs, noise, test points and partition
+    of the same configuration (the same target function f)."""
     if name not in _DEFAULTS:
         raise ValueError(f"unknown configuration {name!r}")
     p = dict(_DEFAULTS[name])
     for k, v in dict(N=N, M=M, s=s, B=B, U=U).items():
         if v is not None:
             p[k] = int(v)
-    key = (name, p["N"], p["M"], p["s"], p["U"], jitter)
+    key = (name, p["N"], p["M"], p["s"], p["U"], jitter, int(draw))
     if key in _cache:
         return _cache[key].with_B(p["B"])
     idx = CONFIG_NAMES.index(name)
     rx, rnoise, rrff, rS, rtest, rpart = _streams(1411 + idx)
+    if draw:
+        rx, rnoise, _, rS, rtest, rpart = _streams(1411 + idx + 100_000 * int(draw))
     Nn, M_, s_, U_ = p["N"], p["M"], p["s"], p["U"]
     if name == "C1":
         d = 2
@@ -330,6 +334,30 @@ def make_problem(name: str, N: Optional[int] = None, M: Optional[int] = None,
     if Nn <= 200_000 or os.environ.get("LMA_SYNTH_CACHE_ALL"):
         _cache[key] = prob
     return prob
+
+
+def make_replicated(name: str, copies: int, B: Optional[int] = None, **kw) -> Problem:
+    """`copies` draws of configuration `name` (draw 0 first) joined into one
+    problem: their blocks and test blocks are concatenated in draw order and
+    the support set is draw 0's.  Every draw has the configuration's size, so
+    a problem split by draws into `copies` shards keeps the work per shard
+    fixed (weak scaling)."""
+    parts = [make_problem(name, B=B, draw=k, **kw) for k in range(int(copies))]
+    p0 = parts[0]
+    if len(parts) == 1:
+        return p0
+    off, toff = 0, 0
+    ptrs, tptrs = [np.zeros(1, dtype=np.int64)], [np.zeros(1, dtype=np.int64)]
+    for q in parts:
+        ptrs.append(q.block_ptr[1:] + off)
+        tptrs.append(q.test_block_ptr[1:] + toff)
+        off += q.N
+        toff += q.U
+    return dataclasses.replace(
+        p0, name=f"{name}x{copies}", X=np.concatenate([q.X for q in parts]), y=np.concatenate([q.y for q in parts]),
+        block_ptr=np.concatenate(ptrs), XU=np.concatenate([q.XU for q in parts]),
+        yU=np.concatenate([q.yU for q in parts]), test_block_ptr=np.concatenate(tptrs),
+        meta=dict(p0.meta, copies=int(copies)))
 
 
 def make_random_problem(seed: int, sizes, d: int = 2, s: int = 6, B: int = 1,
