@@ -85,6 +85,24 @@ def kernel_work(p, B):
             "k_pred_rhs": prhs, "k_pred_rhs_tc": prhs}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
+# one ncu capture of the same bench command (profiles/k_resid_tc_c2_b1.md),
+# valid only while the kernel sources hash to the value it was taken at.
+NCU_TRAFFIC = {"k_resid_tc": {"bytes": 85319680 + 177819904, "sources": "694f04d402204e14"}}
+
+
+def sources_hash() -> str:
+    import glob
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(here, "paper_1411_4510_gb300", "csrc", "*.cu*"))
+                    + glob.glob(os.path.join(here, "include", "*.h"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_step_tma", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
                   "k_pred_rhs_tc"}
 
@@ -394,6 +412,10 @@ def main():
                     "traffic": None, "kernel": dominant, "launches_timed": n_l, "avg_launch_ms": tot_ms / n_l,
                     "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived, not measured)"}
         roof["work_per_step_gflop"] = work[dominant] / 1e9
+        t = NCU_TRAFFIC.get(dominant)
+        if t and t["sources"] == sources_hash() and world == 1:
+            roof["traffic"] = t["bytes"]
+            roof["traffic_note"] = "ncu dram bytes read+write per launch (profiles/k_resid_tc_c2_b1.md)"
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu, _ = cpu_baseline(p, args.B)
