@@ -166,10 +166,13 @@ lma_status lma_fit_local(const lma_problem* P, const lma_hyper* H, const lma_opt
   md->core.st = (cudaStream_t)O->cuda_stream;
   md->core.keep.st = md->core.st;
   lma_status st = guarded([&] {
-    if (O->precision == LMA_MIXED)
+    if (O->precision == LMA_MIXED) {
       Impl<float>::fit_local(md->core, P, H, win_begin, own_begin, own_end);
-    else
+      Impl<float>::check(md->core, false, 0, true);
+    } else {
       Impl<double>::fit_local(md->core, P, H, win_begin, own_begin, own_end);
+      Impl<double>::check(md->core, false, 0, true);
+    }
   });
   if (st != LMA_OK) {
     md->core.keep.release();
@@ -202,10 +205,13 @@ lma_status lma_model_set_global(lma_model* md, const double* G, double logdet_R,
     LMA_CK(cudaMemcpyAsync(mc.G, G, sizeof(double) * se * se,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, mc.st));
     mc.logdetR = logdet_R;
-    if (mc.prec == LMA_MIXED)
+    if (mc.prec == LMA_MIXED) {
       Impl<float>::fit_global(mc, n_total);
-    else
+      Impl<float>::check(mc, true, n_total, false);
+    } else {
       Impl<double>::fit_global(mc, n_total);
+      Impl<double>::check(mc, true, n_total, false);
+    }
   });
 }
 

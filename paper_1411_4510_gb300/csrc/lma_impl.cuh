@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <atomic>
 #include <string>
 #include <vector>
@@ -87,6 +89,29 @@ inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 blo
 }
 
 inline int64_t roundup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Page-locked staging for the small index tables a call uploads (window
+// descriptors, work-item lists): from pinned memory cudaMemcpyAsync is a
+// true asynchronous copy, while a pageable source can make the driver wait
+// for the stream.  One buffer per host thread, handed out by a bump pointer;
+// the entry points reset it after their final stream synchronisation.  If it
+// fills up, the device is synchronised (every staged copy has landed) and the
+// buffer grows.
+struct Staging {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  void* take(size_t bytes, cudaStream_t st);
+  void reset() { used = 0; }
+};
+Staging& staging();
+
+// Upload `bytes` of host data to device memory `dst` through the staging buffer.
+inline void stage_copy(void* dst, const void* host, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  void* h = staging().take(bytes, st);
+  memcpy(h, host, bytes);
+  LMA_CK(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, st));
+}
 inline unsigned nblk(int64_t n, int t = NT) { return (unsigned)((n + t - 1) / t); }
 
 // Everything a fitted model keeps on the device.
@@ -117,6 +142,13 @@ struct ModelCore {
   int npS = 0;
   int64_t w0 = 0;             // block index of the first window (partitioned fits)
   bool have_global = false;   // global step done (prediction possible)
+  // device status words, checked once at the end of a call:
+  // [0] Sigma_SS pivot failure (+1 column), [1] I + A pivot failure,
+  // [2] tensor-core pipeline wait timed out
+  int* flags = nullptr;
+  int* winfo = nullptr;       // per-window pivot failure (+1 column), 0 = fine
+  double* ldR_d = nullptr;    // device sum of log|R-dot_m^-1| over the owned windows
+  double* sc_d = nullptr;     // device scalars of the global step
 };
 
 }  // namespace lma
@@ -136,6 +168,9 @@ struct Impl {
   static void fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin, int64_t own_begin,
                         int64_t own_end);
   static void fit_global(ModelCore& mc, int64_t n_total);
+  // waits for the stream and turns the status words into an error (if any);
+  // global: also reads the global step's scalars and forms the loglik
+  static void check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
                       int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);

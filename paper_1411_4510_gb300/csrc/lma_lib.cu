@@ -43,6 +43,30 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
   }
 }
 
+void* Staging::take(size_t bytes, cudaStream_t st) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (used + bytes > cap) {
+    // every earlier upload (of any stream of this thread) must have landed
+    (void)st;
+    LMA_CK(cudaDeviceSynchronize());
+    if (bytes > cap) {
+      if (base) cudaFreeHost(base);
+      base = nullptr;
+      cap = std::max<size_t>({bytes, 2 * cap, size_t(1) << 20});
+      LMA_CK(cudaMallocHost((void**)&base, cap));
+    }
+    used = 0;
+  }
+  void* p = base + used;
+  used += bytes;
+  return p;
+}
+
+Staging& staging() {
+  static thread_local Staging s;
+  return s;
+}
+
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
@@ -163,26 +187,16 @@ static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* b
 }
 
 // Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
-// `extra` extra rows).  Returns false when it is not positive definite.
-static bool factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra, int nid) {
-  std::vector<Win> w(1);
-  w[0] = Win{};
-  w[0].n = n;
-  w[0].npad = npad;
-  w[0].rows = npad + extra;
-  w[0].nB = 0;
-  w[0].base = 0;
-  w[0].dinv = 0;
-  Win* wd = tmp.alloc<Win>(1);
+// `extra` extra rows); the first failing pivot (+1) goes to *info (device),
+// which the caller checks after its next synchronisation.
+static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra, int nid,
+                               int* info) {
+  Win w{};
+  w.n = n;
+  w.npad = npad;
+  w.rows = npad + extra;
   double* dv = tmp.alloc<double>((size_t)npad * TB);
-  int* info = tmp.alloc<int>(1);
-  LMA_CK(cudaMemcpyAsync(wd, w.data(), sizeof(Win), cudaMemcpyHostToDevice, st));
-  LMA_CK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  right_looking_fp64(st, w[0], wd, buf, dv, info, nid);
-  int h = 0;
-  LMA_CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LMA_CK(cudaStreamSynchronize(st));
-  return h == 0;
+  right_looking_fp64(st, w, nullptr, buf, dv, info, nid);
 }
 
 // ---------------------------------------------------------------------------
@@ -219,7 +233,7 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   *X_d = X;
   *y_d = y;
   mc.inv_ell_d = mc.keep.alloc<double>(d);
-  LMA_CK(cudaMemcpyAsync(mc.inv_ell_d, mc.inv_ell.data(), sizeof(double) * d, cudaMemcpyHostToDevice, st));
+  stage_copy(mc.inv_ell_d, mc.inv_ell.data(), sizeof(double) * d, st);
   T* xsT = mc.keep.alloc<T>(n * d);
   T* ssT = mc.keep.alloc<T>(s * d);
   double* ss64 = mc.keep.alloc<double>(s * d);
@@ -234,10 +248,9 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   mc.kss = kb;
   mc.npS = npS;
   launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
-  if (!factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s)) {
-    fail(LMA_ERR_NOT_PD, "Sigma_SS + jitter is not positive definite", -1);
-    throw Fail{};
-  }
+  mc.flags = mc.keep.alloc<int>(4);
+  LMA_CK(cudaMemsetAsync(mc.flags, 0, 4 * sizeof(int), st));
+  factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0);
   T* ET = mc.keep.alloc<T>(s * s);
   launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
   mc.ET = ET;
@@ -276,12 +289,13 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     T* dinv = mc.keep.alloc<T>(dinve);
     T* ew = mc.keep.alloc<T>(ewe);
     Win* wd = mc.keep.alloc<Win>(M);
-    int* info = tmp.alloc<int>(M);
+    int* info = mc.keep.alloc<int>(M);
+    mc.winfo = info;
     mc.wbuf = wbuf;
     mc.dinv = dinv;
     mc.ew = ew;
     mc.wins_d = wd;
-    LMA_CK(cudaMemcpyAsync(wd, mc.wins.data(), sizeof(Win) * M, cudaMemcpyHostToDevice, st));
+    stage_copy(wd, mc.wins.data(), sizeof(Win) * M, st);
     LMA_CK(cudaMemsetAsync(info, 0, sizeof(int) * M, st));
     int maxnt = 0;
     for (const Win& w : mc.wins) maxnt = std::max(maxnt, w.npad / TB);
@@ -306,19 +320,11 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
           for (int J = 0; J * TB < np && J <= 2 * I + 1; ++J) items.push_back(make_int4((int)m, I, J, 0));
       }
       int4* itd = tmp.alloc<int4>(items.size());
-      int* rerr = tmp.alloc<int>(1);
-      LMA_CK(cudaMemcpyAsync(itd, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
-      LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+      int* rerr = mc.flags + 2;
+      stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
       launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)xsT, d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
-      int h = 0;
-      LMA_CK(cudaMemcpyAsync(&h, rerr, sizeof(int), cudaMemcpyDeviceToHost, st));
-      LMA_CK(cudaStreamSynchronize(st));
-      if (h) {
-        fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the residual kernel");
-        throw Fail{};
-      }
     } else if (batched) {
       launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
                                                                           (T)mc.sn2, wbuf);
@@ -331,33 +337,8 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
         launch("k_fill_ext", k_fill_ext<T>, dim3(nt, et, 1), NT, 0, st, wd + m, Vt, rT, (int)s, wbuf);
       }
     }
-    int* tc_err = nullptr;
-    if (batched && sizeof(T) == 4 && use_tensor_cores()) {
-      tc_err = tmp.alloc<int>(1);
-      LMA_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
-    }
+    int* tc_err = (batched && sizeof(T) == 4 && use_tensor_cores()) ? mc.flags + 2 : nullptr;
     chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err);
-    if (tc_err) {
-      int h = 0;
-      LMA_CK(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-      LMA_CK(cudaStreamSynchronize(st));
-      if (h) {
-        fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the window sweep");
-        throw Fail{};
-      }
-    }
-    {
-      std::vector<int> hinfo(M);
-      LMA_CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * M, cudaMemcpyDeviceToHost, st));
-      LMA_CK(cudaStreamSynchronize(st));
-      for (int64_t m = 0; m < M; ++m)
-        if (hinfo[m]) {
-          fail(LMA_ERR_NOT_PD, "residual window of block " + std::to_string(mc.wins[m].m) +
-                                   " is not positive definite (pivot " + std::to_string(hinfo[m] - 1) + ")",
-               mc.wins[m].m);
-          throw Fail{};
-        }
-    }
     // Gram of the local summaries of the owned windows, reduced in a fixed order
     const int se = (int)s + 1;
     const int nte = (se + TB - 1) / TB;
@@ -371,13 +352,9 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     mc.G = mc.keep.alloc<double>((size_t)se * se);
     launch("k_gram_reduce", k_gram_reduce, nblk((int64_t)se * se), NT, 0, st, partial, nchunk, se, mc.G);
     double* ldw = tmp.alloc<double>(nown);
-    double* ldR = tmp.alloc<double>(1);
+    mc.ldR_d = mc.keep.alloc<double>(1);
     launch("k_logdet", k_logdet<T>, (unsigned)nown, NT, 0, st, wown, wbuf, ldw);
-    launch("k_sum_ordered", k_sum_ordered, 1, 32, 0, st, ldw, (int)nown, ldR);
-    double hr = 0;
-    LMA_CK(cudaMemcpyAsync(&hr, ldR, sizeof(double), cudaMemcpyDeviceToHost, st));
-    LMA_CK(cudaStreamSynchronize(st));
-    mc.logdetR = hr;
+    launch("k_sum_ordered", k_sum_ordered, 1, 32, 0, st, ldw, (int)nown, mc.ldR_d);
     tmp.release();
   } catch (...) {
     tmp.release();
@@ -402,26 +379,16 @@ void Impl<T>::fit_global(ModelCore& mc, int64_t n_total) {
     const int npC = (int)roundup(s, TB);
     double* cb = tmp.alloc<double>((size_t)(npC + 1 + s) * npC);
     launch("k_build_global", k_build_global, nblk((int64_t)(npC + 1 + s) * npC), NT, 0, st, mc.G, (int)s, npC, cb);
-    if (!factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1, (int)s)) {
-      fail(LMA_ERR_NOT_PD, "global summary Sigma-ddot_SS is not positive definite", -2);
-      throw Fail{};
-    }
+    factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1, (int)s, mc.flags + 1);
     mc.beta = mc.keep.alloc<double>(s);
-    double* sc = tmp.alloc<double>(4);
+    mc.sc_d = mc.keep.alloc<double>(4);
+    double* sc = mc.sc_d;
     launch("k_global_finish", k_global_finish, 1, NT, 0, st, cb, mc.G, (int)s, npC, mc.beta, sc);
     T* LcT = mc.keep.alloc<T>(s * s);
     launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)npC * npC, npC, (int)s, LcT);
     mc.LcT = LcT;
     launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, mc.wins_d, (const T*)mc.wbuf, mc.beta,
            (int)s, (T*)mc.ew);
-    double hs[4];
-    LMA_CK(cudaMemcpyAsync(hs, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
-    LMA_CK(cudaStreamSynchronize(st));
-    mc.quad = hs[0];
-    mc.wCw = hs[1];
-    mc.logdetC = hs[2];
-    mc.loglik = -0.5 * (mc.quad - mc.wCw) - 0.5 * (mc.logdetR + mc.logdetC) - 0.5 * (double)n_total * log(2.0 * M_PI);
-    mc.have_global = true;
     tmp.release();
   } catch (...) {
     tmp.release();
@@ -430,9 +397,51 @@ void Impl<T>::fit_global(ModelCore& mc, int64_t n_total) {
 }
 
 template <typename T>
+void Impl<T>::check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device) {
+  cudaStream_t st = mc.st;
+  int fl[4] = {0, 0, 0, 0};
+  double hs[4] = {0, 0, 0, 0}, hr = 0;
+  const int64_t nw = (int64_t)mc.wins.size();
+  std::vector<int> wi((size_t)nw);
+  LMA_CK(cudaMemcpyAsync(fl, mc.flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+  if (nw && mc.winfo) LMA_CK(cudaMemcpyAsync(wi.data(), mc.winfo, sizeof(int) * nw, cudaMemcpyDeviceToHost, st));
+  if (logdet_from_device && mc.ldR_d) LMA_CK(cudaMemcpyAsync(&hr, mc.ldR_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (global) LMA_CK(cudaMemcpyAsync(hs, mc.sc_d, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+  LMA_CK(cudaStreamSynchronize(st));
+  staging().reset();
+  if (fl[0]) {
+    fail(LMA_ERR_NOT_PD, "Sigma_SS + jitter is not positive definite", -1);
+    throw Fail{};
+  }
+  if (fl[2]) {
+    fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the residual or window-sweep kernels");
+    throw Fail{};
+  }
+  for (int64_t m = 0; m < nw; ++m)
+    if (wi[m]) {
+      fail(LMA_ERR_NOT_PD, "residual window of block " + std::to_string(mc.wins[m].m) +
+                               " is not positive definite (pivot " + std::to_string(wi[m] - 1) + ")",
+           mc.wins[m].m);
+      throw Fail{};
+    }
+  if (logdet_from_device) mc.logdetR = hr;
+  if (!global) return;
+  if (fl[1]) {
+    fail(LMA_ERR_NOT_PD, "global summary Sigma-ddot_SS is not positive definite", -2);
+    throw Fail{};
+  }
+  mc.quad = hs[0];
+  mc.wCw = hs[1];
+  mc.logdetC = hs[2];
+  mc.loglik = -0.5 * (mc.quad - mc.wCw) - 0.5 * (mc.logdetR + mc.logdetC) - 0.5 * (double)n_total * log(2.0 * M_PI);
+  mc.have_global = true;
+}
+
+template <typename T>
 void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
   fit_local(mc, P, H, 0, 0, P->m_blocks);
   fit_global(mc, mc.n);
+  check(mc, true, mc.n, true);
 }
 
 template <typename T>
@@ -506,11 +515,13 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     int2* isd = tmp.alloc<int2>(it_sw.size());
     int4* iad = tmp.alloc<int4>(it_acc.size());
     int4* itd = tmp.alloc<int4>(it_t12.size());
-    LMA_CK(cudaMemcpyAsync(pd, pairs.data(), sizeof(Pair) * pairs.size(), cudaMemcpyHostToDevice, st));
-    LMA_CK(cudaMemcpyAsync(ird, it_rhs.data(), sizeof(int4) * it_rhs.size(), cudaMemcpyHostToDevice, st));
-    LMA_CK(cudaMemcpyAsync(isd, it_sw.data(), sizeof(int2) * it_sw.size(), cudaMemcpyHostToDevice, st));
-    LMA_CK(cudaMemcpyAsync(iad, it_acc.data(), sizeof(int4) * it_acc.size(), cudaMemcpyHostToDevice, st));
-    LMA_CK(cudaMemcpyAsync(itd, it_t12.data(), sizeof(int4) * it_t12.size(), cudaMemcpyHostToDevice, st));
+    stage_copy(pd, pairs.data(), sizeof(Pair) * pairs.size(), st);
+    stage_copy(ird, it_rhs.data(), sizeof(int4) * it_rhs.size(), st);
+    stage_copy(isd, it_sw.data(), sizeof(int2) * it_sw.size(), st);
+    stage_copy(iad, it_acc.data(), sizeof(int4) * it_acc.size(), st);
+    stage_copy(itd, it_t12.data(), sizeof(int4) * it_t12.size(), st);
+    int* perr = tmp.alloc<int>(1);  // tensor-core pipeline timeout, checked at the end
+    LMA_CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
     T* Pbuf = tmp.alloc<T>(pe);
     const T* xs = (const T*)mc.xsT;
     const T* Vt = (const T*)mc.Vt;
@@ -541,18 +552,9 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
             for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
-        int* rerr = tmp.alloc<int>(1);
-        LMA_CK(cudaMemcpyAsync(irr, it_r.data(), sizeof(int4) * it_r.size(), cudaMemcpyHostToDevice, st));
-        LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+        stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
         launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), 256, tc_resid_smem(), st, pd, (const int4*)irr,
-               mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, rerr);
-        int hh = 0;
-        LMA_CK(cudaMemcpyAsync(&hh, rerr, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LMA_CK(cudaStreamSynchronize(st));
-        if (hh) {
-          fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the prediction right-hand sides");
-          throw Fail{};
-        }
+               mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
                (int)s, (T)mc.ss2, Pbuf);
@@ -562,18 +564,9 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
         for (size_t pi = 0; pi < pairs.size(); ++pi)
           for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut) it_tc.push_back(make_int2((int)pi, ut));
         int2* itc = tmp.alloc<int2>(it_tc.size());
-        int* terr = tmp.alloc<int>(1);
-        LMA_CK(cudaMemcpyAsync(itc, it_tc.data(), sizeof(int2) * it_tc.size(), cudaMemcpyHostToDevice, st));
-        LMA_CK(cudaMemsetAsync(terr, 0, sizeof(int), st));
+        stage_copy(itc, it_tc.data(), sizeof(int2) * it_tc.size(), st);
         launch("k_pred_sweep_tc", k_pred_sweep_tc, (unsigned)it_tc.size(), 256, tc_chol_smem(), st, pd,
-               (const int2*)itc, mc.wins_d, (const float*)wbuf, (const float*)mc.dinv, (float*)Pbuf, terr);
-        int h = 0;
-        LMA_CK(cudaMemcpyAsync(&h, terr, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LMA_CK(cudaStreamSynchronize(st));
-        if (h) {
-          fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the prediction sweep");
-          throw Fail{};
-        }
+               (const int2*)itc, mc.wins_d, (const float*)wbuf, (const float*)mc.dinv, (float*)Pbuf, perr);
       } else {
         launch("k_pred_sweep", k_pred_sweep<T>, (unsigned)it_sw.size(), NT, sizeof(CholSmem<T>), st, pd, isd,
                mc.wins_d, wbuf, (const T*)mc.dinv, Pbuf);
@@ -613,8 +606,15 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       LMA_CK(cudaMemcpyAsync(mean, md, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
       LMA_CK(cudaMemcpyAsync(var, vd, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
     }
+    int herr = 0;
+    LMA_CK(cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, st));
     tmp.release();
     LMA_CK(cudaStreamSynchronize(st));
+    staging().reset();
+    if (herr) {
+      fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the prediction kernels");
+      throw Fail{};
+    }
   } catch (...) {
     tmp.release();
     throw;
@@ -636,7 +636,7 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
     Win w = all[m];
     w.base = 0;
     Win* wd = tmp.alloc<Win>(1);
-    LMA_CK(cudaMemcpyAsync(wd, &w, sizeof(Win), cudaMemcpyHostToDevice, st));
+    stage_copy(wd, &w, sizeof(Win), st);
     T* buf = tmp.alloc<T>((size_t)w.npad * w.npad);
     const int nt = w.npad / TB;
     if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
@@ -654,9 +654,8 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
       for (int I = 0; I * 128 < w.npad; ++I)
         for (int J = 0; J * TB < w.npad && J <= 2 * I + 1; ++J) items.push_back(make_int4(0, I, J, 0));
       int4* itd = tmp.alloc<int4>(items.size());
-      int* rerr = tmp.alloc<int>(1);
-      LMA_CK(cudaMemcpyAsync(itd, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
-      LMA_CK(cudaMemsetAsync(rerr, 0, sizeof(int), st));
+      int* rerr = mc.flags + 2;
+      stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
       launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)mc.xsT, (int)mc.d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)buf, rerr);
     } else {
@@ -665,7 +664,7 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
     }
     std::vector<T> h((size_t)w.npad * w.npad);
     LMA_CK(cudaMemcpyAsync(h.data(), buf, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, st));
-    LMA_CK(cudaStreamSynchronize(st));
+    check(mc, false, 0, false);
     const int n = w.n;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
@@ -709,7 +708,7 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
       maxrows = std::max(maxrows, g.nrows);
     }
     GWin* gwd = tmp.alloc<GWin>(M);
-    LMA_CK(cudaMemcpyAsync(gwd, gw.data(), sizeof(GWin) * M, cudaMemcpyHostToDevice, st));
+    stage_copy(gwd, gw.data(), sizeof(GWin) * M, st);
     T* Q = tmp.alloc<T>(qe);
     T* Gb = tmp.alloc<T>(ge);
     T* GV = tmp.alloc<T>(gve);
@@ -727,8 +726,8 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     }
     int2* isw = tmp.alloc<int2>(it_sw.size());
     int2* ig = tmp.alloc<int2>(it_g.size());
-    LMA_CK(cudaMemcpyAsync(isw, it_sw.data(), sizeof(int2) * it_sw.size(), cudaMemcpyHostToDevice, st));
-    LMA_CK(cudaMemcpyAsync(ig, it_g.data(), sizeof(int2) * it_g.size(), cudaMemcpyHostToDevice, st));
+    stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
+    stage_copy(ig, it_g.data(), sizeof(int2) * it_g.size(), st);
     launch("k_bwd_sweep", k_bwd_sweep<T>, dim3((unsigned)it_sw.size()), NT, sizeof(CholSmem<T>), st, isw,
            mc.wins_d, gwd, wbuf, (const T*)mc.dinv, Q);
     const int np2 = d + 2;
@@ -738,7 +737,7 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd,
            (const T*)Gb, (const T*)mc.Vt, si, GV);
     int64_t* bptr_d = tmp.alloc<int64_t>(M + 1);
-    LMA_CK(cudaMemcpyAsync(bptr_d, mc.bptr.data(), sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, st));
+    stage_copy(bptr_d, mc.bptr.data(), sizeof(int64_t) * (M + 1), st);
     T* PsiT = tmp.alloc<T>((s + 1) * n);
     T* GVT = tmp.alloc<T>(s * n);
     launch("k_grad_gather", k_grad_gather<T>, dim3(nblk(n), (unsigned)(2 * s + 1)), NT, 0, st, mc.wins_d, gwd,
