@@ -69,7 +69,7 @@ Staging& staging() {
 
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
-static size_t tc_resid_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
+static size_t tc_resid_smem() { return sizeof(tc::TcSmem<RB>) + tc::kTcAlignSlack; }
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
 // SIMT kernels instead (used to compare the two on the same build).
@@ -317,12 +317,12 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       for (int64_t m = 0; m < M; ++m) {
         const int np = mc.wins[m].npad;
         for (int I = 0; I * 128 < np; ++I)
-          for (int J = 0; J * TB < np && J <= 2 * I + 1; ++J) items.push_back(make_int4((int)m, I, J, 0));
+          for (int J = 0; J * RB < np && J * RB <= 128 * I + 127; ++J) items.push_back(make_int4((int)m, I, J, 0));
       }
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 4 * RB, tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)xsT, d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
     } else if (batched) {
@@ -547,13 +547,13 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
         }
         std::vector<int4> it_r;
         for (size_t pi = 0; pi < pairs.size(); ++pi) {
-          const int nct = mc.wins[pairs[pi].win].npad / TB;
+          const int nct = (mc.wins[pairs[pi].win].npad + RB - 1) / RB;
           for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut)
             for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
         stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), 256, tc_resid_smem(), st, pd, (const int4*)irr,
+        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), 4 * RB, tc_resid_smem(), st, pd, (const int4*)irr,
                mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
@@ -652,11 +652,11 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
       }
       std::vector<int4> items;
       for (int I = 0; I * 128 < w.npad; ++I)
-        for (int J = 0; J * TB < w.npad && J <= 2 * I + 1; ++J) items.push_back(make_int4(0, I, J, 0));
+        for (int J = 0; J * RB < w.npad && J * RB <= 128 * I + 127; ++J) items.push_back(make_int4(0, I, J, 0));
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 256, tc_resid_smem(), st, (const int4*)itd, wd,
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 4 * RB, tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)mc.xsT, (int)mc.d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)buf, rerr);
     } else {
       launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,

@@ -851,17 +851,21 @@ __global__ void __launch_bounds__(256, 2) k_pred_sweep_tc(const Pair* __restrict
 
 namespace lma {
 
-// Compensated tile product on the tensor cores: hi + lo = sum_{k<K} A(r,k) B(c,k)
-// for the calling thread's row r = 32 (warp mod 4) + lane and its 32 columns
-// c = 32 (warp / 4) + j of a 128 x 64 tile.  Each 32-wide K chunk goes into
-// one of two tensor-memory slots (columns [0,64) and [64,128) of tmem); as
-// soon as its MMAs complete, the chunk's partial sums are drained into
-// registers and added with TwoSum.  The tensor core's FP32 accumulation is
-// thus only 12 MMA steps deep and the cross-chunk sum is compensated.
-template <class RA, class RB>
-__device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, RB rowB, float (&hi)[32],
+// Compensated tile product on the tensor cores over a 128 x BN tile, run by
+// 4 BN threads: hi + lo = sum_{k<K} A(r,k) B(c,k) for the calling thread's
+// row r = 32 (warp mod 4) + lane and its 32 columns c = 32 (warp / 4) + j.
+// Each 32-wide K chunk goes into one of two tensor-memory slots (columns
+// [0, BN) and [BN, 2 BN) of tmem); as soon as its MMAs complete, the chunk's
+// partial sums are drained into registers and added with TwoSum.  The tensor
+// core's FP32 accumulation is thus only 12 MMA steps deep and the cross-chunk
+// sum is compensated.  BN = 128 issues half as many MMA instructions per
+// product as BN = 64 at the same cost per instruction.
+template <int BN, class RA, class RB>
+__device__ bool comp_product(tc::TcSmem<BN>& sm, uint32_t tmem, int K, RA rowA, RB rowB, float (&hi)[32],
                              float (&lo)[32]) {
   using namespace tc;
+  constexpr int NTHR = 4 * BN;
+  constexpr int NA = 128 * 8 / NTHR, NB = BN * 8 / NTHR;  // float4 per thread per chunk
   const int tid = threadIdx.x, warp = tid >> 5;
   const int q = warp & 3, half = warp >> 2;
   const uint32_t tlane = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
@@ -871,27 +875,27 @@ __device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, 
     float t[16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      tmem_ld16(tlane + 64 * slot + 16 * h, t);
+      tmem_ld16(tlane + BN * slot + 16 * h, t);
 #pragma unroll
       for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
     }
   };
-  const uint32_t idesc = idesc_tf32(128, 64);
+  const uint32_t idesc = idesc_tf32(128, BN);
   const int nchunk = K / 32;
   TcPipe p;
   bool ok = true;
-  float4 ra[4], rb[2];
+  float4 ra[NA], rb[NB];
   auto load = [&](int c) {
     const int k0 = c * 32;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+    for (int j = 0; j < NA; ++j) {
+      const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
       const float* src = rowA(row);
       ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+    for (int j = 0; j < NB; ++j) {
+      const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
       const float* src = rowB(row);
       rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -906,15 +910,15 @@ __device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, 
       drain(s);
       fence_before_sync();
     }
-    TcStage<64>& S = sm.st[s];
+    TcStage<BN>& S = sm.st[s];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = tid + 256 * j;
+    for (int j = 0; j < NA; ++j) {
+      const int i = tid + NTHR * j;
       store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int i = tid + 256 * j;
+    for (int j = 0; j < NB; ++j) {
+      const int i = tid + NTHR * j;
       store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
     }
     if (c + 1 < nchunk) load(c + 1);
@@ -926,7 +930,7 @@ __device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, 
       if (tid == 0) {
         const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
         const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-        const uint32_t dcol = tmem + 64 * s;
+        const uint32_t dcol = tmem + BN * s;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           const uint32_t o = ks * 32;
@@ -956,7 +960,8 @@ __device__ bool comp_product(tc::TcSmem<64>& sm, uint32_t tmem, int K, RA rowA, 
   return __syncthreads_and(ok) != 0;
 }
 
-__device__ __forceinline__ void tc_setup(tc::TcSmem<64>& sm, uint32_t ncols) {
+template <int BN>
+__device__ __forceinline__ void tc_setup(tc::TcSmem<BN>& sm, uint32_t ncols) {
   using namespace tc;
   if (threadIdx.x == 0) {
     mbar_init(&sm.bar[0], 1);
@@ -969,7 +974,8 @@ __device__ __forceinline__ void tc_setup(tc::TcSmem<64>& sm, uint32_t ncols) {
   fence_after_sync();
 }
 
-__device__ __forceinline__ void tc_teardown(tc::TcSmem<64>& sm, uint32_t ncols) {
+template <int BN>
+__device__ __forceinline__ void tc_teardown(tc::TcSmem<BN>& sm, uint32_t ncols) {
   using namespace tc;
   fence_before_sync();
   __syncthreads();
@@ -977,27 +983,28 @@ __device__ __forceinline__ void tc_teardown(tc::TcSmem<64>& sm, uint32_t ncols) 
 }
 
 // Residual tiles on the tensor cores (mixed form).  Item (window, I, J): rows
-// [128 I, 128 I + 128) x columns [64 J, 64 J + 64) of the window's residual
+// [128 I, 128 I + 128) x columns [RB J, RB J + RB) of the window's residual
 // R = K + sigma_n^2 I - Vt Vt^T, blanket-first, with the Vt Vt^T sum of
-// comp_product.  Vtp: point-major V with leading dimension ldv (a multiple
-// of 32, zero pad).
-__global__ void __launch_bounds__(256, 2) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
-                                                  const float* __restrict__ xs, int d, const float* __restrict__ Vtp,
-                                                  int ldv, float ss2, float sn2, float* __restrict__ buf,
-                                                  int* __restrict__ err) {
+// comp_product (RB = 128 columns, 512 threads).  Vtp: point-major V with
+// leading dimension ldv (a multiple of 32, zero pad).
+constexpr int RB = 128;
+__global__ void __launch_bounds__(4 * RB, 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
+                                                     const float* __restrict__ xs, int d, const float* __restrict__ Vtp,
+                                                     int ldv, float ss2, float sn2, float* __restrict__ buf,
+                                                     int* __restrict__ err) {
   using namespace tc;
   const int4 it = items[blockIdx.x];
   const Win w = wins[it.x];
-  const int r0 = it.y * 128, c0 = it.z * TB;
+  const int r0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TcSmem<64>& sm = tc_smem<64>(smraw);
-  __shared__ float xc[TB][MAXD + 1];
+  TcSmem<RB>& sm = tc_smem<RB>(smraw);
+  __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < TB * d; e += 256) {
+  for (int e = tid; e < RB * d; e += 4 * RB) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  tc_setup(sm, 128);
+  tc_setup(sm, 2 * RB);
   auto rowA = [&](int r) -> const float* {
     const int i = r0 + r;
     return (i < w.n) ? Vtp + (w.g_end - 1 - i) * (int64_t)ldv : nullptr;
@@ -1011,10 +1018,11 @@ __global__ void __launch_bounds__(256, 2) k_resid_tc(const int4* __restrict__ it
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int i = r0 + q * 32 + lane;
-  if (ok && i < w.npad) {
+  const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
+  if (ok && i < w.npad && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = (i < w.n) ? xs[(w.g_end - 1 - i) * d + t] : 0.f;
-    float* dst = buf + w.base + (int64_t)i * w.npad + c0 + half * 32;
+    float* dst = buf + w.base + (int64_t)i * w.npad + cg;
     float out[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -1038,32 +1046,33 @@ __global__ void __launch_bounds__(256, 2) k_resid_tc(const int4* __restrict__ it
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  tc_teardown(sm, 128);
+  tc_teardown(sm, 2 * RB);
 }
 
 // Prediction right-hand sides on the tensor cores: item (pair, u tile of
-// 128, column tile of 64): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
+// 128, column tile of RB): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
 // the window of the pair, with the compensated product (the same cancellation
 // as the residual).  Vup / Vtp: leading dimension ldv (multiple of 32).
-__global__ void __launch_bounds__(256, 2) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
-                                                     const Win* __restrict__ wins, const float* __restrict__ xs,
-                                                     const float* __restrict__ xu, int d, const float* __restrict__ Vtp,
-                                                     const float* __restrict__ Vup, int ldv, float ss2,
-                                                     float* __restrict__ P, int* __restrict__ err) {
+__global__ void __launch_bounds__(4 * RB, 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
+                                                        const Win* __restrict__ wins, const float* __restrict__ xs,
+                                                        const float* __restrict__ xu, int d,
+                                                        const float* __restrict__ Vtp, const float* __restrict__ Vup,
+                                                        int ldv, float ss2, float* __restrict__ P,
+                                                        int* __restrict__ err) {
   using namespace tc;
   const int4 it = items[blockIdx.x];
   const Pair pr = pairs[it.x];
   const Win w = wins[pr.win];
-  const int u0 = it.y * 128, c0 = it.z * TB;
+  const int u0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TcSmem<64>& sm = tc_smem<64>(smraw);
-  __shared__ float xc[TB][MAXD + 1];
+  TcSmem<RB>& sm = tc_smem<RB>(smraw);
+  __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < TB * d; e += 256) {
+  for (int e = tid; e < RB * d; e += 4 * RB) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  tc_setup(sm, 128);
+  tc_setup(sm, 2 * RB);
   auto rowA = [&](int r) -> const float* {
     const int uu = u0 + r;
     return (uu < pr.nu) ? Vup + (int64_t)(pr.u0 + uu) * ldv : nullptr;
@@ -1077,10 +1086,11 @@ __global__ void __launch_bounds__(256, 2) k_pred_rhs_tc(const Pair* __restrict__
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int uu = u0 + q * 32 + lane;
-  if (ok && uu < pr.nu) {
+  const int cg = c0 + half * 32;
+  if (ok && uu < pr.nu && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = xu[(int64_t)(pr.u0 + uu) * d + t];
-    float* dst = P + pr.pbase + (int64_t)uu * w.npad + c0 + half * 32;
+    float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
     float out[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -1100,7 +1110,7 @@ __global__ void __launch_bounds__(256, 2) k_pred_rhs_tc(const Pair* __restrict__
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  tc_teardown(sm, 128);
+  tc_teardown(sm, 2 * RB);
 }
 
 }  // namespace lma
