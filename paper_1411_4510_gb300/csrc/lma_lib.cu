@@ -69,7 +69,7 @@ Staging& staging() {
 
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
-static size_t tc_resid_smem() { return sizeof(tc::TcSmem<RB>) + tc::kTcAlignSlack; }
+static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
 // SIMT kernels instead (used to compare the two on the same build).
@@ -322,7 +322,7 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 4 * RB, tc_resid_smem(), st, (const int4*)itd, wd,
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), comp_threads<RB>(), tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)xsT, d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
     } else if (batched) {
@@ -553,7 +553,7 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
         stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), 4 * RB, tc_resid_smem(), st, pd, (const int4*)irr,
+        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), comp_threads<RB>(), tc_resid_smem(), st, pd, (const int4*)irr,
                mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
@@ -656,7 +656,7 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), 4 * RB, tc_resid_smem(), st, (const int4*)itd, wd,
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), comp_threads<RB>(), tc_resid_smem(), st, (const int4*)itd, wd,
              (const float*)mc.xsT, (int)mc.d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)buf, rerr);
     } else {
       launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,

@@ -851,86 +851,158 @@ __global__ void __launch_bounds__(256, 2) k_pred_sweep_tc(const Pair* __restrict
 
 namespace lma {
 
-// Compensated tile product on the tensor cores over a 128 x BN tile, run by
-// 4 BN threads: hi + lo = sum_{k<K} A(r,k) B(c,k) for the calling thread's
-// row r = 32 (warp mod 4) + lane and its 32 columns c = 32 (warp / 4) + j.
-// Each 32-wide K chunk goes into one of two tensor-memory slots (columns
-// [0, BN) and [BN, 2 BN) of tmem); as soon as its MMAs complete, the chunk's
-// partial sums are drained into registers and added with TwoSum.  The tensor
-// core's FP32 accumulation is thus only 12 MMA steps deep and the cross-chunk
-// sum is compensated.  BN = 128 issues half as many MMA instructions per
-// product as BN = 64 at the same cost per instruction.
-template <int BN, class RA, class RB>
-__device__ bool comp_product(tc::TcSmem<BN>& sm, uint32_t tmem, int K, RA rowA, RB rowB, float (&hi)[32],
-                             float (&lo)[32]) {
+// Compensated tile product on the tensor cores over a 128 x BN tile:
+// hi + lo = sum_{k<K} A(r,k) B(c,k) for worker thread t's row
+// r = 32 (warp mod 4) + lane and its 32 columns c = 32 (warp / 4) + j.
+// 4 BN worker threads (warps 0 .. BN/8 - 1) load each 32-wide K chunk one
+// chunk ahead into registers, split it into TF32 hi/lo into stage c mod 2 and
+// arrive on full[s]; the last warp issues the chunk's 12 MMAs into tensor-
+// memory slot c mod 2 (columns [BN s, BN s + BN)) and commits to done[s].
+// Before refilling stage s the workers wait for done[s] of chunk c - 2 and
+// drain that slot into registers, adding the chunk sums with TwoSum; their
+// arrival on full[s] therefore also frees slot s for the next MMAs.  The
+// tensor core's FP32 accumulation is only 12 MMA steps deep, the cross-chunk
+// sum is compensated, and no CTA-wide barrier waits for the MMA issue.
+template <int BN>
+struct CompSmem {
+  tc::TcStage<BN> st[2];
+  uint64_t full[2], done[2], fin;
+  uint32_t tmem;
+  int abort;
+};
+template <int BN>
+__device__ __forceinline__ CompSmem<BN>& comp_smem(unsigned char* raw) {
+  uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+  p = (p + 1023) & ~uintptr_t(1023);
+  return *reinterpret_cast<CompSmem<BN>*>(p);
+}
+template <int BN>
+constexpr int comp_threads() { return 4 * BN + 32; }
+
+// Barriers and tensor memory (2 BN columns, allocated by the MMA warp).
+template <int BN>
+__device__ __forceinline__ void comp_setup(CompSmem<BN>& sm) {
   using namespace tc;
-  constexpr int NTHR = 4 * BN;
-  constexpr int NA = 128 * 8 / NTHR, NB = BN * 8 / NTHR;  // float4 per thread per chunk
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int q = warp & 3, half = warp >> 2;
-  const uint32_t tlane = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+  constexpr int NW = BN / 8;  // worker warps
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&sm.full[s], NW);
+      mbar_init(&sm.done[s], 1);
+    }
+    mbar_init(&sm.fin, 1);
+    sm.abort = 0;
+    mbar_fence_init();
+  }
+  if ((threadIdx.x >> 5) == NW) tmem_alloc(&sm.tmem, 2 * BN);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+template <int BN>
+__device__ __forceinline__ void comp_teardown(CompSmem<BN>& sm) {
+  using namespace tc;
+  fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == BN / 8) tmem_dealloc(sm.tmem, 2 * BN);
+}
+
+// Returns false (in every thread) when a wait timed out.  hi / lo are only
+// meaningful in worker threads.
+template <int BN, class RA, class RB>
+__device__ bool comp_product(CompSmem<BN>& sm, int K, RA rowA, RB rowB, float (&hi)[32], float (&lo)[32]) {
+  using namespace tc;
+  constexpr int NW = BN / 8, NTHR = 4 * BN;
+  constexpr int NA = 128 * 8 / NTHR, NB = BN * 8 / NTHR;  // float4 per worker per chunk
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nchunk = K / 32;
+  volatile int* abort_flag = &sm.abort;
 #pragma unroll
   for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
-  auto drain = [&](int slot) {
-    float t[16];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld16(tlane + BN * slot + 16 * h, t);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
-    }
-  };
-  const uint32_t idesc = idesc_tf32(128, BN);
-  const int nchunk = K / 32;
-  TcPipe p;
-  bool ok = true;
-  float4 ra[NA], rb[NB];
-  auto load = [&](int c) {
-    const int k0 = c * 32;
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
-      const float* src = rowA(row);
-      ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
-      const float* src = rowB(row);
-      rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  };
-  if (nchunk > 0) load(0);
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
-    if (p.pending[s]) {  // chunk c-2 used stage s and slot s: wait for it, then drain the slot
-      ok = tc_drain(sm, p, s);
-      if (!ok) break;
+  if (warp < NW) {
+    const int q = warp & 3, half = warp >> 2;
+    const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+    auto wait_done = [&](int c) -> bool {  // MMAs of chunk c have completed (warp-uniform result)
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&sm.done[c & 1], (c >> 1) & 1) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) *abort_flag = 1;
+      return okw != 0;
+    };
+    auto drain = [&](int c) {
       fence_after_sync();
-      drain(s);
+      float t[16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tmem_ld16(tlane + BN * (c & 1) + 16 * h, t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
+      }
       fence_before_sync();
-    }
-    TcStage<BN>& S = sm.st[s];
+    };
+    float4 ra[NA], rb[NB];
+    auto load = [&](int c) {
+      const int k0 = c * 32;
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const int i = tid + NTHR * j;
-      store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
-    }
+      for (int j = 0; j < NA; ++j) {
+        const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
+        const float* src = rowA(row);
+        ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int i = tid + NTHR * j;
-      store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
+      for (int j = 0; j < NB; ++j) {
+        const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
+        const float* src = rowB(row);
+        rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    if (nchunk > 0) load(0);
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c & 1;
+      if (c >= 2) {  // chunk c - 2 used stage s and slot s
+        if (!wait_done(c - 2)) break;
+        drain(c - 2);
+      }
+      if (*abort_flag) break;
+      TcStage<BN>& S = sm.st[s];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int i = tid + NTHR * j;
+        store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int i = tid + NTHR * j;
+        store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[j]);
+      }
+      if (c + 1 < nchunk) load(c + 1);
+      fence_async_smem();
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.full[s]);
     }
-    if (c + 1 < nchunk) load(c + 1);
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (tid < 32) {
-      if (tid == 0) {
+    for (int c = max(0, nchunk - 2); c < nchunk && !*abort_flag; ++c) {  // the last one or two chunks, in order
+      if (!wait_done(c)) break;
+      drain(c);
+    }
+  } else {
+    // MMA warp: the whole warp runs the loop, lane 0 issues
+    const uint32_t idesc = idesc_tf32(128, BN);
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c & 1;
+      if (*abort_flag) break;
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&sm.full[s], (c >> 1) & 1) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after_sync();
+      if (lane == 0) {
+        TcStage<BN>& S = sm.st[s];
         const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
         const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-        const uint32_t dcol = tmem + BN * s;
+        const uint32_t dcol = sm.tmem + BN * s;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           const uint32_t o = ks * 32;
@@ -938,48 +1010,16 @@ __device__ bool comp_product(tc::TcSmem<BN>& sm, uint32_t tmem, int K, RA rowA, 
           mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
           mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
         }
-        mma_commit(&sm.bar[s]);
+        mma_commit(&sm.done[s]);
       }
-      __syncwarp();  // lanes 1-31 wait here, so no divergent wait stalls the issuing lane
+      __syncwarp();
     }
-    p.cnt[s] += 1;
-    p.pending[s] = true;
+    if (lane == 0) mma_commit(&sm.fin);  // arrives once every MMA issued above has completed
+    __syncwarp();
   }
-  for (int k = 0; k < 2 && ok; ++k) {  // the last one or two chunks, in order
-    const int c = nchunk - 2 + k;
-    if (c < 0) continue;
-    const int s = c & 1;
-    if (p.pending[s]) {
-      ok = tc_drain(sm, p, s);
-      if (!ok) break;
-      fence_after_sync();
-      drain(s);
-      fence_before_sync();
-    }
-  }
-  return __syncthreads_and(ok) != 0;
-}
-
-template <int BN>
-__device__ __forceinline__ void tc_setup(tc::TcSmem<BN>& sm, uint32_t ncols) {
-  using namespace tc;
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.bar[0], 1);
-    mbar_init(&sm.bar[1], 1);
-    mbar_fence_init();
-  }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sm.tmem, ncols);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-}
-
-template <int BN>
-__device__ __forceinline__ void tc_teardown(tc::TcSmem<BN>& sm, uint32_t ncols) {
-  using namespace tc;
-  fence_before_sync();
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(sm.tmem, ncols);
+  // every issued MMA has completed before anyone reads or frees tensor memory
+  const bool w = mbar_wait(&sm.fin, 0);
+  return __syncthreads_and(w && !*abort_flag) != 0;
 }
 
 // Residual tiles on the tensor cores (mixed form).  Item (window, I, J): rows
@@ -988,7 +1028,7 @@ __device__ __forceinline__ void tc_teardown(tc::TcSmem<BN>& sm, uint32_t ncols) 
 // comp_product (RB = 128 columns, 512 threads).  Vtp: point-major V with
 // leading dimension ldv (a multiple of 32, zero pad).
 constexpr int RB = 128;
-__global__ void __launch_bounds__(4 * RB, 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
+__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
                                                      const float* __restrict__ xs, int d, const float* __restrict__ Vtp,
                                                      int ldv, float ss2, float sn2, float* __restrict__ buf,
                                                      int* __restrict__ err) {
@@ -997,14 +1037,14 @@ __global__ void __launch_bounds__(4 * RB, 1) k_resid_tc(const int4* __restrict__
   const Win w = wins[it.x];
   const int r0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TcSmem<RB>& sm = tc_smem<RB>(smraw);
+  CompSmem<RB>& sm = comp_smem<RB>(smraw);
   __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += 4 * RB) {
+  for (int e = tid; e < RB * d; e += comp_threads<RB>()) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  tc_setup(sm, 2 * RB);
+  comp_setup(sm);
   auto rowA = [&](int r) -> const float* {
     const int i = r0 + r;
     return (i < w.n) ? Vtp + (w.g_end - 1 - i) * (int64_t)ldv : nullptr;
@@ -1014,12 +1054,12 @@ __global__ void __launch_bounds__(4 * RB, 1) k_resid_tc(const int4* __restrict__
     return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
   };
   float hi[32], lo[32];
-  const bool ok = comp_product(sm, sm.tmem, ldv, rowA, rowB, hi, lo);
+  const bool ok = comp_product(sm, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int i = r0 + q * 32 + lane;
   const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
-  if (ok && i < w.npad && cg < w.npad) {
+  if (ok && warp < RB / 8 && i < w.npad && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = (i < w.n) ? xs[(w.g_end - 1 - i) * d + t] : 0.f;
     float* dst = buf + w.base + (int64_t)i * w.npad + cg;
@@ -1046,14 +1086,14 @@ __global__ void __launch_bounds__(4 * RB, 1) k_resid_tc(const int4* __restrict__
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  tc_teardown(sm, 2 * RB);
+  comp_teardown(sm);
 }
 
 // Prediction right-hand sides on the tensor cores: item (pair, u tile of
 // 128, column tile of RB): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
 // the window of the pair, with the compensated product (the same cancellation
 // as the residual).  Vup / Vtp: leading dimension ldv (multiple of 32).
-__global__ void __launch_bounds__(4 * RB, 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
+__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
                                                         const Win* __restrict__ wins, const float* __restrict__ xs,
                                                         const float* __restrict__ xu, int d,
                                                         const float* __restrict__ Vtp, const float* __restrict__ Vup,
@@ -1065,14 +1105,14 @@ __global__ void __launch_bounds__(4 * RB, 1) k_pred_rhs_tc(const Pair* __restric
   const Win w = wins[pr.win];
   const int u0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TcSmem<RB>& sm = tc_smem<RB>(smraw);
+  CompSmem<RB>& sm = comp_smem<RB>(smraw);
   __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += 4 * RB) {
+  for (int e = tid; e < RB * d; e += comp_threads<RB>()) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  tc_setup(sm, 2 * RB);
+  comp_setup(sm);
   auto rowA = [&](int r) -> const float* {
     const int uu = u0 + r;
     return (uu < pr.nu) ? Vup + (int64_t)(pr.u0 + uu) * ldv : nullptr;
@@ -1082,12 +1122,12 @@ __global__ void __launch_bounds__(4 * RB, 1) k_pred_rhs_tc(const Pair* __restric
     return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
   };
   float hi[32], lo[32];
-  const bool ok = comp_product(sm, sm.tmem, ldv, rowA, rowB, hi, lo);
+  const bool ok = comp_product(sm, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int uu = u0 + q * 32 + lane;
   const int cg = c0 + half * 32;
-  if (ok && uu < pr.nu && cg < w.npad) {
+  if (ok && warp < RB / 8 && uu < pr.nu && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = xu[(int64_t)(pr.u0 + uu) * d + t];
     float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
@@ -1110,7 +1150,7 @@ __global__ void __launch_bounds__(4 * RB, 1) k_pred_rhs_tc(const Pair* __restric
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  tc_teardown(sm, 2 * RB);
+  comp_teardown(sm);
 }
 
 }  // namespace lma
