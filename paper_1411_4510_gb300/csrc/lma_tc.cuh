@@ -152,12 +152,14 @@ __device__ __forceinline__ TcSmem<BN>& tc_smem(unsigned char* raw) {
 
 // Split a float4 of K-consecutive values into TF32 hi/lo and store both at
 // (row, k..k+3) of a swizzled tile.
+// The remainder is rounded to TF32 as well: the MMA would otherwise read
+// its FP32 encoding truncated, a one-sided error of up to 2^-23 |x|.
 __device__ __forceinline__ void store_split4(float* hi, float* lo, uint32_t row, uint32_t k, float4 v) {
   float4 h, l;
-  h.x = tf32_round(v.x); l.x = v.x - h.x;
-  h.y = tf32_round(v.y); l.y = v.y - h.y;
-  h.z = tf32_round(v.z); l.z = v.z - h.z;
-  h.w = tf32_round(v.w); l.w = v.w - h.w;
+  h.x = tf32_round(v.x); l.x = tf32_round(v.x - h.x);
+  h.y = tf32_round(v.y); l.y = tf32_round(v.y - h.y);
+  h.z = tf32_round(v.z); l.z = tf32_round(v.z - h.z);
+  h.w = tf32_round(v.w); l.w = tf32_round(v.w - h.w);
   const uint32_t off = sw128_offset(row, k) >> 2;
   *reinterpret_cast<float4*>(hi + off) = h;
   *reinterpret_cast<float4*>(lo + off) = l;
