@@ -301,8 +301,10 @@ def main():
 
     def step(prec=L.MIXED, host=None):
         src = dsrc if host is None else host
-        if sh is None:
-            m = L.lma_fit(src["X"], src["y"], S=src["S"], precision=prec, **kw)
+        if sh is None:  # fit and predict in one call: the global step overlaps the prediction
+            mean, var, m = L.lma_fit_predict(src["X"], src["y"], S=src["S"], XU=src["XU"], test_block_ptr=tptr,
+                                             precision=prec, keep_model=True, **kw)
+            return m, (mean, var)
         else:  # local summaries, one all-reduce of the summary Gram, global step
             m = api.lma_fit_local(src["X"], src["y"], S=src["S"], win_begin=0, own_begin=sh.own_begin,
                                   own_end=sh.own_end, precision=prec, **kw)

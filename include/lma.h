@@ -110,6 +110,19 @@ lma_status lma_predict(const lma_model* model, int64_t u, const double* XU,
                        const int64_t* test_block_ptr, int noisy, int io_on_device,
                        double* mean_out, double* var_out);
 
+/* lma_fit followed by lma_predict in one call, with the same results: the
+ * FP64 global step (Definition 2) runs on a library-owned second stream
+ * while the prediction's kernels that do not need its results run on
+ * cuda_stream, and the rest of the prediction waits for it.  Arguments as in
+ * lma_fit and lma_predict; `out` may be NULL (the model is then freed) or
+ * receives the model (free with lma_model_free).  Outputs are valid when the
+ * call returns.  Errors as in lma_fit and lma_predict; on an error nothing
+ * is returned in *out.                                                     */
+lma_status lma_fit_predict(const lma_problem* problem, const lma_hyper* hyper,
+                           const lma_options* options, int64_t u, const double* XU,
+                           const int64_t* test_block_ptr, int noisy, int io_on_device,
+                           double* mean_out, double* var_out, lma_model** out);
+
 /* log N(y_D; mu, Sigma-bar_DD) of a fitted model (Sigma-bar by Eq. acov). */
 lma_status lma_model_loglik(const lma_model* model, double* out);
 

@@ -120,6 +120,32 @@ def lma_predict(model: Model, XU, test_block_ptr, noisy: bool = True, out=None):
     return mean, var
 
 
+def lma_fit_predict(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, XU, test_block_ptr, jitter=1e-6,
+                    mean=0.0, precision=MIXED, noisy: bool = True, stream=None, keep_model: bool = False):
+    """lma_fit + lma_predict in one call (the global step overlaps the
+    prediction).  Returns (mean, var) or (mean, var, model) with keep_model."""
+    lib = _abi.load()
+    keep = []
+    prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
+                              precision, stream, keep)
+    u = int(XU.shape[0])
+    xp, dev = _f64(XU, keep)
+    tp = _i64(test_block_ptr, keep)
+    if dev:
+        m = torch.empty(u, dtype=torch.float64, device=XU.device)
+        v = torch.empty(u, dtype=torch.float64, device=XU.device)
+        mp, vp = m.data_ptr(), v.data_ptr()
+    else:
+        m, v = np.empty(u), np.empty(u)
+        mp, vp = m.ctypes.data, v.ctypes.data
+    h = C.c_void_p()
+    _abi.check(lib.lma_fit_predict(C.byref(prob), C.byref(hyp), C.byref(opt), u, xp, tp, int(bool(noisy)), int(dev),
+                                   mp, vp, C.byref(h) if keep_model else None))
+    if keep_model:
+        return m, v, Model(h.value, prob.m_blocks, prob.s)
+    return m, v
+
+
 def lma_model_loglik(model: Model) -> float:
     out = C.c_double()
     _abi.check(_abi.load().lma_model_loglik(model.handle, C.byref(out)))

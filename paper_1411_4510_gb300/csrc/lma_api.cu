@@ -239,6 +239,41 @@ lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const i
   });
 }
 
+lma_status lma_fit_predict(const lma_problem* P, const lma_hyper* H, const lma_options* O, int64_t u,
+                           const double* XU, const int64_t* tptr, int noisy, int io_on_device, double* mean_out,
+                           double* var_out, lma_model** out) {
+  if (out) *out = nullptr;
+  lma_status cs = check_problem(P, H, O);
+  if (cs != LMA_OK) return cs;
+  if (u < 0) return fail(LMA_ERR_INVALID_ARG, "negative test count");
+  if (u > 0 && (!XU || !tptr || !mean_out || !var_out)) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  if (u > 0) {
+    if (tptr[0] != 0 || tptr[P->m_blocks] != u)
+      return fail(LMA_ERR_INVALID_ARG, "test_block_ptr must start at 0, end at u");
+    for (int64_t m = 0; m < P->m_blocks; ++m)
+      if (tptr[m + 1] < tptr[m]) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr decreases", m);
+  }
+  lma_model* md = new (std::nothrow) lma_model();
+  if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+  md->core.prec = O->precision;
+  md->core.st = (cudaStream_t)O->cuda_stream;
+  md->core.keep.st = md->core.st;
+  lma_status st = guarded([&] {
+    if (O->precision == LMA_MIXED)
+      Impl<float>::fit_predict(md->core, P, H, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
+    else
+      Impl<double>::fit_predict(md->core, P, H, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
+  });
+  if (st != LMA_OK || !out) {
+    md->core.keep.release();
+    cudaStreamSynchronize(md->core.st);
+    delete md;
+    return st;
+  }
+  *out = md;
+  return LMA_OK;
+}
+
 lma_status lma_model_loglik(const lma_model* md, double* out) {
   if (!md || !out) return fail(LMA_ERR_INVALID_ARG, "null pointer");
   if (!md->core.have_global) return fail(LMA_ERR_INVALID_ARG, "model has no global step yet (lma_model_set_global)");

@@ -167,12 +167,14 @@ struct Impl {
   static void fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H);
   static void fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin, int64_t own_begin,
                         int64_t own_end);
-  static void fit_global(ModelCore& mc, int64_t n_total);
+  static void fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on = nullptr);
   // waits for the stream and turns the status words into an error (if any);
   // global: also reads the global step's scalars and forms the loglik
   static void check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
-                      int on_device, double* mean, double* var);
+                      int on_device, double* mean, double* var, cudaEvent_t global_done = nullptr);
+  static void fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
+                          const int64_t* tptr, int noisy, int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);
   static void loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad);
   static void setup_attributes();

@@ -367,10 +367,17 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
 // C = I + A, L_C, beta = C^-1 y-ddot, L_C^-T, the per-window L^-1 e and the
 // log-likelihood of n_total training points.
 template <typename T>
-void Impl<T>::fit_global(ModelCore& mc, int64_t n_total) {
-  cudaStream_t st = mc.st;
+void Impl<T>::fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on) {
+  cudaStream_t st = on ? on : mc.st;
   Arena tmp;
   tmp.st = st;
+  const cudaStream_t keep_st = mc.keep.st;
+  mc.keep.st = st;  // model buffers of the global step are ordered on its stream
+  struct Restore {
+    ModelCore& m;
+    cudaStream_t s;
+    ~Restore() { m.keep.st = s; }
+  } restore{mc, keep_st};
   try {
     const int64_t s = mc.s, M = (int64_t)mc.wins.size();
     int maxnt = 0;
@@ -444,9 +451,54 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
   check(mc, true, mc.n, true);
 }
 
+// Fit and predict with the FP64 global step (Definition 2) on a second stream:
+// the prediction's kernels that do not read its results (test-point support
+// coordinates, right-hand sides, window sweeps, the h accumulation) overlap
+// it, and the rest waits for its event.
+template <typename T>
+void Impl<T>::fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
+                          const int64_t* tptr, int noisy, int on_device, double* mean, double* var) {
+  struct Side {  // one side stream and two events per host thread and device
+    int dev = -1;
+    cudaStream_t st = nullptr;
+    cudaEvent_t local = nullptr, global = nullptr;
+    void drop() {
+      if (local) cudaEventDestroy(local);
+      if (global) cudaEventDestroy(global);
+      if (st) cudaStreamDestroy(st);
+      st = nullptr;
+      local = global = nullptr;
+    }
+    ~Side() { drop(); }
+  };
+  static thread_local Side side;
+  int dev = 0;
+  LMA_CK(cudaGetDevice(&dev));
+  if (side.dev != dev) {
+    side.drop();
+    LMA_CK(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+    LMA_CK(cudaEventCreateWithFlags(&side.local, cudaEventDisableTiming));
+    LMA_CK(cudaEventCreateWithFlags(&side.global, cudaEventDisableTiming));
+    side.dev = dev;
+  }
+  fit_local(mc, P, H, 0, 0, P->m_blocks);
+  LMA_CK(cudaEventRecord(side.local, mc.st));
+  LMA_CK(cudaStreamWaitEvent(side.st, side.local, 0));
+  try {
+    fit_global(mc, mc.n, side.st);
+    LMA_CK(cudaEventRecord(side.global, side.st));
+    predict(mc, U, XU, tptr, noisy, on_device, mean, var, side.global);
+  } catch (...) {
+    cudaStreamSynchronize(side.st);  // nothing of this call may still run on the side stream
+    throw;
+  }
+  LMA_CK(cudaStreamWaitEvent(mc.st, side.global, 0));
+  check(mc, true, mc.n, true);
+}
+
 template <typename T>
 void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
-                      double* mean, double* var) {
+                      double* mean, double* var, cudaEvent_t global_done) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -590,6 +642,8 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     launch("k_pred_accum", k_pred_accum<T>, (unsigned)it_acc.size(), NT, 0, st, pd, iad, mc.wins_d, wbuf, Pbuf, Vu, (int)s, h);
     double* t1 = tmp.alloc<double>(U);
     double* t2 = tmp.alloc<double>(U);
+    // from here on the global step's results (beta, L^-1 e, L_C^-1) are read
+    if (global_done) LMA_CK(cudaStreamWaitEvent(st, global_done, 0));
     launch("k_pred_t12", k_pred_t12<T>, nblk((int64_t)it_t12.size() * 32), NT, 0, st, pd, itd, (int)it_t12.size(), mc.wins_d, Pbuf,
                                                                     (const T*)mc.ew, t1, t2);
     double* part = tmp.alloc<double>((size_t)nst * U);
