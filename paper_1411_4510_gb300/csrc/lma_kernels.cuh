@@ -536,12 +536,14 @@ __global__ void __launch_bounds__(NT) k_gram(const Win* __restrict__ wins, int n
     }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ partial, int nchunk, int se, double* __restrict__ G) {
+__global__ void k_gram_reduce(const double* __restrict__ partial, int nchunk, int se, double* __restrict__ G,
+                              int tile) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)se * se) return;
   int i = (int)(e / se), j = (int)(e % se);
+  (void)tile;
   int a = i, b = j;
-  if ((a / TB) < (b / TB)) { a = j; b = i; }  // computed tiles are lower tiles
+  if (a < b) { a = j; b = i; }  // the lower triangle is computed; mirror it exactly
   double sum = 0.0;
   for (int c = 0; c < nchunk; ++c) sum += partial[(int64_t)c * se * se + (int64_t)a * se + b];
   G[e] = sum;

@@ -101,6 +101,7 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
     done = true;
   }
@@ -347,10 +348,23 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     const int nchunk = (int)std::min<int64_t>(nown, 32);
     const int chunk = (int)((nown + nchunk - 1) / nchunk);
     double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
-    launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wown, (int)nown, chunk, (int)s, wbuf,
-           partial);
+    int gtile = TB;
+    if (tc_err) {  // tensor cores: 128 x 128 tiles of the lower triangle
+      gtile = 128;
+      const int nt = (se + 127) / 128;
+      std::vector<int2> tl;
+      for (int I = 0; I < nt; ++I)
+        for (int J = 0; J <= I; ++J) tl.push_back(make_int2(I, J));
+      int2* tld = tmp.alloc<int2>(tl.size());
+      stage_copy(tld, tl.data(), sizeof(int2) * tl.size(), st);
+      launch("k_gram_tc", k_gram_tc, dim3((unsigned)tl.size(), nchunk), comp_threads<RB>(), tc_resid_smem(), st,
+             (const int2*)tld, wown, (int)nown, chunk, (int)s, (const float*)wbuf, partial, tc_err);
+    } else {
+      launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wown, (int)nown, chunk, (int)s, wbuf,
+             partial);
+    }
     mc.G = mc.keep.alloc<double>((size_t)se * se);
-    launch("k_gram_reduce", k_gram_reduce, nblk((int64_t)se * se), NT, 0, st, partial, nchunk, se, mc.G);
+    launch("k_gram_reduce", k_gram_reduce, nblk((int64_t)se * se), NT, 0, st, partial, nchunk, se, mc.G, gtile);
     double* ldw = tmp.alloc<double>(nown);
     mc.ldR_d = mc.keep.alloc<double>(1);
     launch("k_logdet", k_logdet<T>, (unsigned)nown, NT, 0, st, wown, wbuf, ldw);

@@ -908,61 +908,86 @@ __device__ __forceinline__ void comp_teardown(CompSmem<BN>& sm) {
   if ((threadIdx.x >> 5) == BN / 8) tmem_dealloc(sm.tmem, 2 * BN);
 }
 
-// Returns false (in every thread) when a wait timed out.  hi / lo are only
-// meaningful in worker threads.
-template <int BN, class RA, class RB>
-__device__ bool comp_product(CompSmem<BN>& sm, int K, RA rowA, RB rowB, float (&hi)[32], float (&lo)[32]) {
+// Chunk and call counters of a CTA's compensated products: a kernel may call
+// comp_product several times (one K range each) and the barrier phases
+// continue from one call to the next.
+struct CompState {
+  int chunks = 0;
+  int calls = 0;
+};
+
+// Adds sum over k in [kbeg, kend) of A(r,k) B(c,k) to hi + lo (zeroed first
+// unless ACC).  rowA(r) / rowB(c) return a 16-byte-aligned row pointer (or
+// nullptr for a zero row) whose row holds at least kend rounded up to 4
+// values; values outside [kbeg, kend) are masked.  Returns false (in every
+// thread) when a wait timed out.  hi / lo are only meaningful in workers.
+template <int BN, bool ACC = false, class RA, class RB>
+__device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend, RA rowA, RB rowB,
+                             float (&hi)[32], float (&lo)[32]) {
   using namespace tc;
   constexpr int NW = BN / 8, NTHR = 4 * BN;
   constexpr int NA = 128 * 8 / NTHR, NB = BN * 8 / NTHR;  // float4 per worker per chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nchunk = K / 32;
+  const int kal = kbeg & ~3;
+  const int nchunk = kend > kbeg ? (kend - kal + 31) / 32 : 0;
+  const int g0 = cs.chunks;  // global index of this call's first chunk
   volatile int* abort_flag = &sm.abort;
+  if (!ACC) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+    for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  }
   if (warp < NW) {
     const int q = warp & 3, half = warp >> 2;
     const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
-    auto wait_done = [&](int c) -> bool {  // MMAs of chunk c have completed (warp-uniform result)
+    auto wait_done = [&](int g) -> bool {  // MMAs of global chunk g have completed (warp-uniform result)
       int okw = 1;
-      if (lane == 0) okw = mbar_wait(&sm.done[c & 1], (c >> 1) & 1) ? 1 : 0;
+      if (lane == 0) okw = mbar_wait(&sm.done[g & 1], (g >> 1) & 1) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) *abort_flag = 1;
       return okw != 0;
     };
-    auto drain = [&](int c) {
+    auto drain = [&](int g) {
       fence_after_sync();
       float t[16];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        tmem_ld16(tlane + BN * (c & 1) + 16 * h, t);
+        tmem_ld16(tlane + BN * (g & 1) + 16 * h, t);
 #pragma unroll
         for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
       }
       fence_before_sync();
     };
     float4 ra[NA], rb[NB];
+    auto ld4 = [&](const float* src, int kk) -> float4 {
+      if (!src || kk >= kend) return make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 v = *reinterpret_cast<const float4*>(src + kk);
+      if (kk < kbeg || kk + 4 > kend) {
+        v.x = (kk >= kbeg && kk < kend) ? v.x : 0.f;
+        v.y = (kk + 1 >= kbeg && kk + 1 < kend) ? v.y : 0.f;
+        v.z = (kk + 2 >= kbeg && kk + 2 < kend) ? v.z : 0.f;
+        v.w = (kk + 3 >= kbeg && kk + 3 < kend) ? v.w : 0.f;
+      }
+      return v;
+    };
     auto load = [&](int c) {
-      const int k0 = c * 32;
+      const int k0 = kal + c * 32;
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
-        const float* src = rowA(row);
-        ra[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ra[j] = ld4(rowA(row), k0 + c4 * 4);
       }
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         const int i = tid + NTHR * j, row = i >> 3, c4 = i & 7;
-        const float* src = rowB(row);
-        rb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb[j] = ld4(rowB(row), k0 + c4 * 4);
       }
     };
     if (nchunk > 0) load(0);
     for (int c = 0; c < nchunk; ++c) {
-      const int s = c & 1;
-      if (c >= 2) {  // chunk c - 2 used stage s and slot s
-        if (!wait_done(c - 2)) break;
-        drain(c - 2);
+      const int g = g0 + c, s = g & 1;
+      if (c >= 2) {  // chunk g - 2 used stage s and slot s
+        if (!wait_done(g - 2)) break;
+        drain(g - 2);
       }
       if (*abort_flag) break;
       TcStage<BN>& S = sm.st[s];
@@ -983,17 +1008,17 @@ __device__ bool comp_product(CompSmem<BN>& sm, int K, RA rowA, RB rowB, float (&
       if (lane == 0) mbar_arrive(&sm.full[s]);
     }
     for (int c = max(0, nchunk - 2); c < nchunk && !*abort_flag; ++c) {  // the last one or two chunks, in order
-      if (!wait_done(c)) break;
-      drain(c);
+      if (!wait_done(g0 + c)) break;
+      drain(g0 + c);
     }
   } else {
     // MMA warp: the whole warp runs the loop, lane 0 issues
     const uint32_t idesc = idesc_tf32(128, BN);
     for (int c = 0; c < nchunk; ++c) {
-      const int s = c & 1;
+      const int g = g0 + c, s = g & 1;
       if (*abort_flag) break;
       int okw = 1;
-      if (lane == 0) okw = mbar_wait(&sm.full[s], (c >> 1) & 1) ? 1 : 0;
+      if (lane == 0) okw = mbar_wait(&sm.full[s], (g >> 1) & 1) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) {
         *abort_flag = 1;
@@ -1020,7 +1045,9 @@ __device__ bool comp_product(CompSmem<BN>& sm, int K, RA rowA, RB rowB, float (&
     __syncwarp();
   }
   // every issued MMA has completed before anyone reads or frees tensor memory
-  const bool w = mbar_wait(&sm.fin, 0);
+  const bool w = mbar_wait(&sm.fin, cs.calls & 1);
+  cs.chunks += nchunk;
+  cs.calls += 1;
   return __syncthreads_and(w && !*abort_flag) != 0;
 }
 
@@ -1056,7 +1083,8 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* 
     return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
   };
   float hi[32], lo[32];
-  const bool ok = comp_product(sm, ldv, rowA, rowB, hi, lo);
+  CompState cs;
+  const bool ok = comp_product(sm, cs, 0, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int i = r0 + q * 32 + lane;
@@ -1087,6 +1115,51 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* 
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
+  }
+  comp_teardown(sm);
+}
+
+// Gram of the local summaries on the tensor cores (mixed form): after the
+// sweep, the extra rows of window m hold (L^-1 [r | Vt_W])^T, whose block
+// columns [nB, n) are [z_m | Z_m]^T (Definition 1 whitened), so
+// G = sum_m [z_m | Z_m]^T [z_m | Z_m] is a product of extra rows with K over
+// block points.  CTA (tile x of the lower 128-tiles of G, window chunk y)
+// adds the windows [chunk y, chunk y + chunk) with the compensated product
+// and writes hi + lo as FP64 partials, summed over chunks by k_gram_reduce.
+__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_gram_tc(const int2* __restrict__ tiles,
+                                                                 const Win* __restrict__ wins, int nwin, int chunk,
+                                                                 int s, const float* __restrict__ buf,
+                                                                 double* __restrict__ partial, int* __restrict__ err) {
+  using namespace tc;
+  const int2 tl = tiles[blockIdx.x];
+  const int se = s + 1, r0 = tl.x * 128, c0 = tl.y * RB;
+  const int w0 = blockIdx.y * chunk, w1 = min(nwin, w0 + chunk);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CompSmem<RB>& sm = comp_smem<RB>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  comp_setup(sm);
+  CompState cs;
+  float hi[32], lo[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  bool ok = true;
+  for (int wi = w0; wi < w1 && ok; ++wi) {
+    const Win w = wins[wi];
+    const float* E = buf + w.base + (int64_t)w.npad * w.npad;
+    const int64_t ld = w.npad;
+    auto rowA = [&](int r) -> const float* { return (r0 + r < se) ? E + (r0 + r) * ld : nullptr; };
+    auto rowB = [&](int c) -> const float* { return (c0 + c < se) ? E + (c0 + c) * ld : nullptr; };
+    ok = comp_product<RB, true>(sm, cs, w.nB, w.n, rowA, rowB, hi, lo);
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int q = warp & 3, half = warp >> 2;
+  const int e1 = r0 + q * 32 + lane;
+  const int cg = c0 + half * 32;
+  if (ok && warp < RB / 8 && e1 < se) {
+    double* P = partial + (int64_t)blockIdx.y * se * se + (int64_t)e1 * se;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (cg + j < se) P[cg + j] = (double)hi[j] + (double)lo[j];
   }
   comp_teardown(sm);
 }
@@ -1124,7 +1197,8 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_rhs_tc(const Pai
     return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
   };
   float hi[32], lo[32];
-  const bool ok = comp_product(sm, ldv, rowA, rowB, hi, lo);
+  CompState cs;
+  const bool ok = comp_product(sm, cs, 0, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int uu = u0 + q * 32 + lane;
