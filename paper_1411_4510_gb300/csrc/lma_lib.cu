@@ -102,6 +102,7 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
     done = true;
   }
@@ -653,7 +654,20 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       }
     }
     T* h = tmp.alloc<T>(U * s);
-    launch("k_pred_accum", k_pred_accum<T>, (unsigned)it_acc.size(), NT, 0, st, pd, iad, mc.wins_d, wbuf, Pbuf, Vu, (int)s, h);
+    if (mc.prec == LMA_MIXED && sizeof(T) == 4 && use_tensor_cores()) {
+      std::vector<int4> it_a;
+      for (const int4& t : tb)
+        for (int ut = 0; ut < (t.w + 127) / 128; ++ut)
+          for (int kt = 0; kt < (s + RB - 1) / RB; ++kt) it_a.push_back(make_int4(t.x, t.y, ut, kt));
+      int4* iat = tmp.alloc<int4>(it_a.size());
+      stage_copy(iat, it_a.data(), sizeof(int4) * it_a.size(), st);
+      launch("k_pred_accum_tc", k_pred_accum_tc, (unsigned)it_a.size(), comp_threads<RB>(), tc_resid_smem(), st, pd,
+             (const int4*)iat, mc.wins_d, (const float*)wbuf, (const float*)Pbuf, (const float*)Vu, (int)s, (float*)h,
+             perr);
+    } else {
+      launch("k_pred_accum", k_pred_accum<T>, (unsigned)it_acc.size(), NT, 0, st, pd, iad, mc.wins_d, wbuf, Pbuf, Vu,
+             (int)s, h);
+    }
     double* t1 = tmp.alloc<double>(U);
     double* t2 = tmp.alloc<double>(U);
     // from here on the global step's results (beta, L^-1 e, L_C^-1) are read
