@@ -217,6 +217,90 @@ __global__ void __launch_bounds__(NT) k_proj(const T* __restrict__ Kds, int64_t 
     }
 }
 
+// The same product with 128 x 128 tiles and an 8 x 8 register block per
+// thread (FP32 FMA in the same k order as k_proj, so the same rounding):
+// Vt[p][i] = sum_{k <= i} Kds[p][k] ET[k][i].  Needs s % 4 == 0 (float4 rows).
+__global__ void __launch_bounds__(256) k_proj128(const float* __restrict__ Kds, int64_t n, int s,
+                                                 const float* __restrict__ ET, float* __restrict__ Vt, int ldo) {
+  constexpr int BM = 128, BK = 8;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BM + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t p0 = (int64_t)blockIdx.y * BM;
+  const int i0 = blockIdx.x * BM;
+  const int K = min(s, i0 + BM);  // ET[k][i] = 0 for k > i
+  // loader mapping: A: row ar = tid / 2 (128 rows), k offset 4 (tid & 1); B: row br = tid / 32 (8 rows), cols 4 (tid & 31)
+  const int ar = tid >> 1, ak = (tid & 1) * 4;
+  const int br = tid >> 5, bc = (tid & 31) * 4;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  auto ldA = [&](int k0) -> float4 {
+    const int64_t p = p0 + ar;
+    const int k = k0 + ak;
+    if (p >= n || k >= K) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = *reinterpret_cast<const float4*>(Kds + p * s + k);
+    if (k + 4 > K) {
+      v.y = (k + 1 < K) ? v.y : 0.f;
+      v.z = (k + 2 < K) ? v.z : 0.f;
+      v.w = 0.f;
+    }
+    return v;
+  };
+  auto ldB = [&](int k0) -> float4 {
+    const int k = k0 + br, i = i0 + bc;
+    if (k >= K || i >= s) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return *reinterpret_cast<const float4*>(ET + (int64_t)k * s + i);  // s % 4 == 0: whole float4 in range
+  };
+  auto stash = [&](int buf, float4 a, float4 b) {
+    As[buf][ak + 0][ar] = a.x;
+    As[buf][ak + 1][ar] = a.y;
+    As[buf][ak + 2][ar] = a.z;
+    As[buf][ak + 3][ar] = a.w;
+    *reinterpret_cast<float4*>(&Bs[buf][br][bc]) = b;
+  };
+  float4 a = ldA(0), b = ldB(0);
+  stash(0, a, b);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) {
+      a = ldA(k0 + BK);
+      b = ldB(k0 + BK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float ra[8], rb[8];
+      *reinterpret_cast<float4*>(ra) = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      *reinterpret_cast<float4*>(ra + 4) = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      *reinterpret_cast<float4*>(rb) = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 8]);
+      *reinterpret_cast<float4*>(rb + 4) = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 8 + 4]);
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(ra[x], rb[y], acc[x][y]);
+    }
+    if (more) {
+      stash(buf ^ 1, a, b);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 8; ++x) {
+    const int64_t p = p0 + ty * 8 + x;
+    if (p >= n) continue;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const int i = i0 + tx * 8 + y;
+      if (i < s) Vt[p * ldo + i] = acc[x][y];
+    }
+  }
+}
+
 // Residual over a window (Section 3): R = Sigma - Q with
 // Sigma = K + sigma_n^2 I and Q = Vt Vt^T, written blanket-first into the
 // window buffer (lower 64x64 tiles; padding rows/columns = identity).

@@ -260,7 +260,11 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   T* Kds = tmp.alloc<T>(n * s);
   launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, xsT, n, (int)d, ssT, (int)s, (T)mc.ss2, Kds);
   T* Vt = mc.keep.alloc<T>(n * s);
-  launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt, (int)s);
+  if (sizeof(T) == 4 && s % 4 == 0)
+    launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(n, 128)), NT, 0, st, (const float*)Kds, n, (int)s,
+           (const float*)ET, (float*)Vt, (int)s);
+  else
+    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt, (int)s);
   mc.Vt = Vt;
 }
 
@@ -535,8 +539,12 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     T* Kus = tmp.alloc<T>(U * s);
     launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s, (T)mc.ss2, Kus);
     T* Vu = tmp.alloc<T>(U * s);
-    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
-           (int)s);
+    if (sizeof(T) == 4 && s % 4 == 0)
+      launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
+             (const float*)mc.ET, (float*)Vu, (int)s);
+    else
+      launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
+             (int)s);
     // pairs (test block n, window m in [n-B, n])
     std::vector<Pair> pairs;
     std::vector<int4> tb;  // per test block: first pair, count, u0, nu
