@@ -919,9 +919,10 @@ struct CompState {
 // Adds sum over k in [kbeg, kend) of A(r,k) B(c,k) to hi + lo (zeroed first
 // unless ACC).  rowA(r) / rowB(c) return a 16-byte-aligned row pointer (or
 // nullptr for a zero row) whose row holds at least kend rounded up to 4
-// values; values outside [kbeg, kend) are masked.  Returns false (in every
+// values; values outside [kbeg, kend) are masked.  MASK = false is for
+// kbeg = 0 and kend a multiple of 32 (nothing to mask).  Returns false (in every
 // thread) when a wait timed out.  hi / lo are only meaningful in workers.
-template <int BN, bool ACC = false, class RA, class RB>
+template <int BN, bool ACC = false, bool MASK = true, class RA, class RB>
 __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend, RA rowA, RB rowB,
                              float (&hi)[32], float (&lo)[32]) {
   using namespace tc;
@@ -959,6 +960,7 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
     };
     float4 ra[NA], rb[NB];
     auto ld4 = [&](const float* src, int kk) -> float4 {
+      if (!MASK) return src ? *reinterpret_cast<const float4*>(src + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
       if (!src || kk >= kend) return make_float4(0.f, 0.f, 0.f, 0.f);
       float4 v = *reinterpret_cast<const float4*>(src + kk);
       if (kk < kbeg || kk + 4 > kend) {
@@ -1084,7 +1086,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* 
   };
   float hi[32], lo[32];
   CompState cs;
-  const bool ok = comp_product(sm, cs, 0, ldv, rowA, rowB, hi, lo);
+  const bool ok = comp_product<RB, false, false>(sm, cs, 0, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int i = r0 + q * 32 + lane;
@@ -1247,7 +1249,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_rhs_tc(const Pai
   };
   float hi[32], lo[32];
   CompState cs;
-  const bool ok = comp_product(sm, cs, 0, ldv, rowA, rowB, hi, lo);
+  const bool ok = comp_product<RB, false, false>(sm, cs, 0, ldv, rowA, rowB, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int uu = u0 + q * 32 + lane;
