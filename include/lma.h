@@ -110,6 +110,17 @@ lma_status lma_predict(const lma_model* model, int64_t u, const double* XU,
                        const int64_t* test_block_ptr, int noisy, int io_on_device,
                        double* mean_out, double* var_out);
 
+/* lma_predict plus the predictive covariance of every test block: for the
+ * test points of block n, Eq. (vapvar) restricted to U_n x U_n (these pairs
+ * are in-band, so Sigma-bar_UU = Sigma_UU there), evaluated by the same local
+ * route as the variance.  cov_out receives the blocks one after the other,
+ * block n as a row-major |U_n| x |U_n| matrix, sum_n |U_n|^2 doubles in
+ * total (host or device memory as io_on_device says, like mean_out and
+ * var_out).  Errors as in lma_predict.                                     */
+lma_status lma_predict_cov(const lma_model* model, int64_t u, const double* XU,
+                           const int64_t* test_block_ptr, int noisy, int io_on_device,
+                           double* mean_out, double* var_out, double* cov_out);
+
 /* lma_fit followed by lma_predict in one call, with the same results: the
  * FP64 global step (Definition 2) runs on a library-owned second stream
  * while the prediction's kernels that do not need its results run on

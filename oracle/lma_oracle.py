@@ -13,6 +13,8 @@ loglik           log N(y_D; mu, Sigma-bar_DD) in summary form:
                  determinant lemma on the same identity; log|R-bar_DD| is the
                  sum of log|R-dot_m^-1| (Lemma 1: R-bar^-1 = U^T U with
                  U_mm^T U_mm = R-dot_m).
+predict_cov()    The same local route for the full covariance of each test
+                 block (Eq. vapvar on U_n x U_n).
 predict_thm2()   Theorem 2 given Sigma-bar_DU (paper's route; tiny N only).
 predict()        Local route: for u in U_n the row R-bar_{uD} R-bar_DD^-1 is
                  supported on the blocks J = n-B..n+B and equals
@@ -284,6 +286,42 @@ def predict(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True,
         var[u] = (prior - np.sum(Wu * Wu, axis=0) - np.sum(Ru * Z, axis=0)
                   + np.sum(hc * hc, axis=0))
     return mean, var
+
+
+def predict_cov(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True, blocks=None) -> list:
+    """Predictive covariance of each test block U_n (Eq. vapvar restricted to
+    U_n x U_n, where Sigma-bar_UU = Sigma_UU since the pairs are in-band), by
+    the local route of predict():
+        Cov_n = Sigma_{U_n U_n} - W_u^T W_u - R_{D_J u}^T (R-bar_JJ)^-1 R_{D_J u}
+                + hc^T hc.
+    Returns one |U_n| x |U_n| matrix per test block (None for empty blocks
+    and blocks not asked for)."""
+    p = f.prob
+    XU = p.XU if XU is None else XU
+    tptr = p.test_block_ptr if test_block_ptr is None else test_block_ptr
+    cv = _Cov(p)
+    ptr = p.block_ptr
+    M = len(ptr) - 1
+    B = f.B
+    out = [None] * M
+    it = range(M) if blocks is None else blocks
+    for n in it:
+        u = np.arange(tptr[n], tptr[n + 1])
+        if u.size == 0:
+            continue
+        Jb = list(range(max(0, n - B), min(M - 1, n + B) + 1))
+        rows, P = _subchain_precision(cv, ptr, Jb, B)
+        Xu = XU[u]
+        XJ = p.X[rows]
+        Wu = cv.W(Xu)
+        WJ = cv.W(XJ)
+        Ru = cv.K(XJ, Xu) - WJ.T @ Wu
+        Z = P @ Ru
+        h = WJ @ Z - Wu
+        hc = sla.solve_triangular(f.Lc, h, lower=True)
+        Kuu = cv.K(Xu, Xu) + (cv.sn2 * np.eye(u.size) if noisy else 0.0)
+        out[n] = Kuu - Wu.T @ Wu - Ru.T @ Z + hc.T @ hc
+    return out
 
 
 def predict_thm2(f: LMAFit, Sigmabar_DU: np.ndarray, Sigma_UU_diag: np.ndarray):

@@ -120,6 +120,35 @@ def lma_predict(model: Model, XU, test_block_ptr, noisy: bool = True, out=None):
     return mean, var
 
 
+def lma_predict_cov(model: Model, XU, test_block_ptr, noisy: bool = True):
+    """(mean, var, covs): covs[n] is the |U_n| x |U_n| predictive covariance of
+    test block n (None for empty blocks); numpy for host input, torch CUDA
+    tensors for device input."""
+    lib = _abi.load()
+    keep = []
+    u = int(XU.shape[0])
+    xp, dev = _f64(XU, keep)
+    tp = np.asarray(test_block_ptr, dtype=np.int64)
+    tpp = _i64(tp, keep)
+    sizes = np.diff(tp)
+    total = int(np.sum(sizes * sizes))
+    if dev:
+        mean = torch.empty(u, dtype=torch.float64, device=XU.device)
+        var = torch.empty(u, dtype=torch.float64, device=XU.device)
+        cov = torch.empty(max(total, 1), dtype=torch.float64, device=XU.device)
+        ptrs = mean.data_ptr(), var.data_ptr(), cov.data_ptr()
+    else:
+        mean, var, cov = np.empty(u), np.empty(u), np.empty(max(total, 1))
+        ptrs = mean.ctypes.data, var.ctypes.data, cov.ctypes.data
+    _abi.check(lib.lma_predict_cov(model.handle, u, xp, tpp, int(bool(noisy)), int(dev), *ptrs))
+    covs, off = [], 0
+    for k in sizes:
+        k = int(k)
+        covs.append(cov[off:off + k * k].reshape(k, k) if k else None)
+        off += k * k
+    return mean, var, covs
+
+
 def lma_fit_predict(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, XU, test_block_ptr, jitter=1e-6,
                     mean=0.0, precision=MIXED, noisy: bool = True, stream=None, keep_model: bool = False):
     """lma_fit + lma_predict in one call (the global step overlaps the

@@ -958,6 +958,94 @@ __global__ void __launch_bounds__(NT) k_var_gemm(const T* __restrict__ h, int64_
   }
 }
 
+// g_u = L_C^-1 h_u for the block covariance: g[u][i] = sum_k h[u][k] LcT[k][i]
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lc_apply(const T* __restrict__ h, int64_t U, int s, const T* __restrict__ LcT,
+                                                 T* __restrict__ g) {
+  __shared__ GemmSmem<T> sm;
+  const int64_t u0 = (int64_t)blockIdx.y * TB;
+  const int i0 = blockIdx.x * TB;
+  const int K = min(s, i0 + TB);
+  T acc[4][4] = {};
+  auto fa = [&](int r, int k) -> T { return (u0 + r < U) ? h[(u0 + r) * s + k] : T(0); };
+  auto fb = [&](int r, int k) -> T { return (i0 + r < s) ? LcT[(int64_t)k * s + i0 + r] : T(0); };
+  tile_mma<T, true, false>(acc, K, sm, fa, fb);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t u = u0 + ty + 16 * a;
+      const int i = i0 + tx + 16 * b;
+      if (u < U && i < s) g[u * s + i] = acc[a][b];
+    }
+}
+
+// Predictive covariance of test block n (Eq. vapvar on U_n x U_n, local
+// route): Cov(u, u') = K(u, u') [+ sigma_n^2 delta] - Vu_u . Vu_u'
+//   - sum over the block's pairs of P_u . P_u' (kept window columns)
+//   + g_u . g_u'  (g = L_C^-1 h).  Items: x = first pair of the block,
+// y = pair count, z / w = 64-row tiles of the block; cov_off[n] is the
+// block's offset in the packed output (row-major |U_n| x |U_n|).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_pred_cov(const Pair* __restrict__ pairs, const int4* __restrict__ items,
+                                                 const Win* __restrict__ wins, const T* __restrict__ xu, int d,
+                                                 const T* __restrict__ Vu, const T* __restrict__ P,
+                                                 const T* __restrict__ g, int s, double ss2, double noise,
+                                                 const int64_t* __restrict__ cov_off, double* __restrict__ cov) {
+  const int4 it = items[blockIdx.x];
+  const Pair first = pairs[it.x];
+  const int a0 = it.z * TB, b0 = it.w * TB, nu = first.nu;
+  const int64_t ub = first.u0;
+  __shared__ GemmSmem<T> sm;
+  __shared__ T xa[TB][MAXD + 1];
+  __shared__ T xb[TB][MAXD + 1];
+  for (int e = threadIdx.x; e < TB * d; e += NT) {
+    const int r = e / d, q = e % d;
+    xa[r][q] = (a0 + r < nu) ? xu[(ub + a0 + r) * d + q] : T(0);
+    xb[r][q] = (b0 + r < nu) ? xu[(ub + b0 + r) * d + q] : T(0);
+  }
+  T sub[4][4] = {}, add[4][4] = {};
+  {
+    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? Vu[(ub + a0 + r) * s + k] : T(0); };
+    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? Vu[(ub + b0 + r) * s + k] : T(0); };
+    tile_mma<T, true, true>(sub, s, sm, fa, fb);
+  }
+  for (int pi = 0; pi < it.y; ++pi) {
+    const Pair pr = pairs[it.x + pi];
+    const Win w = wins[pr.win];
+    const T* Pp = P + pr.pbase;
+    const int64_t ld = w.npad;
+    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? Pp[(int64_t)(a0 + r) * ld + pr.c0 + k] : T(0); };
+    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? Pp[(int64_t)(b0 + r) * ld + pr.c0 + k] : T(0); };
+    tile_mma<T, true, true>(sub, pr.c1 - pr.c0, sm, fa, fb);
+  }
+  {
+    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? g[(ub + a0 + r) * s + k] : T(0); };
+    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? g[(ub + b0 + r) * s + k] : T(0); };
+    tile_mma<T, true, true>(add, s, sm, fa, fb);
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double* C = cov + cov_off[first.n];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      const int i = a0 + r, j = b0 + c;
+      if (i < nu && j < nu) {
+        double d2 = 0.0;
+        for (int q = 0; q < d; ++q) {
+          const double t = (double)xa[r][q] - (double)xb[c][q];
+          d2 += t * t;
+        }
+        double v = ss2 * exp(-0.5 * d2) - (double)sub[a][b] + (double)add[a][b];
+        if (i == j) v += noise;
+        C[(int64_t)i * nu + j] = v;
+      }
+    }
+}
+
 // mean_u = mu + Vu_u . beta + t1_u ; var_u = sigma_s^2 [+ sigma_n^2] - |Vu_u|^2 - t2_u + |L_C^-1 h_u|^2
 template <typename T>
 __global__ void k_pred_final(const T* __restrict__ Vu, int64_t U, int s, const double* __restrict__ beta,

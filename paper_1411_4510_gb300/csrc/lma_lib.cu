@@ -517,7 +517,7 @@ void Impl<T>::fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* 
 
 template <typename T>
 void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
-                      double* mean, double* var, cudaEvent_t global_done) {
+                      double* mean, double* var, cudaEvent_t global_done, double* cov) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -692,6 +692,32 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     }
     const double prior = mc.ss2 + (noisy ? mc.sn2 : 0.0);
     launch("k_pred_final", k_pred_final<T>, nblk(U * 32), NT, 0, st, Vu, U, (int)s, mc.beta, t1, t2, part, nst, mc.mu, prior, md, vd);
+    if (cov) {  // covariance of each test block, packed row-major block after block
+      std::vector<int64_t> off(M, 0);
+      std::vector<int4> it_c;
+      int64_t total = 0;
+      for (const int4& t : tb) {
+        const Pair& f = pairs[t.x];
+        off[f.n] = total;
+        total += (int64_t)t.w * t.w;
+        const int nt = (t.w + TB - 1) / TB;
+        for (int a = 0; a < nt; ++a)
+          for (int b = 0; b < nt; ++b) it_c.push_back(make_int4(t.x, t.y, a, b));
+      }
+      T* g = tmp.alloc<T>(U * s);
+      launch("k_lc_apply", k_lc_apply<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const T*)h, U, (int)s,
+             (const T*)mc.LcT, g);
+      int64_t* offd = tmp.alloc<int64_t>(M);
+      int4* icd = tmp.alloc<int4>(it_c.size());
+      stage_copy(offd, off.data(), sizeof(int64_t) * M, st);
+      stage_copy(icd, it_c.data(), sizeof(int4) * it_c.size(), st);
+      double* cd = on_device ? cov : tmp.alloc<double>(total);
+      if (!it_c.empty())
+        launch("k_pred_cov", k_pred_cov<T>, (unsigned)it_c.size(), NT, 0, st, pd, (const int4*)icd, mc.wins_d,
+               (const T*)xu, d, (const T*)Vu, (const T*)Pbuf, (const T*)g, (int)s, mc.ss2, noisy ? mc.sn2 : 0.0,
+               (const int64_t*)offd, cd);
+      if (!on_device && total) LMA_CK(cudaMemcpyAsync(cov, cd, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+    }
     if (!on_device) {
       LMA_CK(cudaMemcpyAsync(mean, md, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
       LMA_CK(cudaMemcpyAsync(var, vd, sizeof(double) * U, cudaMemcpyDeviceToHost, st));

@@ -189,3 +189,26 @@ def test_toy_appendix_d():
         slope = (mean[i + 1] - mean[i - 2]) / (x[i + 1] - x[i - 2])
         jump = abs((mean[i] - mean[i - 1]) - slope * (x[i] - x[i - 1]))
         assert jump < 0.1 * sn, (b, jump)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("noisy", [True, False])
+def test_block_covariance_equals_dense(case, noisy):
+    """Eq. (vapvar) on each test block U_n x U_n: the local route's block
+    covariance equals the dense definition's diagonal blocks, and its
+    diagonal equals the local-route variance."""
+    p = _p(*case)
+    f = O2.fit(p)
+    d = O1.lma_dense(p, noisy=noisy)
+    covs = O2.predict_cov(f, noisy=noisy)
+    _, var = O2.predict(f, noisy=noisy)
+    tp = p.test_block_ptr
+    for n, C in enumerate(covs):
+        u = np.arange(tp[n], tp[n + 1])
+        if u.size == 0:
+            assert C is None
+            continue
+        ref = d["cov"][np.ix_(u, u)]
+        assert np.allclose(C, ref, rtol=1e-9, atol=1e-11)
+        assert np.allclose(np.diag(C), var[u], rtol=1e-12, atol=1e-13)
+        assert np.allclose(C, C.T, rtol=0, atol=1e-12)
