@@ -812,9 +812,12 @@ __global__ void __launch_bounds__(256, 2) k_pred_sweep_tc(const Pair* __restrict
     }
     if (live) {
       float* dst = myrow + k0 + half * 32;
+      float4 av[8];  // all loads first: they are independent of the stores below
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(dst + 4 * j4);
 #pragma unroll
       for (int j4 = 0; j4 < 8; ++j4) {
-        float4 a = *reinterpret_cast<const float4*>(dst + 4 * j4);
+        float4 a = av[j4];
         a.x -= v[4 * j4 + 0];
         a.y -= v[4 * j4 + 1];
         a.z -= v[4 * j4 + 2];
