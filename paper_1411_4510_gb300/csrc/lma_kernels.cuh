@@ -413,8 +413,11 @@ struct CholSmem {
 template <typename T, int N = TB>
 __device__ void diag_factor(T (*D)[N + 1], T* Lout, int64_t ld, T* Dv, int* info, int k0) {
   constexpr int NQ = N / 4;
-  __shared__ T colb[2][N];
-  __shared__ T xrow[2][N];
+  constexpr int VW = 16 / sizeof(T);  // values per 16-byte shared-memory load
+  // published column j and inverse row j, stored phase-major: element
+  // p + 4 q at [p][q], so a thread reads its NQ values with 16-byte loads
+  __shared__ __align__(16) T colb[2][4][NQ];
+  __shared__ __align__(16) T xrow[2][4][NQ];
   __shared__ T rjs[2];
   const int t = threadIdx.x, rr = t >> 2, p = t & 3;
   const bool act = t < 4 * N;
@@ -429,14 +432,14 @@ __device__ void diag_factor(T (*D)[N + 1], T* Lout, int64_t ld, T* Dv, int* info
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     const int qj = j >> 2, pj = j & 3;
-    T* cb = colb[j & 1];
-    T* xb = xrow[j & 1];
+    T(*cb)[NQ] = colb[j & 1];
+    T(*xb)[NQ] = xrow[j & 1];
     if (act && rr >= j) {
-      if (p == pj) cb[rr] = d[qj];
+      if (p == pj) cb[rr & 3][rr >> 2] = d[qj];
       if (rr == j) {
 #pragma unroll
         for (int q = 0; q <= qj; ++q)
-          if (p + 4 * q <= j) xb[p + 4 * q] = x[q];
+          if (p + 4 * q <= j) xb[p][q] = x[q];
         if (p == pj) {
           T piv = d[qj];
           if (!(piv > T(0))) {
@@ -455,19 +458,25 @@ __device__ void diag_factor(T (*D)[N + 1], T* Lout, int64_t ld, T* Dv, int* info
 #pragma unroll
       for (int q = 0; q <= qj; ++q) x[q] *= rj;
     } else if (act && rr > j) {
-      const T lr = cb[rr];
+      const T lr = cb[rr & 3][rr >> 2];
       const T l = lr * rj;
       const T a = l * rj;
       if (p == pj) D[rr][j] = l;
+      T cv[NQ], xv[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; q += VW) {
+        *reinterpret_cast<float4*>(&cv[q]) = *reinterpret_cast<const float4*>(&cb[p][q]);
+        *reinterpret_cast<float4*>(&xv[q]) = *reinterpret_cast<const float4*>(&xb[p][q]);
+      }
 #pragma unroll
       for (int q = qj; q < NQ; ++q) {
         const int cc = p + 4 * q;
-        if (cc > j && cc <= rr) d[q] = fma(-a, cb[cc], d[q]);
+        if (cc > j && cc <= rr) d[q] = fma(-a, cv[q], d[q]);
       }
 #pragma unroll
       for (int q = 0; q <= qj; ++q) {
         const int c = p + 4 * q;
-        if (c <= j) x[q] = fma(-a, xb[c], x[q]);
+        if (c <= j) x[q] = fma(-a, xv[q], x[q]);
       }
     }
   }
