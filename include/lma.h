@@ -270,6 +270,15 @@ lma_status lma_global_step_noalloc(int64_t s, int64_t n, const double* A, const 
 void lma_profile_start(const char* name_filter);
 int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* launches, int cap);
 
+/* Per-launch trace of the records made since lma_profile_start (call before
+ * lma_profile_stop, which discards them).  For record i < min(count, cap),
+ * t0_ms[i] / t1_ms[i] are its start / end events' times in milliseconds
+ * after the first record's start event (events on different streams of one
+ * device share that clock), and names holds the records' kernel names in
+ * order, newline-separated (names_cap bytes, NUL-terminated, may be NULL).
+ * Waits for the recorded events; returns the number of records.           */
+int lma_profile_trace(char* names, int names_cap, double* t0_ms, double* t1_ms, int cap);
+
 #ifdef __cplusplus
 }
 #endif

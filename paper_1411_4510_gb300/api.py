@@ -303,6 +303,18 @@ def profile_start(name_filter: str = "") -> None:
     _abi.load().lma_profile_start(name_filter.encode())
 
 
+def profile_trace(cap: int = 4096) -> list:
+    """[(kernel name, start ms, end ms)] of every launch recorded since
+    profile_start, relative to the first one (call before profile_stop)."""
+    lib = _abi.load()
+    names = C.create_string_buffer(64 * cap)
+    t0 = np.zeros(cap)
+    t1 = np.zeros(cap)
+    k = lib.lma_profile_trace(names, 64 * cap, t0.ctypes.data, t1.ctypes.data, cap)
+    keys = names.value.decode().split("\n")
+    return [(keys[i], float(t0[i]), float(t1[i])) for i in range(min(k, cap, len(keys)))]
+
+
 def profile_stop() -> dict:
     """{kernel name: (total milliseconds, launches)} since profile_start."""
     lib = _abi.load()

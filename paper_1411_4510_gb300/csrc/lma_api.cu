@@ -439,6 +439,30 @@ void lma_profile_start(const char* name_filter) {
   prof::g_recs.clear();
 }
 
+int lma_profile_trace(char* names, int names_cap, double* t0_ms, double* t1_ms, int cap) {
+  std::string all;
+  const int k = (int)prof::g_recs.size();
+  for (int i = 0; i < k; ++i) {
+    const prof::Rec& r = prof::g_recs[i];
+    cudaEventSynchronize(r.b);
+    if (i < cap) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, prof::g_recs[0].a, r.a);
+      cudaEventElapsedTime(&b, prof::g_recs[0].a, r.b);
+      if (t0_ms) t0_ms[i] = a;
+      if (t1_ms) t1_ms[i] = b;
+    }
+    all += r.name;
+    all += "\n";
+  }
+  if (names && names_cap > 0) {
+    size_t n = all.size() < (size_t)(names_cap - 1) ? all.size() : (size_t)(names_cap - 1);
+    memcpy(names, all.data(), n);
+    names[n] = 0;
+  }
+  return k;
+}
+
 int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* launches, int cap) {
   prof::g_on = false;
   std::map<std::string, std::pair<double, int64_t>> agg;

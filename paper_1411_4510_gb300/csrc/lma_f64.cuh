@@ -69,6 +69,8 @@ __device__ __forceinline__ void solve_tile(double (*out)[TS + 1], const double (
 // factorised inside k_f64_panel).
 __global__ void __launch_bounds__(NTH) k_f64_potrf(double* __restrict__ buf, int64_t ld, int kp,
                                                    double* __restrict__ dinv, int* __restrict__ info) {
+  grid_dep_wait();
+  grid_dep_launch();
   __shared__ double D[TS][TS + 1];
   double* A = buf + (int64_t)kp * TS * ld + kp * TS;
   load_tile(D, A, ld, 0, 0, TS);
@@ -81,6 +83,8 @@ __global__ void __launch_bounds__(NTH) k_f64_potrf(double* __restrict__ buf, int
 // [t2, t2 + nrt - kp) deferred solves of row tiles kp .. nrt - 1 of panel kp - 1.
 __global__ void __launch_bounds__(NTH) k_f64_panel(double* __restrict__ buf, int64_t ld, int rows, int npan, int kp,
                                                    int nid, double* __restrict__ dinv, int* __restrict__ info) {
+  grid_dep_wait();
+  grid_dep_launch();
   const int nrt = (rows + TS - 1) / TS, napp = nrt - npan;
   const int m = npan - kp - 1;  // trailing panels (may be <= 0)
   const int t1 = m > 0 ? m * (m + 1) / 2 : 0;

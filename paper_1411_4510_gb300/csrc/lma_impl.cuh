@@ -88,6 +88,35 @@ inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 blo
   }
 }
 
+// launch() with programmatic stream serialisation: the kernel may become
+// resident while its predecessor in the stream still runs, which hides the
+// launch latency of long chains of short dependent launches (the panel steps
+// of the factorisations).  Only for kernels that call grid_dep_wait() first.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  const bool p = prof::active(name);
+  if (p) prof::start(name, st);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+  count_launch();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (p) prof::stop(st);
+  if (e != cudaSuccess) {
+    fail(LMA_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    throw Fail{};
+  }
+}
+
 inline int64_t roundup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // Page-locked staging for the small index tables a call uploads (window

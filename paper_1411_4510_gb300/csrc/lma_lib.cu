@@ -134,15 +134,15 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
         const int kb = (k0 / SP) * SP;
         if (k0 == kb && kb > 0) {
           const unsigned gy = (unsigned)((maxrows - kb + 127) / 128);
-          launch("k_chol_wide", k_chol_wide, dim3(nw, gy), tc::kWsThreads, wide_smem(), st, wins_d, (float*)buf, kb,
+          launch_pdl("k_chol_wide", k_chol_wide, dim3(nw, gy), tc::kWsThreads, wide_smem(), st, wins_d, (float*)buf, kb,
                  tc_err);
         }
         const unsigned gy = (unsigned)((maxrows - k0 + 127) / 128);
-        launch("k_chol_step_tc", k_chol_step_tc, dim3(nw, gy), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+        launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, gy), 256, tc_chol_smem(), st, wins_d, (float*)buf,
                (float*)dinv, info, kp, kb, tc_err);
         if (maxrows - (kp + 1) * TB > 0) {
           const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
-          launch("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+          launch_pdl("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
                  (const float*)dinv, kp, tc_err);
         }
       } else {
@@ -177,13 +177,13 @@ static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* b
   using namespace f64;
   const int npan = w.npad / TS, nrt = (w.rows + TS - 1) / TS;
   const int64_t ld = w.npad;
-  launch("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
+  launch_pdl("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
   for (int kp = 0; kp <= npan; ++kp) {
     const int m = npan - kp - 1;
     const int trail = m > 0 ? m * (m + 1) / 2 + (nrt - npan) * m : 0;
     const int solve = kp >= 1 ? nrt - kp : 0;
     if (trail + solve > 0)
-      launch("k_f64_panel", k_f64_panel, (unsigned)(trail + solve), NTH, 0, st, buf, ld, w.rows, npan, kp, nid, dv,
+      launch_pdl("k_f64_panel", k_f64_panel, (unsigned)(trail + solve), NTH, 0, st, buf, ld, w.rows, npan, kp, nid, dv,
              info);
   }
 }

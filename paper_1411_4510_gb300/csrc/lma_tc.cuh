@@ -380,6 +380,8 @@ namespace lma {
 __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
                                                       int kb, int* __restrict__ err) {
+  grid_dep_wait();
+  grid_dep_launch();
   using namespace tc;
   const Win w = wins[blockIdx.x];
   const int k0 = kp * TB;
@@ -636,6 +638,8 @@ __device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
 __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __restrict__ wins,
                                                                 float* __restrict__ buf, int s0,
                                                                 int* __restrict__ err) {
+  grid_dep_wait();
+  grid_dep_launch();
   using namespace tc;
   const Win w = wins[blockIdx.x];
   if (s0 >= w.npad) return;
@@ -698,6 +702,8 @@ namespace lma {
 // read into shared memory before any result is written back.
 __global__ void __launch_bounds__(256, 2) k_chol_trsm_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       const float* __restrict__ dinv, int kp, int* __restrict__ err) {
+  grid_dep_wait();
+  grid_dep_launch();
   using namespace tc;
   const Win w = wins[blockIdx.y];
   const int k0 = kp * TB;

@@ -10,6 +10,17 @@ constexpr int NT = 256;    // threads per CTA
 constexpr int KS = 16;     // K step of the SIMT tile product
 constexpr int MAXD = 24;   // largest input dimension held in shared memory
 
+// Programmatic dependent launch.  A kernel started with programmatic stream
+// serialisation (launch_pdl) may become resident while the kernel before it
+// in the stream is still running.  grid_dep_wait() returns once that kernel
+// has completed and its writes are visible (at once when the launch had no
+// such predecessor), so it must come before anything that reads or writes
+// the predecessor's data; every kernel launched through launch_pdl calls it
+// first.  grid_dep_launch() allows the next kernel in the stream to start
+// launching; the dependent still waits in its own grid_dep_wait().
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // One factorisation problem ("window").  The window of block m is
 // D_m u D^B_m (Section 3) stored in REVERSED row order: local row i is the
 // global training row g_end-1-i, so the blanket D^B_m comes first and block
