@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lma_impl.cuh"
 #include "lma_kernels.cuh"
 #include "lma_grad.cuh"
@@ -70,6 +72,61 @@ Staging& staging() {
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
+static size_t split_smem_bytes() { return sizeof(SplitSmem) + tc::kTcAlignSlack; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a row-major FP32 matrix (rows x cols, cols a multiple of 32,
+// 16-byte-aligned base): 32 x 128 boxes with the 128-byte swizzle the MMA
+// descriptors expect; rows outside [0, rows) read zero.
+static CUtensorMap rows_tensor_map(const float* base, int64_t rows, int cols) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    throw Fail{};
+  }
+  CUtensorMap m;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * sizeof(float)};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    throw Fail{};
+  }
+  return m;
+}
+
+// TF32 hi/lo halves (k_split_tf32) of the point-major rows of V (n x s) with
+// the row length padded to ld = s rounded up to 32 (zero pad), reversed or not.
+static void split_rows(cudaStream_t st, const float* V, int64_t n, int64_t s, int ld, bool reverse, float* hi,
+                       float* lo, Arena& tmp) {
+  const float* src = V;
+  if (ld != s) {
+    float* pad = tmp.alloc<float>((size_t)n * ld);
+    LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * ld, st));
+    LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * ld, V, sizeof(float) * s, sizeof(float) * s, n,
+                             cudaMemcpyDeviceToDevice, st));
+    src = pad;
+  }
+  launch("k_split_tf32", k_split_tf32, nblk(n * (ld / 4)), NT, 0, st, src, n, ld, reverse ? 1 : 0, hi, lo);
+}
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
 // SIMT kernels instead (used to compare the two on the same build).
@@ -99,8 +156,8 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
-    cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
-    cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
@@ -309,16 +366,14 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     const T* xsT = (const T*)mc.xsT;
     const unsigned et = nblk(s + 1, TB);
     if (batched && sizeof(T) == 4 && use_tensor_cores()) {
-      // residual tiles on the tensor cores; V with a row stride padded to 32
+      // residual tiles on the tensor cores, fed by TMA from the TF32 halves
+      // of V (row length padded to 32) in reversed point order
       const int sp = (int)roundup(s, 32);
-      const float* Vtp = (const float*)Vt;
-      if (sp != s) {
-        float* pad = tmp.alloc<float>((size_t)n * sp);
-        LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * sp, st));
-        LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * sp, Vt, sizeof(float) * s, sizeof(float) * s, n,
-                                 cudaMemcpyDeviceToDevice, st));
-        Vtp = pad;
-      }
+      mc.ldvs = sp;
+      mc.vhi = mc.keep.alloc<float>((size_t)n * sp);
+      mc.vlo = mc.keep.alloc<float>((size_t)n * sp);
+      split_rows(st, (const float*)Vt, n, s, sp, true, mc.vhi, mc.vlo, tmp);
+      const CUtensorMap vh = rows_tensor_map(mc.vhi, n, sp), vl = rows_tensor_map(mc.vlo, n, sp);
       std::vector<int4> items;
       for (int64_t m = 0; m < M; ++m) {
         const int np = mc.wins[m].npad;
@@ -328,8 +383,9 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), comp_threads<RB>(), tc_resid_smem(), st, (const int4*)itd, wd,
-             (const float*)xsT, d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), kSplitThreads, split_smem_bytes(), st,
+             (const int4*)itd, wd, (const float*)xsT, d, vh, vl, (int)n, sp / 32, (float)mc.ss2, (float)mc.sn2,
+             (float*)wbuf, rerr);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
     } else if (batched) {
       launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
@@ -604,22 +660,21 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     if (mc.prec == LMA_MIXED) {
       const bool tc = (sizeof(T) == 4 && use_tensor_cores());
       if (tc) {
-        // right-hand sides on the tensor cores; V rows with a stride padded to 32
+        // right-hand sides on the tensor cores, fed by TMA from the TF32
+        // halves of Vu (test order) and of Vt (reversed point order)
         const int sp = (int)roundup(s, 32);
-        const float* Vtp = (const float*)Vt;
-        const float* Vup = (const float*)Vu;
-        if (sp != s) {
-          float* a = tmp.alloc<float>((size_t)mc.n * sp);
-          float* b = tmp.alloc<float>((size_t)U * sp);
-          LMA_CK(cudaMemsetAsync(a, 0, sizeof(float) * mc.n * sp, st));
-          LMA_CK(cudaMemsetAsync(b, 0, sizeof(float) * U * sp, st));
-          LMA_CK(cudaMemcpy2DAsync(a, sizeof(float) * sp, Vt, sizeof(float) * s, sizeof(float) * s, mc.n,
-                                   cudaMemcpyDeviceToDevice, st));
-          LMA_CK(cudaMemcpy2DAsync(b, sizeof(float) * sp, Vu, sizeof(float) * s, sizeof(float) * s, U,
-                                   cudaMemcpyDeviceToDevice, st));
-          Vtp = a;
-          Vup = b;
+        float* vhi = mc.vhi;
+        float* vlo = mc.vlo;
+        if (!vhi || mc.ldvs != sp) {
+          vhi = tmp.alloc<float>((size_t)mc.n * sp);
+          vlo = tmp.alloc<float>((size_t)mc.n * sp);
+          split_rows(st, (const float*)Vt, mc.n, s, sp, true, vhi, vlo, tmp);
         }
+        float* uhi = tmp.alloc<float>((size_t)U * sp);
+        float* ulo = tmp.alloc<float>((size_t)U * sp);
+        split_rows(st, (const float*)Vu, U, s, sp, false, uhi, ulo, tmp);
+        const CUtensorMap vh = rows_tensor_map(vhi, mc.n, sp), vl = rows_tensor_map(vlo, mc.n, sp);
+        const CUtensorMap uh = rows_tensor_map(uhi, U, sp), ul = rows_tensor_map(ulo, U, sp);
         std::vector<int4> it_r;
         for (size_t pi = 0; pi < pairs.size(); ++pi) {
           const int nct = (mc.wins[pairs[pi].win].npad + RB - 1) / RB;
@@ -628,8 +683,9 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
         stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), comp_threads<RB>(), tc_resid_smem(), st, pd, (const int4*)irr,
-               mc.wins_d, (const float*)xs, (const float*)xu, d, Vtp, Vup, sp, (float)mc.ss2, (float*)Pbuf, perr);
+        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), kSplitThreads, split_smem_bytes(), st, pd,
+               (const int4*)irr, mc.wins_d, (const float*)xs, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n,
+               sp / 32, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
                (int)s, (T)mc.ss2, Pbuf);
@@ -758,22 +814,23 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
     if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
       const int64_t s = mc.s, n = mc.n;
       const int sp = (int)roundup(s, 32);
-      const float* Vtp = (const float*)mc.Vt;
-      if (sp != s) {
-        float* pad = tmp.alloc<float>((size_t)n * sp);
-        LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * sp, st));
-        LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * sp, mc.Vt, sizeof(float) * s, sizeof(float) * s, n,
-                                 cudaMemcpyDeviceToDevice, st));
-        Vtp = pad;
+      float* vhi = mc.vhi;
+      float* vlo = mc.vlo;
+      if (!vhi || mc.ldvs != sp) {
+        vhi = tmp.alloc<float>((size_t)n * sp);
+        vlo = tmp.alloc<float>((size_t)n * sp);
+        split_rows(st, (const float*)mc.Vt, n, s, sp, true, vhi, vlo, tmp);
       }
+      const CUtensorMap vh = rows_tensor_map(vhi, n, sp), vl = rows_tensor_map(vlo, n, sp);
       std::vector<int4> items;
       for (int I = 0; I * 128 < w.npad; ++I)
         for (int J = 0; J * RB < w.npad && J * RB <= 128 * I + 127; ++J) items.push_back(make_int4(0, I, J, 0));
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), comp_threads<RB>(), tc_resid_smem(), st, (const int4*)itd, wd,
-             (const float*)mc.xsT, (int)mc.d, Vtp, sp, (float)mc.ss2, (float)mc.sn2, (float*)buf, rerr);
+      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), kSplitThreads, split_smem_bytes(), st,
+             (const int4*)itd, wd, (const float*)mc.xsT, (int)mc.d, vh, vl, (int)n, sp / 32, (float)mc.ss2,
+             (float)mc.sn2, (float*)buf, rerr);
     } else {
       launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,
              (const T*)mc.Vt, (int)mc.s, (T)mc.ss2, (T)mc.sn2, buf);

@@ -8,6 +8,7 @@
 // FP32 tensor memory (the published "3xTF32" technique), which keeps about
 // 22 bits of every product.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,6 +46,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// ---- TMA ---------------------------------------------------------------------
+// 2-D tiled load of the box at (x = column, y = row) of `map` into shared
+// memory; completion is counted in bytes on *bar.  x * 4 bytes must be a
+// multiple of 16; y may be negative or past the end (those rows read zero).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // ---- fences ----------------------------------------------------------------
@@ -1062,45 +1078,226 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
   return __syncthreads_and(w && !*abort_flag) != 0;
 }
 
+// ---------------------------------------------------------------------------
+// Compensated product with pre-split operands fed by TMA.  The TF32 hi/lo
+// halves of both operands are in global memory (k_split_tf32), so a
+// 128 x 128 output tile costs no conversion work on the SM: one producer
+// thread loads each 32-wide K chunk (four 128 x 32 boxes, 64 KB) into a ring
+// of kSplitStages stages, one thread issues the chunk's 12 MMAs
+// (hi.hi + hi.lo + lo.hi per 8-wide K step) into one of two tensor-memory
+// accumulators, and 16 worker warps drain each chunk's accumulator into
+// (hi, lo) with TwoSum while the next chunk is multiplied.  Products, chunk
+// sums and their rounding are exactly those of comp_product.
+constexpr int kSplitStages = 3;
+constexpr int kSplitWorkers = 16;                        // 4 lane quarters x 4 groups of 32 columns
+constexpr int kSplitThreads = 32 * (kSplitWorkers + 2);  // + MMA warp + TMA warp
+struct SplitSmem {
+  tc::TcStage<128> st[kSplitStages];
+  uint64_t full[kSplitStages], empty[kSplitStages], done[2], drained[2], fin;
+  uint32_t tmem;
+  int abort;
+};
+__device__ __forceinline__ SplitSmem& split_smem(unsigned char* raw) {
+  uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+  p = (p + 1023) & ~uintptr_t(1023);
+  return *reinterpret_cast<SplitSmem*>(p);
+}
+
+// TF32 hi/lo halves of a point-major FP32 matrix (n rows of ld values, ld a
+// multiple of 4), rounded as store_split4 rounds them: hi = tf32(x),
+// lo = tf32(x - hi).  reverse != 0 stores row p at row n - 1 - p: the rows
+// of a window (training points in reverse) are then consecutive.
+__global__ void k_split_tf32(const float* __restrict__ V, int64_t n, int ld, int reverse, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+  const int l4 = ld >> 2;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n * l4) return;
+  const int64_t p = q / l4, c = q - p * l4;
+  const float4 v = reinterpret_cast<const float4*>(V)[q];
+  float4 h, l;
+  h.x = tc::tf32_round(v.x); l.x = tc::tf32_round(v.x - h.x);
+  h.y = tc::tf32_round(v.y); l.y = tc::tf32_round(v.y - h.y);
+  h.z = tc::tf32_round(v.z); l.z = tc::tf32_round(v.z - h.z);
+  h.w = tc::tf32_round(v.w); l.w = tc::tf32_round(v.w - h.w);
+  const int64_t o = (reverse ? n - 1 - p : p) * l4 + c;
+  reinterpret_cast<float4*>(hi)[o] = h;
+  reinterpret_cast<float4*>(lo)[o] = l;
+}
+
+__device__ __forceinline__ void split_setup(SplitSmem& sm) {
+  using namespace tc;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSplitStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&sm.done[a], 1);
+      mbar_init(&sm.drained[a], kSplitWorkers);
+    }
+    mbar_init(&sm.fin, 1);
+    sm.abort = 0;
+    mbar_fence_init();
+  }
+  if ((threadIdx.x >> 5) == kSplitWorkers) tmem_alloc(&sm.tmem, 256);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+__device__ __forceinline__ void split_teardown(SplitSmem& sm) {
+  using namespace tc;
+  fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == kSplitWorkers) tmem_dealloc(sm.tmem, 256);
+}
+
+// hi + lo = sum over k < 32 nchunk of A(r, k) B(c, k) with A rows
+// [ya, ya + 128) of (ahi, alo) and B rows [yb, yb + 128) of (bhi, blo) (rows
+// outside the maps read zero); worker warp w holds row 32 (w mod 4) + lane,
+// columns 32 (w / 4) + j in hi[j] + lo[j].  Every wait has an iteration
+// limit: on a timeout the kernel's roles stop, no copy is left landing, and
+// false is returned in every thread.
+__device__ bool split_product(SplitSmem& sm, const CUtensorMap* ahi, const CUtensorMap* alo, int ya,
+                              const CUtensorMap* bhi, const CUtensorMap* blo, int yb, int nchunk, float (&hi)[32],
+                              float (&lo)[32]) {
+  using namespace tc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_flag = &sm.abort;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  if (warp < kSplitWorkers) {
+    const int q = warp & 3, half = warp >> 2;
+    const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+    for (int c = 0; c < nchunk; ++c) {
+      const int a = c & 1;
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&sm.done[a], (c >> 1) & 1) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after_sync();
+      float t[16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tmem_ld16(tlane + 128 * a + 16 * h, t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.drained[a]);
+      if (*abort_flag) break;
+    }
+  } else if (warp == kSplitWorkers) {
+    // MMA warp: the whole warp runs the loop, lane 0 waits and issues
+    const uint32_t idesc = idesc_tf32(128, 128);
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % kSplitStages, a = c & 1;
+      int okw = 1;
+      if (lane == 0) {
+        okw = mbar_wait(&sm.full[s], (c / kSplitStages) & 1) ? 1 : 0;
+        if (okw && c >= 2) okw = mbar_wait(&sm.drained[a], ((c - 2) >> 1) & 1) ? 1 : 0;
+      }
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      fence_after_sync();
+      if (lane == 0) {
+        TcStage<128>& S = sm.st[s];
+        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+        const uint32_t dcol = sm.tmem + 128 * a;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
+          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+          mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+        }
+        mma_commit(&sm.empty[s]);  // the stage may be refilled
+        mma_commit(&sm.done[a]);   // the accumulator may be drained
+      }
+      __syncwarp();
+    }
+    if (lane == 0) mma_commit(&sm.fin);  // arrives once every MMA issued above has completed
+    __syncwarp();
+  } else {
+    // TMA producer: the whole warp runs the loop (no lane spins apart from
+    // the issuing one), lane 0 waits and issues
+    int issued = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % kSplitStages;
+      int okw = 1;
+      if (lane == 0 && c >= kSplitStages) okw = mbar_wait(&sm.empty[s], (c / kSplitStages - 1) & 1) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      if (lane == 0) {
+        TcStage<128>& S = sm.st[s];
+        mbar_arrive_expect_tx(&sm.full[s], 4u * 128u * 32u * 4u);
+        tma_load_2d(S.a_hi, ahi, 32 * c, ya, &sm.full[s]);
+        tma_load_2d(S.a_lo, alo, 32 * c, ya, &sm.full[s]);
+        tma_load_2d(S.b_hi, bhi, 32 * c, yb, &sm.full[s]);
+        tma_load_2d(S.b_lo, blo, 32 * c, yb, &sm.full[s]);
+      }
+      __syncwarp();
+      issued = c + 1;
+    }
+    // no copy may still be landing in shared memory when the CTA leaves
+    if (lane == 0)
+      for (int c = issued > kSplitStages ? issued - kSplitStages : 0; c < issued; ++c)
+        mbar_wait(&sm.full[c % kSplitStages], (c / kSplitStages) & 1);
+    __syncwarp();
+  }
+  // every issued MMA has completed before anyone reads or frees tensor memory
+  const bool w = mbar_wait(&sm.fin, 0);
+  return __syncthreads_and(w && !*abort_flag) != 0;
+}
+
 // Residual tiles on the tensor cores (mixed form).  Item (window, I, J): rows
 // [128 I, 128 I + 128) x columns [RB J, RB J + RB) of the window's residual
 // R = K + sigma_n^2 I - Vt Vt^T, blanket-first, with the Vt Vt^T sum of
-// comp_product (RB = 128 columns, 512 threads).  Vtp: point-major V with
-// leading dimension ldv (a multiple of 32, zero pad).
+// split_product (RB = 128 columns).  (vhi, vlo): tensor maps of the TF32
+// halves of V in reversed point order (row nrev - 1 - p holds point p), 32 x
+// 128 boxes, 128-byte swizzle; nchunk = (row length of V) / 32.  Rows and
+// columns past the window's order read other points' rows (or zeros): the
+// epilogue writes the identity there and never reads those sums.
 constexpr int RB = 128;
-__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
-                                                     const float* __restrict__ xs, int d, const float* __restrict__ Vtp,
-                                                     int ldv, float ss2, float sn2, float* __restrict__ buf,
-                                                     int* __restrict__ err) {
+__global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
+                                                  const float* __restrict__ xs, int d,
+                                                  const __grid_constant__ CUtensorMap vhi,
+                                                  const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
+                                                  float ss2, float sn2, float* __restrict__ buf,
+                                                  int* __restrict__ err) {
   using namespace tc;
   const int4 it = items[blockIdx.x];
   const Win w = wins[it.x];
   const int r0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  CompSmem<RB>& sm = comp_smem<RB>(smraw);
+  SplitSmem& sm = split_smem(smraw);
   __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += comp_threads<RB>()) {
+  for (int e = tid; e < RB * d; e += kSplitThreads) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  comp_setup(sm);
-  auto rowA = [&](int r) -> const float* {
-    const int i = r0 + r;
-    return (i < w.n) ? Vtp + (w.g_end - 1 - i) * (int64_t)ldv : nullptr;
-  };
-  auto rowB = [&](int c) -> const float* {
-    const int j = c0 + c;
-    return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
-  };
+  split_setup(sm);
+  const int base = nrev - (int)w.g_end;  // reversed row of the window's local row 0
   float hi[32], lo[32];
-  CompState cs;
-  const bool ok = comp_product<RB, false, false>(sm, cs, 0, ldv, rowA, rowB, hi, lo);
+  const bool ok = split_product(sm, &vhi, &vlo, base + r0, &vhi, &vlo, base + c0, nchunk, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int i = r0 + q * 32 + lane;
   const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
-  if (ok && warp < RB / 8 && i < w.npad && cg < w.npad) {
+  if (ok && warp < kSplitWorkers && i < w.npad && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = (i < w.n) ? xs[(w.g_end - 1 - i) * d + t] : 0.f;
     float* dst = buf + w.base + (int64_t)i * w.npad + cg;
@@ -1127,7 +1324,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_resid_tc(const int4* 
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  comp_teardown(sm);
+  split_teardown(sm);
 }
 
 // Gram of the local summaries on the tensor cores (mixed form): after the
@@ -1226,44 +1423,40 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_tc(const P
 
 // Prediction right-hand sides on the tensor cores: item (pair, u tile of
 // 128, column tile of RB): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
-// the window of the pair, with the compensated product (the same cancellation
-// as the residual).  Vup / Vtp: leading dimension ldv (multiple of 32).
-__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
-                                                        const Win* __restrict__ wins, const float* __restrict__ xs,
-                                                        const float* __restrict__ xu, int d,
-                                                        const float* __restrict__ Vtp, const float* __restrict__ Vup,
-                                                        int ldv, float ss2, float* __restrict__ P,
-                                                        int* __restrict__ err) {
+// the window of the pair, with split_product (the same cancellation as the
+// residual).  (uhi, ulo): tensor maps of the TF32 halves of Vu in test-point
+// order; (vhi, vlo) those of Vt in reversed point order (row nrev - 1 - p
+// holds point p); nchunk = (row length) / 32.  Test rows past the block and
+// window columns past its order are never written from their sums.
+__global__ void __launch_bounds__(kSplitThreads, 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
+                                                     const Win* __restrict__ wins, const float* __restrict__ xs,
+                                                     const float* __restrict__ xu, int d,
+                                                     const __grid_constant__ CUtensorMap uhi,
+                                                     const __grid_constant__ CUtensorMap ulo,
+                                                     const __grid_constant__ CUtensorMap vhi,
+                                                     const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
+                                                     float ss2, float* __restrict__ P, int* __restrict__ err) {
   using namespace tc;
   const int4 it = items[blockIdx.x];
   const Pair pr = pairs[it.x];
   const Win w = wins[pr.win];
   const int u0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  CompSmem<RB>& sm = comp_smem<RB>(smraw);
+  SplitSmem& sm = split_smem(smraw);
   __shared__ float xc[RB][MAXD + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += comp_threads<RB>()) {
+  for (int e = tid; e < RB * d; e += kSplitThreads) {
     const int r = e / d, q = e % d;
     xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
   }
-  comp_setup(sm);
-  auto rowA = [&](int r) -> const float* {
-    const int uu = u0 + r;
-    return (uu < pr.nu) ? Vup + (int64_t)(pr.u0 + uu) * ldv : nullptr;
-  };
-  auto rowB = [&](int c) -> const float* {
-    const int j = c0 + c;
-    return (j < w.n) ? Vtp + (w.g_end - 1 - j) * (int64_t)ldv : nullptr;
-  };
+  split_setup(sm);
   float hi[32], lo[32];
-  CompState cs;
-  const bool ok = comp_product<RB, false, false>(sm, cs, 0, ldv, rowA, rowB, hi, lo);
+  const bool ok = split_product(sm, &uhi, &ulo, pr.u0 + u0, &vhi, &vlo, nrev - (int)w.g_end + c0, nchunk, hi, lo);
   if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
   const int uu = u0 + q * 32 + lane;
   const int cg = c0 + half * 32;
-  if (ok && warp < RB / 8 && uu < pr.nu && cg < w.npad) {
+  if (ok && warp < kSplitWorkers && uu < pr.nu && cg < w.npad) {
     float xr[MAXD];
     for (int t = 0; t < d; ++t) xr[t] = xu[(int64_t)(pr.u0 + uu) * d + t];
     float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
@@ -1286,7 +1479,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_rhs_tc(const Pai
     for (int j4 = 0; j4 < 8; ++j4)
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
   }
-  comp_teardown(sm);
+  split_teardown(sm);
 }
 
 }  // namespace lma
