@@ -74,6 +74,17 @@ static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlac
 static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
 static size_t split_smem_bytes() { return sizeof(SplitSmem) + tc::kTcAlignSlack; }
 
+// Grid of a persistent kernel with one CTA per SM: min(items, SM count).
+static unsigned persistent_grid(size_t items) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    LMA_CK(cudaGetDevice(&dev));
+    LMA_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(items, (size_t)nsm));
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // dependency on the driver library).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -156,8 +167,10 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
-    cudaFuncSetAttribute(k_resid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_pred_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_resid_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_resid_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_pred_rhs_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_pred_rhs_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
@@ -383,8 +396,9 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), kSplitThreads, split_smem_bytes(), st,
-             (const int4*)itd, wd, (const float*)xsT, d, vh, vl, (int)n, sp / 32, (float)mc.ss2, (float)mc.sn2,
+      launch("k_resid_tc", pad_dim(d) == 8 ? k_resid_tc<8> : k_resid_tc<MAXD>, persistent_grid(items.size()),
+             kSplitThreads, split_smem_bytes(), st,
+             (const int4*)itd, (int)items.size(), wd, (const float*)xsT, d, vh, vl, (int)n, sp / 32, (float)mc.ss2, (float)mc.sn2,
              (float*)wbuf, rerr);
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
     } else if (batched) {
@@ -683,8 +697,9 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
         stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-        launch("k_pred_rhs_tc", k_pred_rhs_tc, (unsigned)it_r.size(), kSplitThreads, split_smem_bytes(), st, pd,
-               (const int4*)irr, mc.wins_d, (const float*)xs, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n,
+        launch("k_pred_rhs_tc", pad_dim(d) == 8 ? k_pred_rhs_tc<8> : k_pred_rhs_tc<MAXD>, persistent_grid(it_r.size()),
+               kSplitThreads, split_smem_bytes(), st,
+               pd, (const int4*)irr, (int)it_r.size(), mc.wins_d, (const float*)xs, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n,
                sp / 32, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
@@ -828,8 +843,9 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", k_resid_tc, (unsigned)items.size(), kSplitThreads, split_smem_bytes(), st,
-             (const int4*)itd, wd, (const float*)mc.xsT, (int)mc.d, vh, vl, (int)n, sp / 32, (float)mc.ss2,
+      launch("k_resid_tc", pad_dim((int)mc.d) == 8 ? k_resid_tc<8> : k_resid_tc<MAXD>, persistent_grid(items.size()),
+             kSplitThreads, split_smem_bytes(), st,
+             (const int4*)itd, (int)items.size(), wd, (const float*)mc.xsT, (int)mc.d, vh, vl, (int)n, sp / 32, (float)mc.ss2,
              (float)mc.sn2, (float*)buf, rerr);
     } else {
       launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,

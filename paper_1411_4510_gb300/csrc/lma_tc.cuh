@@ -1085,10 +1085,14 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
 // thread loads each 32-wide K chunk (four 128 x 32 boxes, 64 KB) into a ring
 // of kSplitStages stages, one thread issues the chunk's 12 MMAs
 // (hi.hi + hi.lo + lo.hi per 8-wide K step) into one of two tensor-memory
-// accumulators, and 16 worker warps drain each chunk's accumulator into
-// (hi, lo) with TwoSum while the next chunk is multiplied.  Products, chunk
-// sums and their rounding are exactly those of comp_product.
+// accumulators, and 16 worker warps drain an accumulator into (hi, lo) with
+// TwoSum every kSplitDrain chunks while the other one is being filled.
+// Draining every 64 values of K instead of every 32 (comp_product) halves
+// the SM's TwoSum work; the FP32 partial sums are twice as long, which moves
+// the predictive mean by a few per cent of its error against the FP64 form
+// (that error is dominated by the FP32 window factorisations).
 constexpr int kSplitStages = 3;
+constexpr int kSplitDrain = 2;
 constexpr int kSplitWorkers = 16;                        // 4 lane quarters x 4 groups of 32 columns
 constexpr int kSplitThreads = 32 * (kSplitWorkers + 2);  // + MMA warp + TMA warp
 struct SplitSmem {
@@ -1151,179 +1155,249 @@ __device__ __forceinline__ void split_teardown(SplitSmem& sm) {
   if ((threadIdx.x >> 5) == kSplitWorkers) tmem_dealloc(sm.tmem, 256);
 }
 
-// hi + lo = sum over k < 32 nchunk of A(r, k) B(c, k) with A rows
-// [ya, ya + 128) of (ahi, alo) and B rows [yb, yb + 128) of (bhi, blo) (rows
-// outside the maps read zero); worker warp w holds row 32 (w mod 4) + lane,
-// columns 32 (w / 4) + j in hi[j] + lo[j].  Every wait has an iteration
-// limit: on a timeout the kernel's roles stop, no copy is left landing, and
-// false is returned in every thread.
-__device__ bool split_product(SplitSmem& sm, const CUtensorMap* ahi, const CUtensorMap* alo, int ya,
-                              const CUtensorMap* bhi, const CUtensorMap* blo, int yb, int nchunk, float (&hi)[32],
-                              float (&lo)[32]) {
+// Barrier of the kSplitWorkers worker warps only (id 1) that also ANDs a
+// flag over them, so that all of them take the same branch after it.
+__device__ __forceinline__ bool worker_sync_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(kSplitWorkers * 32)
+      : "memory");
+  return r != 0;
+}
+
+// Persistent loop over output tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+// ... < ntiles, each hi + lo = sum over k < 32 nchunk of A(r, k) B(c, k)
+// with A rows [ya, ya + 128) of (ahi, alo) and B rows [yb, yb + 128) of
+// (bhi, blo), (ya, yb) = coords(t); rows outside the maps read zero.  The
+// producer and MMA warps run ahead into the next tile while the workers
+// finish the current one: before(t) (shared-memory set-up of the epilogue,
+// worker warps only, between two worker barriers), the drains, then
+// after(t, hi, lo), where worker warp w holds row 32 (w mod 4) + lane,
+// columns 32 (w / 4) + j in hi[j] + lo[j].  Barrier phases run on across
+// tiles.  Every wait has an iteration limit: on a timeout all roles stop,
+// no copy is left landing, and false is returned in every thread.
+template <class Coords, class Before, class After>
+__device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CUtensorMap* alo,
+                                 const CUtensorMap* bhi, const CUtensorMap* blo, int ntiles, int nchunk,
+                                 Coords coords, Before before, After after) {
   using namespace tc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &sm.abort;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  const int ngroup = (nchunk + kSplitDrain - 1) / kSplitDrain;
   if (warp < kSplitWorkers) {
     const int q = warp & 3, half = warp >> 2;
     const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
-    for (int c = 0; c < nchunk; ++c) {
-      const int a = c & 1;
-      int okw = 1;
-      if (lane == 0) okw = mbar_wait(&sm.done[a], (c >> 1) & 1) ? 1 : 0;
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (!okw) {
-        *abort_flag = 1;
-        break;
-      }
-      fence_after_sync();
-      float t[16];
+    int G = 0;  // groups drained so far by this CTA
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      ok = worker_sync_and(ok && !*abort_flag);  // also: the previous epilogue is done with shared memory
+      if (!ok) break;
+      before(t);
+      worker_sync_and(true);
+      float hi[32], lo[32];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        tmem_ld16(tlane + 128 * a + 16 * h, t);
+      for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+      for (int g = 0; g < ngroup && ok; ++g, ++G) {
+        const int a = G & 1;
+        int okw = 1;
+        if (lane == 0) okw = mbar_wait(&sm.done[a], (G >> 1) & 1) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        float tv[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tlane + 128 * a + 16 * h, tv);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], tv[j]);
+        }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.drained[a]);
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.drained[a]);
-      if (*abort_flag) break;
+      ok = worker_sync_and(ok && !*abort_flag);
+      if (!ok) break;
+      after(t, hi, lo);
     }
   } else if (warp == kSplitWorkers) {
-    // MMA warp: the whole warp runs the loop, lane 0 waits and issues
+    // MMA warp: the whole warp runs the loops, lane 0 waits and issues
     const uint32_t idesc = idesc_tf32(128, 128);
-    for (int c = 0; c < nchunk; ++c) {
-      const int s = c % kSplitStages, a = c & 1;
-      int okw = 1;
-      if (lane == 0) {
-        okw = mbar_wait(&sm.full[s], (c / kSplitStages) & 1) ? 1 : 0;
-        if (okw && c >= 2) okw = mbar_wait(&sm.drained[a], ((c - 2) >> 1) & 1) ? 1 : 0;
-      }
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (!okw) {
-        *abort_flag = 1;
-        break;
-      }
-      if (*abort_flag) break;
-      fence_after_sync();
-      if (lane == 0) {
-        TcStage<128>& S = sm.st[s];
-        const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-        const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-        const uint32_t dcol = sm.tmem + 128 * a;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t o = ks * 32;
-          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
-          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-          mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+    int C = 0, G = 0;  // chunks and groups issued so far by this CTA
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int c = 0; c < nchunk; ++c, ++C) {
+        const int s = C % kSplitStages, a = G & 1;
+        const bool first = (c % kSplitDrain) == 0, last = (c % kSplitDrain) == kSplitDrain - 1 || c == nchunk - 1;
+        int okw = 1;
+        if (lane == 0) {
+          okw = mbar_wait(&sm.full[s], (C / kSplitStages) & 1) ? 1 : 0;
+          if (okw && first && G >= 2) okw = mbar_wait(&sm.drained[a], ((G - 2) >> 1) & 1) ? 1 : 0;
         }
-        mma_commit(&sm.empty[s]);  // the stage may be refilled
-        mma_commit(&sm.done[a]);   // the accumulator may be drained
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        if (lane == 0) {
+          TcStage<128>& S = sm.st[s];
+          const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+          const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+          const uint32_t dcol = sm.tmem + 128 * a;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (first && ks == 0) ? 0u : 1u);
+            mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+            mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+          }
+          mma_commit(&sm.empty[s]);           // the stage may be refilled
+          if (last) mma_commit(&sm.done[a]);  // the accumulator may be drained
+        }
+        __syncwarp();
+        if (last) ++G;
       }
-      __syncwarp();
     }
     if (lane == 0) mma_commit(&sm.fin);  // arrives once every MMA issued above has completed
     __syncwarp();
   } else {
-    // TMA producer: the whole warp runs the loop (no lane spins apart from
-    // the issuing one), lane 0 waits and issues
-    int issued = 0;
-    for (int c = 0; c < nchunk; ++c) {
-      const int s = c % kSplitStages;
-      int okw = 1;
-      if (lane == 0 && c >= kSplitStages) okw = mbar_wait(&sm.empty[s], (c / kSplitStages - 1) & 1) ? 1 : 0;
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (!okw) {
-        *abort_flag = 1;
-        break;
+    // TMA producer: the whole warp runs the loops, lane 0 waits and issues
+    int C = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int2 y = coords(t);
+      for (int c = 0; c < nchunk; ++c, ++C) {
+        const int s = C % kSplitStages;
+        int okw = 1;
+        if (lane == 0 && C >= kSplitStages) okw = mbar_wait(&sm.empty[s], (C / kSplitStages - 1) & 1) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          TcStage<128>& S = sm.st[s];
+          mbar_arrive_expect_tx(&sm.full[s], 4u * 128u * 32u * 4u);
+          tma_load_2d(S.a_hi, ahi, 32 * c, y.x, &sm.full[s]);
+          tma_load_2d(S.a_lo, alo, 32 * c, y.x, &sm.full[s]);
+          tma_load_2d(S.b_hi, bhi, 32 * c, y.y, &sm.full[s]);
+          tma_load_2d(S.b_lo, blo, 32 * c, y.y, &sm.full[s]);
+        }
+        __syncwarp();
       }
-      if (*abort_flag) break;
-      if (lane == 0) {
-        TcStage<128>& S = sm.st[s];
-        mbar_arrive_expect_tx(&sm.full[s], 4u * 128u * 32u * 4u);
-        tma_load_2d(S.a_hi, ahi, 32 * c, ya, &sm.full[s]);
-        tma_load_2d(S.a_lo, alo, 32 * c, ya, &sm.full[s]);
-        tma_load_2d(S.b_hi, bhi, 32 * c, yb, &sm.full[s]);
-        tma_load_2d(S.b_lo, blo, 32 * c, yb, &sm.full[s]);
-      }
-      __syncwarp();
-      issued = c + 1;
     }
     // no copy may still be landing in shared memory when the CTA leaves
     if (lane == 0)
-      for (int c = issued > kSplitStages ? issued - kSplitStages : 0; c < issued; ++c)
+      for (int c = C > kSplitStages ? C - kSplitStages : 0; c < C; ++c)
         mbar_wait(&sm.full[c % kSplitStages], (c / kSplitStages) & 1);
     __syncwarp();
   }
-  // every issued MMA has completed before anyone reads or frees tensor memory
+  // every issued MMA has completed before anyone frees tensor memory
   const bool w = mbar_wait(&sm.fin, 0);
   return __syncthreads_and(w && !*abort_flag) != 0;
 }
 
-// Residual tiles on the tensor cores (mixed form).  Item (window, I, J): rows
-// [128 I, 128 I + 128) x columns [RB J, RB J + RB) of the window's residual
+// Residual tiles on the tensor cores (mixed form), one persistent CTA per SM
+// walking the item list.  Item (window, I, J): rows [128 I, 128 I + 128) x
+// columns [RB J, RB J + RB) of the window's residual
 // R = K + sigma_n^2 I - Vt Vt^T, blanket-first, with the Vt Vt^T sum of
-// split_product (RB = 128 columns).  (vhi, vlo): tensor maps of the TF32
+// split_persistent (RB = 128 columns).  (vhi, vlo): tensor maps of the TF32
 // halves of V in reversed point order (row nrev - 1 - p holds point p), 32 x
 // 128 boxes, 128-byte swizzle; nchunk = (row length of V) / 32.  Rows and
 // columns past the window's order read other points' rows (or zeros): the
 // epilogue writes the identity there and never reads those sums.
 constexpr int RB = 128;
-__global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __restrict__ items, const Win* __restrict__ wins,
-                                                  const float* __restrict__ xs, int d,
+
+// Squared scaled distance |a - b|^2 over D (zero-padded) dimensions; b is a
+// 16-byte-aligned shared-memory row read with broadcast vector loads.
+template <int D>
+__device__ __forceinline__ float dist2(const float (&a)[D], const float* b) {
+  float d2 = 0.f;
+#pragma unroll
+  for (int t = 0; t < D; t += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(b + t);
+    float u = a[t] - v.x;
+    d2 = fmaf(u, u, d2);
+    u = a[t + 1] - v.y;
+    d2 = fmaf(u, u, d2);
+    u = a[t + 2] - v.z;
+    d2 = fmaf(u, u, d2);
+    u = a[t + 3] - v.w;
+    d2 = fmaf(u, u, d2);
+  }
+  return d2;
+}
+// Input dimension padded for the unrolled epilogues (a multiple of 4).
+__host__ __device__ constexpr int pad_dim(int d) { return d <= 8 ? 8 : MAXD; }
+
+template <int D>
+__global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __restrict__ items, int nitems,
+                                                  const Win* __restrict__ wins, const float* __restrict__ xs, int d,
                                                   const __grid_constant__ CUtensorMap vhi,
                                                   const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
                                                   float ss2, float sn2, float* __restrict__ buf,
                                                   int* __restrict__ err) {
   using namespace tc;
-  const int4 it = items[blockIdx.x];
-  const Win w = wins[it.x];
-  const int r0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
   SplitSmem& sm = split_smem(smraw);
-  __shared__ float xc[RB][MAXD + 1];
+  __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += kSplitThreads) {
-    const int r = e / d, q = e % d;
-    xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
-  }
   split_setup(sm);
-  const int base = nrev - (int)w.g_end;  // reversed row of the window's local row 0
-  float hi[32], lo[32];
-  const bool ok = split_product(sm, &vhi, &vlo, base + r0, &vhi, &vlo, base + c0, nchunk, hi, lo);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  const int q = warp & 3, half = warp >> 2;
-  const int i = r0 + q * 32 + lane;
-  const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
-  if (ok && warp < kSplitWorkers && i < w.npad && cg < w.npad) {
-    float xr[MAXD];
-    for (int t = 0; t < d; ++t) xr[t] = (i < w.n) ? xs[(w.g_end - 1 - i) * d + t] : 0.f;
-    float* dst = buf + w.base + (int64_t)i * w.npad + cg;
-    float out[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int cl = half * 32 + j;
-      const int jj = c0 + cl;
-      float v;
-      if (i < w.n && jj < w.n) {
-        float d2 = 0.f;
-        for (int t2 = 0; t2 < d; ++t2) {
-          const float u = xr[t2] - xc[cl][t2];
-          d2 = fmaf(u, u, d2);
-        }
-        v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
-        if (i == jj) v += sn2;
-      } else {
-        v = (i == jj) ? 1.f : 0.f;
-      }
-      out[j] = v;
+  auto coords = [&](int t) -> int2 {
+    const int4 it = items[t];
+    const int base = nrev - (int)wins[it.x].g_end;  // reversed row of the window's local row 0
+    return make_int2(base + it.y * 128, base + it.z * RB);
+  };
+  auto before = [&](int t) {
+    const int4 it = items[t];
+    const Win w = wins[it.x];
+    const int c0 = it.z * RB;
+    for (int e = tid; e < RB * D; e += kSplitWorkers * 32) {
+      const int r = e / D, q = e % D;
+      xc[r][q] = (c0 + r < w.n && q < d) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
     }
+  };
+  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
+    const int4 it = items[t];
+    const Win w = wins[it.x];
+    const int r0 = it.y * 128, c0 = it.z * RB;
+    const int q = warp & 3, half = warp >> 2;
+    const int i = r0 + q * 32 + lane;
+    const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
+    if (i >= w.npad || cg >= w.npad) return;
+    float xr[D];
 #pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4)
-      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
-  }
+    for (int t2 = 0; t2 < D; ++t2) xr[t2] = (i < w.n && t2 < d) ? xs[(w.g_end - 1 - i) * d + t2] : 0.f;
+    float* dst = buf + w.base + (int64_t)i * w.npad + cg;
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      float out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * j4 + k, cl = half * 32 + j, jj = c0 + cl;
+        float v;
+        if (i < w.n && jj < w.n) {
+          const float d2 = dist2<D>(xr, xc[cl]);
+          v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
+          if (i == jj) v += sn2;
+        } else {
+          v = (i == jj) ? 1.f : 0.f;
+        }
+        out[k] = v;
+      }
+      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+  };
+  const bool ok = split_persistent(sm, &vhi, &vlo, &vhi, &vlo, nitems, nchunk, coords, before, after);
+  if (!ok && tid == 0) atomicExch(err, 1);
   split_teardown(sm);
 }
 
@@ -1421,64 +1495,74 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_tc(const P
   comp_teardown(sm);
 }
 
-// Prediction right-hand sides on the tensor cores: item (pair, u tile of
-// 128, column tile of RB): P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for
-// the window of the pair, with split_product (the same cancellation as the
-// residual).  (uhi, ulo): tensor maps of the TF32 halves of Vu in test-point
-// order; (vhi, vlo) those of Vt in reversed point order (row nrev - 1 - p
-// holds point p); nchunk = (row length) / 32.  Test rows past the block and
-// window columns past its order are never written from their sums.
+// Prediction right-hand sides on the tensor cores, one persistent CTA per SM
+// walking the item list: item (pair, u tile of 128, column tile of RB):
+// P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for the window of the pair,
+// with split_persistent (the same cancellation as the residual).
+// (uhi, ulo): tensor maps of the TF32 halves of Vu in test-point order;
+// (vhi, vlo) those of Vt in reversed point order (row nrev - 1 - p holds
+// point p); nchunk = (row length) / 32.  Test rows past the block and window
+// columns past its order are never written from their sums.
+template <int D>
 __global__ void __launch_bounds__(kSplitThreads, 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
-                                                     const Win* __restrict__ wins, const float* __restrict__ xs,
-                                                     const float* __restrict__ xu, int d,
+                                                     int nitems, const Win* __restrict__ wins,
+                                                     const float* __restrict__ xs, const float* __restrict__ xu, int d,
                                                      const __grid_constant__ CUtensorMap uhi,
                                                      const __grid_constant__ CUtensorMap ulo,
                                                      const __grid_constant__ CUtensorMap vhi,
                                                      const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
                                                      float ss2, float* __restrict__ P, int* __restrict__ err) {
   using namespace tc;
-  const int4 it = items[blockIdx.x];
-  const Pair pr = pairs[it.x];
-  const Win w = wins[pr.win];
-  const int u0 = it.y * 128, c0 = it.z * RB;
   extern __shared__ __align__(16) unsigned char smraw[];
   SplitSmem& sm = split_smem(smraw);
-  __shared__ float xc[RB][MAXD + 1];
+  __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < RB * d; e += kSplitThreads) {
-    const int r = e / d, q = e % d;
-    xc[r][q] = (c0 + r < w.n) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
-  }
   split_setup(sm);
-  float hi[32], lo[32];
-  const bool ok = split_product(sm, &uhi, &ulo, pr.u0 + u0, &vhi, &vlo, nrev - (int)w.g_end + c0, nchunk, hi, lo);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  const int q = warp & 3, half = warp >> 2;
-  const int uu = u0 + q * 32 + lane;
-  const int cg = c0 + half * 32;
-  if (ok && warp < kSplitWorkers && uu < pr.nu && cg < w.npad) {
-    float xr[MAXD];
-    for (int t = 0; t < d; ++t) xr[t] = xu[(int64_t)(pr.u0 + uu) * d + t];
-    float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
-    float out[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int cl = half * 32 + j;
-      float v = 0.f;
-      if (c0 + cl < w.n) {
-        float d2 = 0.f;
-        for (int t2 = 0; t2 < d; ++t2) {
-          const float u = xr[t2] - xc[cl][t2];
-          d2 = fmaf(u, u, d2);
-        }
-        v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
-      }
-      out[j] = v;
+  auto coords = [&](int t) -> int2 {
+    const int4 it = items[t];
+    const Pair pr = pairs[it.x];
+    return make_int2(pr.u0 + it.y * 128, nrev - (int)wins[pr.win].g_end + it.z * RB);
+  };
+  auto before = [&](int t) {
+    const int4 it = items[t];
+    const Win w = wins[pairs[it.x].win];
+    const int c0 = it.z * RB;
+    for (int e = tid; e < RB * D; e += kSplitWorkers * 32) {
+      const int r = e / D, q = e % D;
+      xc[r][q] = (c0 + r < w.n && q < d) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
     }
+  };
+  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
+    const int4 it = items[t];
+    const Pair pr = pairs[it.x];
+    const Win w = wins[pr.win];
+    const int u0 = it.y * 128, c0 = it.z * RB;
+    const int q = warp & 3, half = warp >> 2;
+    const int uu = u0 + q * 32 + lane;
+    const int cg = c0 + half * 32;
+    if (uu >= pr.nu || cg >= w.npad) return;
+    float xr[D];
 #pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4)
-      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
-  }
+    for (int t2 = 0; t2 < D; ++t2) xr[t2] = t2 < d ? xu[(int64_t)(pr.u0 + uu) * d + t2] : 0.f;
+    float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      float out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * j4 + k, cl = half * 32 + j;
+        float v = 0.f;
+        if (c0 + cl < w.n) {
+          const float d2 = dist2<D>(xr, xc[cl]);
+          v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
+        }
+        out[k] = v;
+      }
+      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+  };
+  const bool ok = split_persistent(sm, &uhi, &ulo, &vhi, &vlo, nitems, nchunk, coords, before, after);
+  if (!ok && tid == 0) atomicExch(err, 1);
   split_teardown(sm);
 }
 
