@@ -689,40 +689,46 @@ __global__ void k_build_global(const double* __restrict__ G, int s, int npad, do
   buf[e] = v;
 }
 
-// scalars[0] = quad, [1] = w^T w (w = L_C^-1 y), [2] = log|C|; beta = L_C^-T w
-__global__ void k_global_finish(const double* __restrict__ buf, const double* __restrict__ G, int s, int npad,
-                                double* __restrict__ beta, double* __restrict__ scalars) {
+// beta = L_C^-T w (w = L_C^-1 y, the appended y row of the factor) as a
+// matrix-vector product with the explicit L_C^-T rows: one warp per row k,
+// coalesced, lane partial sums combined by shuffles (8 rows per CTA).  CTA 0
+// also writes scalars[0] = quad, [1] = w^T w, [2] = log|C|.
+__global__ void __launch_bounds__(NT) k_global_finish(const double* __restrict__ buf, const double* __restrict__ G,
+                                                      int s, int npad, double* __restrict__ beta,
+                                                      double* __restrict__ scalars) {
   const double* E = buf + (int64_t)npad * npad;  // row k = (L_C^-T)[k][.]
   const double* w = E + (int64_t)s * npad;
-  __shared__ double red[NT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (NT / 32) + warp;
+  if (k < s) {
+    const double* row = E + (int64_t)k * npad;
+    double sum = 0.0;
+    for (int i = lane; i < s; i += 32) sum = fma(row[i], w[i], sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) beta[k] = sum;
+  }
+  if (blockIdx.x != 0) return;
+  __shared__ double red[2][NT];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < s; i += NT) {
     a += w[i] * w[i];
     b += log(buf[(int64_t)i * npad + i]);
   }
-  for (int k = threadIdx.x; k < s; k += NT) {
-    double sum = 0.0;
-    const double* row = E + (int64_t)k * npad;
-    for (int i = 0; i < s; ++i) sum += row[i] * w[i];
-    beta[k] = sum;
-  }
-  red[threadIdx.x] = a;
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
   __syncthreads();
   for (int o = NT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) scalars[1] = red[0];
-  __syncthreads();
-  red[threadIdx.x] = b;
-  __syncthreads();
-  for (int o = NT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    scalars[2] = 2.0 * red[0];
     scalars[0] = G[0];
+    scalars[1] = red[0][0];
+    scalars[2] = 2.0 * red[1][0];
   }
 }
 
@@ -753,6 +759,34 @@ __global__ void k_ew(const Win* __restrict__ wins, const T* __restrict__ buf, co
   double v = (double)E[c];
   for (int k = 0; k < s; ++k) v -= beta[k] * (double)E[(int64_t)(1 + k) * w.npad + c];
   ew[w.ew + c] = (T)v;
+}
+
+// The same for FP32 extra rows without FP64 arithmetic (scarce on this part):
+// beta_k = bh_k + bl_k as two floats (k_split_beta), each product
+// bh_k x = p + e exactly (e from an FMA), bl_k x added to e, and the p are
+// summed with TwoSum into (hi, lo), which keeps about 48 bits of the sum.
+__global__ void k_split_beta(const double* __restrict__ beta, int s, float2* __restrict__ bs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= s) return;
+  const float h = (float)beta[k];
+  bs[k] = make_float2(h, (float)(beta[k] - (double)h));
+}
+__global__ void k_ew_f32(const Win* __restrict__ wins, const float* __restrict__ buf, const float2* __restrict__ bs,
+                         int s, float* __restrict__ ew) {
+  const Win w = wins[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= w.npad) return;
+  const float* E = buf + w.base + (int64_t)w.npad * w.npad;
+  float hi = 0.f, lo = 0.f;
+  for (int k = 0; k < s; ++k) {
+    const float x = E[(int64_t)(1 + k) * w.npad + c];
+    const float2 b = bs[k];
+    const float p = b.x * x;
+    const float e = fmaf(b.x, x, -p);
+    lo += fmaf(b.y, x, e);
+    two_sum(hi, lo, p);
+  }
+  ew[w.ew + c] = (float)((double)E[c] - ((double)hi + (double)lo));
 }
 
 // ---------------------------------------------------------------------------

@@ -479,12 +479,19 @@ void Impl<T>::fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on) {
     mc.beta = mc.keep.alloc<double>(s);
     mc.sc_d = mc.keep.alloc<double>(4);
     double* sc = mc.sc_d;
-    launch("k_global_finish", k_global_finish, 1, NT, 0, st, cb, mc.G, (int)s, npC, mc.beta, sc);
+    launch("k_global_finish", k_global_finish, nblk(s, NT / 32), NT, 0, st, cb, mc.G, (int)s, npC, mc.beta, sc);
     T* LcT = mc.keep.alloc<T>(s * s);
     launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)npC * npC, npC, (int)s, LcT);
     mc.LcT = LcT;
-    launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, mc.wins_d, (const T*)mc.wbuf, mc.beta,
-           (int)s, (T*)mc.ew);
+    if (sizeof(T) == 4) {
+      float2* bs = tmp.alloc<float2>(s);
+      launch("k_split_beta", k_split_beta, nblk(s), NT, 0, st, (const double*)mc.beta, (int)s, bs);
+      launch("k_ew", k_ew_f32, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, mc.wins_d, (const float*)mc.wbuf,
+             (const float2*)bs, (int)s, (float*)mc.ew);
+    } else {
+      launch("k_ew", k_ew<T>, dim3(nblk(maxnt * TB), (unsigned)M), NT, 0, st, mc.wins_d, (const T*)mc.wbuf, mc.beta,
+             (int)s, (T*)mc.ew);
+    }
     tmp.release();
   } catch (...) {
     tmp.release();
