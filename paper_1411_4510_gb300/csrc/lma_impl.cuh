@@ -191,6 +191,23 @@ struct lma_model {
 
 namespace lma {
 
+// Test points of lma_fit_predict whose right-hand sides R_{W_m u} are
+// appended to the window buffers as extra rows, below the s + 1 rows of
+// [r | Vt_W], so that the fit's own sweep turns them into (L_m^-1 R_{W_m u})^T
+// (the rows the prediction's local route needs) and no separate prediction
+// sweep runs.  Window m carries the test rows of blocks m .. m + B in block
+// order.  xu / Vu (scaled test inputs, their whitened support coordinates)
+// are kept in `keep` for the prediction.
+struct FusedTest {
+  int64_t U = 0;
+  const double* XU = nullptr;
+  const int64_t* tptr = nullptr;
+  int on_device = 0;
+  Arena keep;
+  void* xu = nullptr;
+  void* Vu = nullptr;
+};
+
 template <typename T>
 struct Impl {
   // prepares inputs, Sigma_SS factor and Vt (shared by fit / residual / grad)
@@ -198,14 +215,16 @@ struct Impl {
                       const double** X_d, const double** y_d);
   static void fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H);
   static void fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin, int64_t own_begin,
-                        int64_t own_end);
+                        int64_t own_end, FusedTest* ft = nullptr);
+  // right-hand sides of ft's test points into the window buffers (before the sweep)
+  static void fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp);
   static void fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on = nullptr);
   // waits for the stream and turns the status words into an error (if any);
   // global: also reads the global step's scalars and forms the loglik
   static void check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
                       int on_device, double* mean, double* var, cudaEvent_t global_done = nullptr,
-                      double* cov = nullptr);
+                      double* cov = nullptr, FusedTest* ft = nullptr);
   static void fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
                           const int64_t* tptr, int noisy, int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);
@@ -223,7 +242,16 @@ void global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y,
 // for blocks [m_begin, m_end) (m_end < 0: all)
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t elem, std::vector<Win>& wins,
                   int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems, int64_t m_begin = 0,
-                  int64_t m_end = -1);
+                  int64_t m_end = -1, const std::vector<int>* test_rows = nullptr);
+
+// Prediction pairs (test block n, window m in [n - B, n]) and per test block
+// (first pair, pair count, first test row, test rows).  fused: P rows of
+// pair (n, m) are window m's appended test rows (FusedTest); otherwise they
+// are packed in a separate buffer of *p_elems elements.
+void make_pairs(const std::vector<Win>& wins, int64_t w0, int64_t M, int64_t B, int64_t s, const int64_t* tptr,
+                bool fused, std::vector<Pair>& pairs, std::vector<int4>& tb, int64_t* p_elems);
+// number of appended test rows of each window of a whole fit (FusedTest)
+std::vector<int> fused_test_rows(int64_t M, int64_t B, const int64_t* tptr);
 
 // sweep helpers (defined per precision)
 template <typename T>

@@ -21,7 +21,8 @@ namespace lma {
 
 // ---------------------------------------------------------------------------
 void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t /*elem*/, std::vector<Win>& wins,
-                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems, int64_t m_begin, int64_t m_end) {
+                  int64_t& buf_elems, int64_t& dinv_elems, int64_t& ew_elems, int64_t m_begin, int64_t m_end,
+                  const std::vector<int>* test_rows) {
   const int64_t M = (int64_t)bptr.size() - 1;
   if (m_end < 0) m_end = M;
   wins.resize(m_end - m_begin);
@@ -32,7 +33,7 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
     w.n = (int)(bptr[last + 1] - bptr[m]);
     w.nB = (int)(bptr[last + 1] - bptr[m + 1]);
     w.npad = (int)roundup(w.n, TB);
-    w.rows = (int)(w.npad + s + 1);
+    w.rows = (int)(w.npad + s + 1) + (test_rows ? (*test_rows)[m] : 0);
     w.g_end = bptr[last + 1];
     w.m = (int)m;
     w.base = buf_elems;
@@ -43,6 +44,44 @@ void make_windows(const std::vector<int64_t>& bptr, int64_t B, int64_t s, size_t
     ew_elems += w.npad;
     wins[m - m_begin] = w;
   }
+}
+
+void make_pairs(const std::vector<Win>& wins, int64_t w0, int64_t M, int64_t B, int64_t s, const int64_t* tptr,
+                bool fused, std::vector<Pair>& pairs, std::vector<int4>& tb, int64_t* p_elems) {
+  std::vector<int> used(wins.size(), 0);  // test rows already placed in each window (fused)
+  int64_t pe = 0;
+  for (int64_t nb = 0; nb < M; ++nb) {
+    const int nu = (int)(tptr[nb + 1] - tptr[nb]);
+    if (nu == 0) continue;
+    const int first = (int)pairs.size();
+    for (int64_t m = std::max<int64_t>(0, nb - B); m <= nb; ++m) {
+      const Win& w = wins[m - w0];
+      Pair p{};
+      if (fused) {
+        p.pbase = w.base + (int64_t)(w.npad + s + 1 + used[m - w0]) * w.npad;
+        used[m - w0] += nu;
+      } else {
+        p.pbase = pe;
+        pe += (int64_t)nu * w.npad;
+      }
+      p.win = (int)(m - w0);
+      p.u0 = (int)tptr[nb];
+      p.nu = nu;
+      p.c0 = (m < nb) ? w.nB : 0;
+      p.c1 = w.n;
+      p.n = (int)nb;
+      pairs.push_back(p);
+    }
+    tb.push_back(make_int4(first, (int)pairs.size() - first, (int)tptr[nb], nu));
+  }
+  if (p_elems) *p_elems = pe;
+}
+
+std::vector<int> fused_test_rows(int64_t M, int64_t B, const int64_t* tptr) {
+  std::vector<int> rows(M, 0);
+  for (int64_t nb = 0; nb < M; ++nb)
+    for (int64_t m = std::max<int64_t>(0, nb - B); m <= nb; ++m) rows[m] += (int)(tptr[nb + 1] - tptr[nb]);
+  return rows;
 }
 
 void* Staging::take(size_t bytes, cudaStream_t st) {
@@ -344,7 +383,7 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
 // mc.logdetR.  A whole fit has w_begin = own_begin = 0, own_end = M.
 template <typename T>
 void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t w_begin,
-                        int64_t own_begin, int64_t own_end) {
+                        int64_t own_begin, int64_t own_end, FusedTest* ft) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -358,7 +397,9 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     launch("k_center", k_center<T>, nblk(n), NT, 0, st, y_d, n, mc.mu, rT);
     // windows
     int64_t bufe, dinve, ewe;
-    make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe, w_begin, own_end);
+    std::vector<int> trows;
+    if (ft) trows = fused_test_rows(mc.M, mc.B, ft->tptr);
+    make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe, w_begin, own_end, ft ? &trows : nullptr);
     mc.w0 = w_begin;
     const int64_t M = (int64_t)mc.wins.size();  // windows of this fit
     T* wbuf = mc.keep.alloc<T>(bufe);
@@ -414,6 +455,7 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       }
     }
     int* tc_err = (batched && sizeof(T) == 4 && use_tensor_cores()) ? mc.flags + 2 : nullptr;
+    if (ft) fused_rhs(mc, *ft, tmp);
     chol_sweep<T>(st, mc.wins, wd, wbuf, dinv, info, batched, tc_err);
     // Gram of the local summaries of the owned windows, reduced in a fixed order
     const int se = (int)s + 1;
@@ -577,24 +619,97 @@ void Impl<T>::fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     LMA_CK(cudaEventCreateWithFlags(&side.global, cudaEventDisableTiming));
     side.dev = dev;
   }
-  fit_local(mc, P, H, 0, 0, P->m_blocks);
-  LMA_CK(cudaEventRecord(side.local, mc.st));
-  LMA_CK(cudaStreamWaitEvent(side.st, side.local, 0));
+  // mixed form on the tensor cores: the test right-hand sides ride the fit's sweep
+  FusedTest ft;
+  FusedTest* ftp = nullptr;
+  if (mc.prec == LMA_MIXED && sizeof(T) == 4 && use_tensor_cores() && U > 0) {
+    ft.U = U;
+    ft.XU = XU;
+    ft.tptr = tptr;
+    ft.on_device = on_device;
+    ft.keep.st = mc.st;
+    ftp = &ft;
+  }
   try {
-    fit_global(mc, mc.n, side.st);
-    LMA_CK(cudaEventRecord(side.global, side.st));
-    predict(mc, U, XU, tptr, noisy, on_device, mean, var, side.global);
+    fit_local(mc, P, H, 0, 0, P->m_blocks, ftp);
+    LMA_CK(cudaEventRecord(side.local, mc.st));
+    LMA_CK(cudaStreamWaitEvent(side.st, side.local, 0));
+    try {
+      fit_global(mc, mc.n, side.st);
+      LMA_CK(cudaEventRecord(side.global, side.st));
+      predict(mc, U, XU, tptr, noisy, on_device, mean, var, side.global, nullptr, ftp);
+    } catch (...) {
+      cudaStreamSynchronize(side.st);  // nothing of this call may still run on the side stream
+      throw;
+    }
   } catch (...) {
-    cudaStreamSynchronize(side.st);  // nothing of this call may still run on the side stream
+    ft.keep.release();
     throw;
   }
+  ft.keep.release();
   LMA_CK(cudaStreamWaitEvent(mc.st, side.global, 0));
   check(mc, true, mc.n, true);
 }
 
 template <typename T>
+void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
+  if (sizeof(T) != 4 || !mc.vhi) {
+    fail(LMA_ERR_INTERNAL, "appended test rows need the mixed form on the tensor cores");
+    throw Fail{};
+  }
+  cudaStream_t st = mc.st;
+  const int64_t s = mc.s, U = ft.U;
+  const int d = (int)mc.d;
+  ft.keep.st = st;
+  const double* XUd = ft.XU;
+  if (!ft.on_device) {
+    double* t = tmp.alloc<double>(U * d);
+    LMA_CK(cudaMemcpyAsync(t, ft.XU, sizeof(double) * U * d, cudaMemcpyHostToDevice, st));
+    XUd = t;
+  }
+  float* xu = ft.keep.alloc<float>(U * d);
+  launch("k_scale", k_scale<float>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
+  float* Kus = tmp.alloc<float>(U * s);
+  launch("k_kds", k_kds<float>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const float*)xu, U, d,
+         (const float*)mc.ssT, (int)s, (float)mc.ss2, Kus);
+  float* Vu = ft.keep.alloc<float>(U * s);
+  if (s % 4 == 0)
+    launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
+           (const float*)mc.ET, Vu, (int)s);
+  else
+    launch("k_proj", k_proj<float>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const float*)Kus, U, (int)s,
+           (const float*)mc.ET, Vu, (int)s);
+  ft.xu = xu;
+  ft.Vu = Vu;
+  std::vector<Pair> pairs;
+  std::vector<int4> tb;
+  make_pairs(mc.wins, mc.w0, mc.M, mc.B, s, ft.tptr, true, pairs, tb, nullptr);
+  if (pairs.empty()) return;
+  Pair* pd = tmp.alloc<Pair>(pairs.size());
+  stage_copy(pd, pairs.data(), sizeof(Pair) * pairs.size(), st);
+  const int sp = mc.ldvs;
+  float* uhi = tmp.alloc<float>((size_t)U * sp);
+  float* ulo = tmp.alloc<float>((size_t)U * sp);
+  split_rows(st, Vu, U, s, sp, false, uhi, ulo, tmp);
+  const CUtensorMap vh = rows_tensor_map(mc.vhi, mc.n, sp), vl = rows_tensor_map(mc.vlo, mc.n, sp);
+  const CUtensorMap uh = rows_tensor_map(uhi, U, sp), ul = rows_tensor_map(ulo, U, sp);
+  std::vector<int4> it_r;
+  for (size_t pi = 0; pi < pairs.size(); ++pi) {
+    const int nct = (mc.wins[pairs[pi].win].npad + RB - 1) / RB;
+    for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut)
+      for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
+  }
+  int4* irr = tmp.alloc<int4>(it_r.size());
+  stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
+  launch("k_pred_rhs_tc", pad_dim(d) == 8 ? k_pred_rhs_tc<8> : k_pred_rhs_tc<MAXD>, persistent_grid(it_r.size()),
+         kSplitThreads, split_smem_bytes(), st, pd, (const int4*)irr, (int)it_r.size(), mc.wins_d,
+         (const float*)mc.xsT, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n, sp / 32, (float)mc.ss2,
+         (float*)mc.wbuf, mc.flags + 2);
+}
+
+template <typename T>
 void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
-                      double* mean, double* var, cudaEvent_t global_done, double* cov) {
+                      double* mean, double* var, cudaEvent_t global_done, double* cov, FusedTest* ft) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -605,46 +720,36 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       tmp.release();
       return;
     }
-    const double* XUd = XU;
-    if (!on_device) {
-      double* t = tmp.alloc<double>(U * d);
-      LMA_CK(cudaMemcpyAsync(t, XU, sizeof(double) * U * d, cudaMemcpyHostToDevice, st));
-      XUd = t;
+    T* xu = nullptr;
+    T* Vu = nullptr;
+    if (ft) {  // test projections made before the fit's sweep
+      xu = (T*)ft->xu;
+      Vu = (T*)ft->Vu;
+    } else {
+      const double* XUd = XU;
+      if (!on_device) {
+        double* t = tmp.alloc<double>(U * d);
+        LMA_CK(cudaMemcpyAsync(t, XU, sizeof(double) * U * d, cudaMemcpyHostToDevice, st));
+        XUd = t;
+      }
+      xu = tmp.alloc<T>(U * d);
+      launch("k_scale", k_scale<T>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
+      T* Kus = tmp.alloc<T>(U * s);
+      launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s,
+             (T)mc.ss2, Kus);
+      Vu = tmp.alloc<T>(U * s);
+      if (sizeof(T) == 4 && s % 4 == 0)
+        launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
+               (const float*)mc.ET, (float*)Vu, (int)s);
+      else
+        launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
+               (int)s);
     }
-    T* xu = tmp.alloc<T>(U * d);
-    launch("k_scale", k_scale<T>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
-    T* Kus = tmp.alloc<T>(U * s);
-    launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s, (T)mc.ss2, Kus);
-    T* Vu = tmp.alloc<T>(U * s);
-    if (sizeof(T) == 4 && s % 4 == 0)
-      launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
-             (const float*)mc.ET, (float*)Vu, (int)s);
-    else
-      launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
-             (int)s);
     // pairs (test block n, window m in [n-B, n])
     std::vector<Pair> pairs;
     std::vector<int4> tb;  // per test block: first pair, count, u0, nu
     int64_t pe = 0;
-    for (int64_t nb = 0; nb < M; ++nb) {
-      const int nu = (int)(tptr[nb + 1] - tptr[nb]);
-      if (nu == 0) continue;
-      const int first = (int)pairs.size();
-      for (int64_t m = std::max<int64_t>(0, nb - B); m <= nb; ++m) {
-        const Win& w = mc.wins[m - mc.w0];
-        Pair p{};
-        p.pbase = pe;
-        p.win = (int)(m - mc.w0);
-        p.u0 = (int)tptr[nb];
-        p.nu = nu;
-        p.c0 = (m < nb) ? w.nB : 0;
-        p.c1 = w.n;
-        p.n = (int)nb;
-        pe += (int64_t)nu * w.npad;
-        pairs.push_back(p);
-      }
-      tb.push_back(make_int4(first, (int)pairs.size() - first, (int)tptr[nb], nu));
-    }
+    make_pairs(mc.wins, mc.w0, M, B, s, tptr, ft != nullptr, pairs, tb, &pe);
     std::vector<int4> it_rhs, it_acc, it_t12;
     std::vector<int2> it_sw;
     for (size_t pi = 0; pi < pairs.size(); ++pi) {
@@ -674,11 +779,13 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     stage_copy(itd, it_t12.data(), sizeof(int4) * it_t12.size(), st);
     int* perr = tmp.alloc<int>(1);  // tensor-core pipeline timeout, checked at the end
     LMA_CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
-    T* Pbuf = tmp.alloc<T>(pe);
+    T* Pbuf = ft ? (T*)mc.wbuf : tmp.alloc<T>(pe);
     const T* xs = (const T*)mc.xsT;
     const T* Vt = (const T*)mc.Vt;
     const T* wbuf = (const T*)mc.wbuf;
-    if (mc.prec == LMA_MIXED) {
+    if (ft) {
+      // the right-hand sides were appended to the windows and solved by the fit's sweep
+    } else if (mc.prec == LMA_MIXED) {
       const bool tc = (sizeof(T) == 4 && use_tensor_cores());
       if (tc) {
         // right-hand sides on the tensor cores, fed by TMA from the TF32

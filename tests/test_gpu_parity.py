@@ -166,6 +166,39 @@ def test_c2_shaped_reduced(L, B):
         assert rel(var, v) <= tol_v, (prec, rel(var, v))
 
 
+def run_fit_predict(L, p, prec, B=None):
+    """lma_fit_predict; in the mixed form the test right-hand sides ride the
+    fit's sweep as extra window rows."""
+    args = L.problem_args(p, B)
+    mean, var, model = L.lma_fit_predict(XU=p.XU, test_block_ptr=p.test_block_ptr, precision=prec,
+                                         keep_model=True, **args)
+    return model, mean, var
+
+
+@pytest.mark.parametrize("case", TINY)
+def test_mixed_fit_predict_matches_oracle(L, case):
+    p = _tiny(case)
+    p.jitter = MIXED_TINY_JITTER
+    f, m, v = oracle(p)
+    model, mean, var = run_fit_predict(L, p, L.MIXED)
+    assert rel(mean, m) <= MEAN_TOL_MIXED
+    assert rel(var, v) <= VAR_TOL_MIXED
+    assert abs(L.lma_model_loglik(model) - f.loglik) <= LL_TOL_MIXED * abs(f.loglik)
+
+
+@pytest.mark.parametrize("B", [1, 2])
+def test_c2_shaped_fit_predict(L, B):
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=B)
+    f, m, v = oracle(p)
+    for prec in ("FP64", "MIXED"):
+        model, mean, var = run_fit_predict(L, p, getattr(L, prec))
+        tol_m = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
+        tol_v = TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED
+        assert rel(mean, m) <= tol_m, (prec, rel(mean, m))
+        assert rel(var, v) <= tol_v, (prec, rel(var, v))
+
+
 def test_single_block_and_tiny_sizes(L):
     from workloads import make_random_problem
     for case in [((37,), 0, 1, 1, (5,)), ((1, 1, 1), 1, 1, 1, (1, 0, 2)), ((3, 200), 1, 2, 3, (0, 4))]:
