@@ -58,37 +58,48 @@ def sweep_flops(p, B):
     return sum(n ** 3 / 3.0 + n * n * (s + 1) for n, _, _ in window_sizes(p.block_ptr, B))
 
 
-def kernel_work(p, B):
-    """Algorithmic flops per step of the main kernels (flop = 2 per multiply-add)."""
-    s = p.s
+def kernel_work(p, B, fused=True):
+    """Algorithmic flops per step of the main kernels (flop = 2 per multiply-add;
+    triangles count half).  fused: lma_fit_predict's mixed form, whose windows
+    carry the test right-hand sides as extra rows solved by the fit's sweep
+    (no separate prediction sweep)."""
+    s, M = p.s, p.M
     ws = window_sizes(p.block_ptr, B)
-    upd = 0.0   # left-looking sweep updates: rows below panel kp times 64 columns times K = 64 kp
-    tri = 0.0   # panel solves: rows below the diagonal block times 64 x 64
-    for n, b, nb in ws:
-        rows = n + s + 1
+    tp = p.test_block_ptr
+    nu = [int(tp[m + 1] - tp[m]) for m in range(M)]
+    trows = [sum(nu[n] for n in range(m, min(m + B, M - 1) + 1)) for m in range(M)] if fused else [0] * M
+    step = wide = tri = 0.0
+    SP = 256  # columns of a super-panel: k_chol_wide applies [0, kb), the 64-wide steps [kb, k0)
+    for (n, b, nb), t in zip(ws, trows):
+        rows = n + s + 1 + t
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
-            upd += 2.0 * (rows - k0) * w * k0
+            kb = (k0 // SP) * SP
+            step += 2.0 * ((rows - k0) * w - w * (w - 1) / 2.0) * (k0 - kb)
             tri += 2.0 * max(0, rows - k0 - w) * w * w / 2.0
+            if k0 == kb and kb > 0:
+                c = min(SP, n - kb)
+                wide += 2.0 * ((rows - kb) * c - c * (c - 1) / 2.0) * kb
     resid = sum(s * n * n for n, _, _ in ws)
     gram = sum(b * (s + 1) * (s + 1) for _, b, _ in ws)
-    tp = p.test_block_ptr
-    psweep = prhs = 0.0
-    for nb_ in range(p.M):
-        nu = int(tp[nb_ + 1] - tp[nb_])
-        for m in range(max(0, nb_ - B), nb_ + 1) if nu else ():
-            n = ws[m][0]
-            psweep += nu * n * n
-            prhs += 2.0 * nu * n * s
-    return {"k_chol_step_tc": upd, "k_chol_step_tma": upd, "k_chol_step": upd, "k_chol_trsm_tc": tri,
-            "k_resid": resid, "k_resid_tc": resid, "k_gram": gram, "k_pred_sweep_tc": psweep, "k_pred_sweep": psweep,
-            "k_pred_rhs": prhs, "k_pred_rhs_tc": prhs}
+    psweep = prhs = pacc = 0.0
+    for nb_ in range(M):
+        for m in range(max(0, nb_ - B), nb_ + 1) if nu[nb_] else ():
+            n, b, nbl = ws[m]
+            psweep += nu[nb_] * n * n
+            prhs += 2.0 * nu[nb_] * n * s
+            pacc += 2.0 * nu[nb_] * (b if m < nb_ else n) * s
+    proj = 2.0 * (p.N + p.U) * s * s
+    f64 = 2.0 * s ** 3  # two FP64 factorisations (Sigma_SS, I + A), each s^3/3 + s^3/6 multiply-adds with L^-T
+    return {"k_chol_step_tc": step, "k_chol_wide": wide, "k_chol_trsm_tc": tri, "k_resid_tc": resid,
+            "k_gram_split": gram, "k_pred_rhs_tc": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
+            "k_f64_panel": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
-# one ncu capture of the same bench command (profiles/k_resid_tc_c2_b1.md),
-# valid only while the kernel sources hash to the value it was taken at.
-NCU_TRAFFIC = {"k_resid_tc": {"bytes": 85319680 + 177819904, "sources": "694f04d402204e14"}}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel from one ncu capture, {kernel: {"bytes": B, "sources": hash, "note": where}};
+# reported only while the kernel sources hash to the value it was taken at.
+NCU_TRAFFIC = {}
 
 
 def sources_hash() -> str:
@@ -103,8 +114,31 @@ def sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_step_tma", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
-                  "k_pred_rhs_tc"}
+TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_wide", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
+                  "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc"}
+FP64_KERNELS = {"k_f64_panel"}
+
+
+def roofline_of(name, flops, tot_ms, n_l, peaks):
+    """Achieved algorithmic rate of one kernel over its launches against its peak."""
+    achieved = flops / (tot_ms / 1e3) / 1e12
+    sm_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+    if name in TENSOR_KERNELS:
+        # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        peak = (peaks or {}).get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        r = {"bound": "tensor", "peak_note": "TF32 dense: measured bf16 burst (MEASURED_PEAKS.json) x 1.1/2.25 "
+             "nominal ratio; 3xTF32 issues 3 TF32 MMAs per algorithmic product, so frac <= 1/3",
+             "tensor_pipe_frac_issued": 3.0 * achieved / peak}
+    elif name in FP64_KERNELS:
+        peak = 1.25
+        r = {"bound": "alu", "peak_note": "FP64: nominal 1.25 TFLOP/s of this part (measured FP64 FMA rate "
+             "about 1.6 lane-ops/clk/SM = 1.0 TFLOP/s at 2070 MHz); a chain of dependent panel steps"}
+    else:
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        r = {"bound": "alu", "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived)"}
+    r.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+              "kernel": name, "launches_timed": n_l, "avg_launch_ms": tot_ms / n_l})
+    return r
 
 
 def predict_flops(p, B):
@@ -325,7 +359,7 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    work = kernel_work(p, args.B)
+    work = kernel_work(p, args.B, fused=(world == 1))
     if world > 1:  # equal shards: each rank does one draw's share
         work = {k: v / world for k, v in work.items()}
 
@@ -405,28 +439,16 @@ def main():
     roof = None
     if prof and dominant in prof:
         tot_ms, n_l = prof[dominant]
-        achieved = work[dominant] * args.steps / (tot_ms / 1e3) / 1e12
-        if dominant in TENSOR_KERNELS:
-            # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
-            bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
-            peak = bf16 * 1.1 / 2.25
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": dominant, "launches_timed": n_l,
-                    "avg_launch_ms": tot_ms / n_l,
-                    "peak_note": "TF32 dense: measured bf16 burst (MEASURED_PEAKS.json) x 1.1/2.25 nominal ratio; "
-                                 "3xTF32 issues 3 TF32 MMAs per algorithmic product, so frac <= 1/3",
-                    "tensor_pipe_frac_issued": 3.0 * achieved / peak}
-        else:
-            sm_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": dominant, "launches_timed": n_l, "avg_launch_ms": tot_ms / n_l,
-                    "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived, not measured)"}
+        roof = roofline_of(dominant, work[dominant] * args.steps, tot_ms, n_l, peaks)
         roof["work_per_step_gflop"] = work[dominant] / 1e9
         t = NCU_TRAFFIC.get(dominant)
         if t and t["sources"] == sources_hash() and world == 1:
             roof["traffic"] = t["bytes"]
-            roof["traffic_note"] = "ncu dram bytes read+write per launch (profiles/k_resid_tc_c2_b1.md)"
+            roof["traffic_note"] = t["note"]
+    # every modelled kernel of the untimed all-kernel profile (one step)
+    roof_all = {k: {kk: vv for kk, vv in roofline_of(k, work[k], v[0], v[1], peaks).items()
+                    if kk in ("bound", "achieved", "peak", "frac", "avg_launch_ms")}
+                for k, v in (prof_all or {}).items() if k in work and v[0] > 0}
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu, _ = cpu_baseline(p, args.B)
@@ -437,6 +459,7 @@ def main():
            "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
            "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+           "roofline_by_kernel": roof_all,
            "cpu_baseline": cpu, "fp64_gpu_form": fp64,
            "kernel_ms_one_step": {k: round(v[0], 4) for k, v in sorted((prof_all or {}).items(), key=lambda kv: -kv[1][0])}}
     if rank == 0:

@@ -210,7 +210,7 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_resid_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_pred_rhs_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_pred_rhs_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
     done = true;
@@ -462,20 +462,36 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     const int nte = (se + TB - 1) / TB;
     const int64_t nown = own_end - own_begin;
     const Win* wown = wd + (own_begin - w_begin);
-    const int nchunk = (int)std::min<int64_t>(nown, 32);
-    const int chunk = (int)((nown + nchunk - 1) / nchunk);
-    double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
-    int gtile = TB;
-    if (tc_err) {  // tensor cores: 128 x 128 tiles of the lower triangle
-      gtile = 128;
+    int nchunk = (int)std::min<int64_t>(nown, 32);
+    int chunk = (int)((nown + nchunk - 1) / nchunk);
+    std::vector<int2> tl;  // tensor cores: 128 x 128 tiles of the lower triangle
+    if (tc_err) {
       const int nt = (se + 127) / 128;
-      std::vector<int2> tl;
       for (int I = 0; I < nt; ++I)
         for (int J = 0; J <= I; ++J) tl.push_back(make_int2(I, J));
+      // window groups: (tile, group) items fill the SMs once
+      const int64_t ngr = std::max<int64_t>(1, std::min<int64_t>(nown, (int64_t)persistent_grid(1u << 30) / (int64_t)tl.size()));
+      chunk = (int)((nown + ngr - 1) / ngr);
+      nchunk = (int)((nown + chunk - 1) / chunk);
+    }
+    double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
+    int gtile = TB;
+    if (tc_err) {
+      gtile = 128;
+      int kmax = 32;
+      for (int64_t m = own_begin; m < own_end; ++m) {
+        const Win& w = mc.wins[m - w_begin];
+        kmax = std::max(kmax, (int)roundup(w.n - w.nB, 32));
+      }
+      float* shi = tmp.alloc<float>((size_t)nown * se * kmax);
+      float* slo = tmp.alloc<float>((size_t)nown * se * kmax);
+      launch("k_split_summary", k_split_summary, dim3(nblk(kmax), (unsigned)se, (unsigned)nown), NT, 0, st, wown,
+             (const float*)wbuf, se, kmax, shi, slo);
+      const CUtensorMap sh = rows_tensor_map(shi, nown * se, kmax), sl = rows_tensor_map(slo, nown * se, kmax);
       int2* tld = tmp.alloc<int2>(tl.size());
       stage_copy(tld, tl.data(), sizeof(int2) * tl.size(), st);
-      launch("k_gram_tc", k_gram_tc, dim3((unsigned)tl.size(), nchunk), comp_threads<RB>(), tc_resid_smem(), st,
-             (const int2*)tld, wown, (int)nown, chunk, (int)s, (const float*)wbuf, partial, tc_err);
+      launch("k_gram_split", k_gram_split, persistent_grid(tl.size() * nchunk), kSplitThreads, split_smem_bytes(), st,
+             (const int2*)tld, (int)tl.size(), (int)nown, chunk, se, kmax, sh, sl, partial, tc_err);
     } else {
       launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wown, (int)nown, chunk, (int)s, wbuf,
              partial);

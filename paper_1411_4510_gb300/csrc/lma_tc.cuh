@@ -1168,9 +1168,10 @@ __device__ __forceinline__ bool worker_sync_and(bool v) {
 }
 
 // Persistent loop over output tiles t = blockIdx.x, blockIdx.x + gridDim.x,
-// ... < ntiles, each hi + lo = sum over k < 32 nchunk of A(r, k) B(c, k)
-// with A rows [ya, ya + 128) of (ahi, alo) and B rows [yb, yb + 128) of
-// (bhi, blo), (ya, yb) = coords(t); rows outside the maps read zero.  The
+// ... < ntiles, each hi + lo = sum over its chunks c < chunks(t) of
+// sum_{k < 32} A(ya + r, x + k) B(yb + c', x + k) with (x, ya, yb) =
+// at(base, c) and base = coords(t) (computed once per tile by the producer):
+// A from (ahi, alo), B from (bhi, blo); rows outside the maps read zero.  The
 // producer and MMA warps run ahead into the next tile while the workers
 // finish the current one: before(t) (shared-memory set-up of the epilogue,
 // worker warps only, between two worker barriers), the drains, then
@@ -1178,14 +1179,13 @@ __device__ __forceinline__ bool worker_sync_and(bool v) {
 // columns 32 (w / 4) + j in hi[j] + lo[j].  Barrier phases run on across
 // tiles.  Every wait has an iteration limit: on a timeout all roles stop,
 // no copy is left landing, and false is returned in every thread.
-template <class Coords, class Before, class After>
+template <class Chunks, class Coords, class At, class Before, class After>
 __device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CUtensorMap* alo,
-                                 const CUtensorMap* bhi, const CUtensorMap* blo, int ntiles, int nchunk,
-                                 Coords coords, Before before, After after) {
+                                 const CUtensorMap* bhi, const CUtensorMap* blo, int ntiles, Chunks chunks,
+                                 Coords coords, At at, Before before, After after) {
   using namespace tc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &sm.abort;
-  const int ngroup = (nchunk + kSplitDrain - 1) / kSplitDrain;
   if (warp < kSplitWorkers) {
     const int q = warp & 3, half = warp >> 2;
     const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
@@ -1199,6 +1199,7 @@ __device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CU
       float hi[32], lo[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+      const int ngroup = (chunks(t) + kSplitDrain - 1) / kSplitDrain;
       for (int g = 0; g < ngroup && ok; ++g, ++G) {
         const int a = G & 1;
         int okw = 1;
@@ -1231,6 +1232,7 @@ __device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CU
     int C = 0, G = 0;  // chunks and groups issued so far by this CTA
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int nchunk = chunks(t);
       for (int c = 0; c < nchunk; ++c, ++C) {
         const int s = C % kSplitStages, a = G & 1;
         const bool first = (c % kSplitDrain) == 0, last = (c % kSplitDrain) == kSplitDrain - 1 || c == nchunk - 1;
@@ -1272,7 +1274,8 @@ __device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CU
     int C = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int2 y = coords(t);
+      const int4 base = coords(t);
+      const int nchunk = chunks(t);
       for (int c = 0; c < nchunk; ++c, ++C) {
         const int s = C % kSplitStages;
         int okw = 1;
@@ -1285,11 +1288,12 @@ __device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CU
         }
         if (lane == 0) {
           TcStage<128>& S = sm.st[s];
+          const int3 y = at(base, c);
           mbar_arrive_expect_tx(&sm.full[s], 4u * 128u * 32u * 4u);
-          tma_load_2d(S.a_hi, ahi, 32 * c, y.x, &sm.full[s]);
-          tma_load_2d(S.a_lo, alo, 32 * c, y.x, &sm.full[s]);
-          tma_load_2d(S.b_hi, bhi, 32 * c, y.y, &sm.full[s]);
-          tma_load_2d(S.b_lo, blo, 32 * c, y.y, &sm.full[s]);
+          tma_load_2d(S.a_hi, ahi, y.x, y.y, &sm.full[s]);
+          tma_load_2d(S.a_lo, alo, y.x, y.y, &sm.full[s]);
+          tma_load_2d(S.b_hi, bhi, y.x, y.z, &sm.full[s]);
+          tma_load_2d(S.b_lo, blo, y.x, y.z, &sm.full[s]);
         }
         __syncwarp();
       }
@@ -1351,11 +1355,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __res
   __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   split_setup(sm);
-  auto coords = [&](int t) -> int2 {
+  auto chunks = [&](int) { return nchunk; };
+  auto coords = [&](int t) -> int4 {
     const int4 it = items[t];
     const int base = nrev - (int)wins[it.x].g_end;  // reversed row of the window's local row 0
-    return make_int2(base + it.y * 128, base + it.z * RB);
+    return make_int4(base + it.y * 128, base + it.z * RB, 0, 0);
   };
+  auto at = [](int4 b, int c) { return make_int3(32 * c, b.x, b.y); };
   auto before = [&](int t) {
     const int4 it = items[t];
     const Win w = wins[it.x];
@@ -1396,54 +1402,75 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __res
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
     }
   };
-  const bool ok = split_persistent(sm, &vhi, &vlo, &vhi, &vlo, nitems, nchunk, coords, before, after);
+  const bool ok = split_persistent(sm, &vhi, &vlo, &vhi, &vlo, nitems, chunks, coords, at, before, after);
   if (!ok && tid == 0) atomicExch(err, 1);
   split_teardown(sm);
 }
 
-// Gram of the local summaries on the tensor cores (mixed form): after the
-// sweep, the extra rows of window m hold (L^-1 [r | Vt_W])^T, whose block
-// columns [nB, n) are [z_m | Z_m]^T (Definition 1 whitened), so
-// G = sum_m [z_m | Z_m]^T [z_m | Z_m] is a product of extra rows with K over
-// block points.  CTA (tile x of the lower 128-tiles of G, window chunk y)
-// adds the windows [chunk y, chunk y + chunk) with the compensated product
-// and writes hi + lo as FP64 partials, summed over chunks by k_gram_reduce.
-__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_gram_tc(const int2* __restrict__ tiles,
-                                                                 const Win* __restrict__ wins, int nwin, int chunk,
-                                                                 int s, const float* __restrict__ buf,
-                                                                 double* __restrict__ partial, int* __restrict__ err) {
+// Block-part summary rows of the owned windows, compacted and split for
+// k_gram_split: window wi's extra rows e < se = s + 1, columns [nB, n) (its
+// [z_m | Z_m]^T, Definition 1 whitened) go to rows wi se + e, columns
+// [0, n - nB) of (hi, lo), row length kmax (a multiple of 32, zero pad).
+__global__ void k_split_summary(const Win* __restrict__ wins, const float* __restrict__ buf, int se, int kmax,
+                                float* __restrict__ hi, float* __restrict__ lo) {
+  const Win w = wins[blockIdx.z];
+  const int e = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kmax) return;
+  const float x = (j < w.n - w.nB) ? buf[w.base + (int64_t)(w.npad + e) * w.npad + w.nB + j] : 0.f;
+  const float h = tc::tf32_round(x);
+  const int64_t o = ((int64_t)blockIdx.z * se + e) * kmax + j;
+  hi[o] = h;
+  lo[o] = tc::tf32_round(x - h);
+}
+
+// Gram of the local summaries on the tensor cores (mixed form), one
+// persistent CTA per SM: item t = (tile (I, J) of the lower 128-tiles of G,
+// window group g) adds sum over the windows of group g of
+// [z_m | Z_m]^T [z_m | Z_m] with split_persistent, whose K runs window by
+// window over the compacted rows of k_split_summary (kmax / 32 chunks each),
+// and writes hi + lo as FP64 partial g, summed over groups by k_gram_reduce.
+// Rows and columns past se read the next window's rows (or zeros) and are
+// never written.
+__global__ void __launch_bounds__(kSplitThreads, 1) k_gram_split(const int2* __restrict__ tiles, int ntile, int nwin,
+                                                    int group, int se, int kmax,
+                                                    const __grid_constant__ CUtensorMap shi,
+                                                    const __grid_constant__ CUtensorMap slo,
+                                                    double* __restrict__ partial, int* __restrict__ err) {
   using namespace tc;
-  const int2 tl = tiles[blockIdx.x];
-  const int se = s + 1, r0 = tl.x * 128, c0 = tl.y * RB;
-  const int w0 = blockIdx.y * chunk, w1 = min(nwin, w0 + chunk);
   extern __shared__ __align__(16) unsigned char smraw[];
-  CompSmem<RB>& sm = comp_smem<RB>(smraw);
+  SplitSmem& sm = split_smem(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  comp_setup(sm);
-  CompState cs;
-  float hi[32], lo[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
-  bool ok = true;
-  for (int wi = w0; wi < w1 && ok; ++wi) {
-    const Win w = wins[wi];
-    const float* E = buf + w.base + (int64_t)w.npad * w.npad;
-    const int64_t ld = w.npad;
-    auto rowA = [&](int r) -> const float* { return (r0 + r < se) ? E + (r0 + r) * ld : nullptr; };
-    auto rowB = [&](int c) -> const float* { return (c0 + c < se) ? E + (c0 + c) * ld : nullptr; };
-    ok = comp_product<RB, true>(sm, cs, w.nB, w.n, rowA, rowB, hi, lo);
-  }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  const int q = warp & 3, half = warp >> 2;
-  const int e1 = r0 + q * 32 + lane;
-  const int cg = c0 + half * 32;
-  if (ok && warp < RB / 8 && e1 < se) {
-    double* P = partial + (int64_t)blockIdx.y * se * se + (int64_t)e1 * se;
+  const int cpw = kmax / 32;
+  const int ngroup = (nwin + group - 1) / group;
+  split_setup(sm);
+  auto chunks = [&](int t) {
+    const int g = t / ntile;
+    return (min(nwin, (g + 1) * group) - g * group) * cpw;
+  };
+  auto coords = [&](int t) -> int4 {
+    const int2 tl = tiles[t % ntile];
+    return make_int4(tl.x * 128, tl.y * 128, (t / ntile) * group, 0);
+  };
+  auto at = [&](int4 b, int c) {
+    const int wi = b.z + c / cpw;
+    return make_int3(32 * (c % cpw), wi * se + b.x, wi * se + b.y);
+  };
+  auto before = [](int) {};
+  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
+    const int2 tl = tiles[t % ntile];
+    const int q = warp & 3, half = warp >> 2;
+    const int e1 = tl.x * 128 + q * 32 + lane;
+    const int cg = tl.y * 128 + half * 32;
+    if (e1 >= se) return;
+    double* P = partial + (int64_t)(t / ntile) * se * se + (int64_t)e1 * se;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (cg + j < se) P[cg + j] = (double)hi[j] + (double)lo[j];
-  }
-  comp_teardown(sm);
+  };
+  const bool ok = split_persistent(sm, &shi, &slo, &shi, &slo, ntile * ngroup, chunks, coords, at, before, after);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  split_teardown(sm);
 }
 
 // h[u][k] = sum over the pairs (n, m) of test block n of
@@ -1518,11 +1545,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_pred_rhs_tc(const Pair* __
   __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   split_setup(sm);
-  auto coords = [&](int t) -> int2 {
+  auto chunks = [&](int) { return nchunk; };
+  auto coords = [&](int t) -> int4 {
     const int4 it = items[t];
     const Pair pr = pairs[it.x];
-    return make_int2(pr.u0 + it.y * 128, nrev - (int)wins[pr.win].g_end + it.z * RB);
+    return make_int4(pr.u0 + it.y * 128, nrev - (int)wins[pr.win].g_end + it.z * RB, 0, 0);
   };
+  auto at = [](int4 b, int c) { return make_int3(32 * c, b.x, b.y); };
   auto before = [&](int t) {
     const int4 it = items[t];
     const Win w = wins[pairs[it.x].win];
@@ -1561,7 +1590,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_pred_rhs_tc(const Pair* __
       *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
     }
   };
-  const bool ok = split_persistent(sm, &uhi, &ulo, &vhi, &vlo, nitems, nchunk, coords, before, after);
+  const bool ok = split_persistent(sm, &uhi, &ulo, &vhi, &vlo, nitems, chunks, coords, at, before, after);
   if (!ok && tid == 0) atomicExch(err, 1);
   split_teardown(sm);
 }
