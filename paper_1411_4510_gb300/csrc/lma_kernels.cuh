@@ -778,7 +778,21 @@ __global__ void k_ew_f32(const Win* __restrict__ wins, const float* __restrict__
   if (c >= w.npad) return;
   const float* E = buf + w.base + (int64_t)w.npad * w.npad;
   float hi = 0.f, lo = 0.f;
-  for (int k = 0; k < s; ++k) {
+  int k = 0;
+  for (; k + 8 <= s; k += 8) {  // eight loads in flight ahead of the dependent sums
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = E[(int64_t)(1 + k + q) * w.npad + c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 b = bs[k + q];
+      const float p = b.x * x[q];
+      const float e = fmaf(b.x, x[q], -p);
+      lo += fmaf(b.y, x[q], e);
+      two_sum(hi, lo, p);
+    }
+  }
+  for (; k < s; ++k) {
     const float x = E[(int64_t)(1 + k) * w.npad + c];
     const float2 b = bs[k];
     const float p = b.x * x;
@@ -999,6 +1013,22 @@ __global__ void __launch_bounds__(NT) k_var_gemm(const T* __restrict__ h, int64_
     for (int q = 0; q < 16; ++q) v += red[threadIdx.x][q];
     if (u0 + threadIdx.x < U) partial[(int64_t)blockIdx.x * U + u0 + threadIdx.x] = v;
   }
+}
+
+// out[u] = |g_u|^2 (FP64 sum) for g = L_C^-1 h formed by k_proj128 (U rows of
+// s values): the variance term of k_var_gemm as one partial (ntile = 1).
+__global__ void k_row_sqnorm(const float* __restrict__ g, int64_t U, int s, double* __restrict__ out) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= U) return;
+  double v = 0.0;
+  for (int k = lane; k < s; k += 32) {
+    const double q = (double)g[row * s + k];
+    v += q * q;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) out[row] = v;
 }
 
 // g_u = L_C^-1 h_u for the block covariance: g[u][i] = sum_k h[u][k] LcT[k][i]

@@ -884,7 +884,16 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     launch("k_pred_t12", k_pred_t12<T>, nblk((int64_t)it_t12.size() * 32), NT, 0, st, pd, itd, (int)it_t12.size(), mc.wins_d, Pbuf,
                                                                     (const T*)mc.ew, t1, t2);
     double* part = tmp.alloc<double>((size_t)nst * U);
-    launch("k_var_gemm", k_var_gemm<T>, dim3(nst, nblk(U, TB)), NT, 0, st, h, U, (int)s, (const T*)mc.LcT, part);
+    int ntile_var = nst;
+    if (sizeof(T) == 4 && s % 4 == 0) {  // L_C^-1 h with the 128 x 128 FP32 product, then row norms
+      float* g = tmp.alloc<float>((size_t)U * s);
+      launch("k_var_gemm", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)h, U, (int)s,
+             (const float*)mc.LcT, g, (int)s);
+      launch("k_row_sqnorm", k_row_sqnorm, nblk(U * 32), NT, 0, st, (const float*)g, U, (int)s, part);
+      ntile_var = 1;
+    } else {
+      launch("k_var_gemm", k_var_gemm<T>, dim3(nst, nblk(U, TB)), NT, 0, st, h, U, (int)s, (const T*)mc.LcT, part);
+    }
     double* md = mean;
     double* vd = var;
     if (!on_device) {
@@ -892,7 +901,8 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       vd = tmp.alloc<double>(U);
     }
     const double prior = mc.ss2 + (noisy ? mc.sn2 : 0.0);
-    launch("k_pred_final", k_pred_final<T>, nblk(U * 32), NT, 0, st, Vu, U, (int)s, mc.beta, t1, t2, part, nst, mc.mu, prior, md, vd);
+    launch("k_pred_final", k_pred_final<T>, nblk(U * 32), NT, 0, st, Vu, U, (int)s, mc.beta, t1, t2, part, ntile_var,
+           mc.mu, prior, md, vd);
     if (cov) {  // covariance of each test block, packed row-major block after block
       std::vector<int64_t> off(M, 0);
       std::vector<int4> it_c;
