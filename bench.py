@@ -254,6 +254,7 @@ def cpu_baseline(p, B, n_blocks=6):
 def run_reference(args, p):
     """Reference arm: the FP64 CPU oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     import numpy as np  # noqa: F401

@@ -121,14 +121,19 @@ lma_status lma_predict_cov(const lma_model* model, int64_t u, const double* XU,
                            const int64_t* test_block_ptr, int noisy, int io_on_device,
                            double* mean_out, double* var_out, double* cov_out);
 
-/* lma_fit followed by lma_predict in one call, with the same results: the
- * FP64 global step (Definition 2) runs on a library-owned second stream
- * while the prediction's kernels that do not need its results run on
- * cuda_stream, and the rest of the prediction waits for it.  Arguments as in
- * lma_fit and lma_predict; `out` may be NULL (the model is then freed) or
- * receives the model (free with lma_model_free).  Outputs are valid when the
- * call returns.  Errors as in lma_fit and lma_predict; on an error nothing
- * is returned in *out.                                                     */
+/* lma_fit followed by lma_predict in one call: the FP64 global step
+ * (Definition 2) runs on a library-owned second stream while the
+ * prediction's kernels that do not need its results run on cuda_stream, and
+ * the rest of the prediction waits for it.  In the mixed form the test
+ * points' right-hand sides R_{W_m u} are appended to the window buffers as
+ * extra rows, so the fit's own sweep turns them into the rows
+ * (L_m^-1 R_{W_m u})^T of the local route (Lemma 1) and no separate
+ * prediction sweep runs: the results equal lma_fit + lma_predict to FP32
+ * accuracy (the FP64 form's exactly).  Arguments as in lma_fit and
+ * lma_predict; `out` may be NULL (the model is then freed) or receives the
+ * model (free with lma_model_free).  Outputs are valid when the call
+ * returns.  Errors as in lma_fit and lma_predict; on an error nothing is
+ * returned in *out.                                                        */
 lma_status lma_fit_predict(const lma_problem* problem, const lma_hyper* hyper,
                            const lma_options* options, int64_t u, const double* XU,
                            const int64_t* test_block_ptr, int noisy, int io_on_device,

@@ -152,7 +152,9 @@ def lma_predict_cov(model: Model, XU, test_block_ptr, noisy: bool = True):
 def lma_fit_predict(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, XU, test_block_ptr, jitter=1e-6,
                     mean=0.0, precision=MIXED, noisy: bool = True, stream=None, keep_model: bool = False):
     """lma_fit + lma_predict in one call (the global step overlaps the
-    prediction).  Returns (mean, var) or (mean, var, model) with keep_model."""
+    prediction; in the mixed form the test right-hand sides ride the fit's
+    sweep as extra window rows).  Returns (mean, var) or (mean, var, model)
+    with keep_model."""
     lib = _abi.load()
     keep = []
     prob, hyp, opt = _structs(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter, mean,
