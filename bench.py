@@ -99,7 +99,9 @@ def kernel_work(p, B, fused=True):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
 # kernel from one ncu capture, {kernel: {"bytes": B, "sources": hash, "note": where}};
 # reported only while the kernel sources hash to the value it was taken at.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"k_f64_panel": {"bytes": 876955, "sources": "e4e0c94931480e8b",
+                               "note": "ncu dram bytes read+write per launch, mean of one fit's 66 launches "
+                                       "(identical for every N at |S| = 512; profiles/k_f64_panel_s512.md)"}}
 
 
 def sources_hash() -> str:
