@@ -97,20 +97,27 @@ def kernel_work(p, B, fused=True):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# kernel from one ncu capture, {kernel: {"bytes": B, "sources": hash, "note": where}};
-# reported only while the kernel sources hash to the value it was taken at.
-NCU_TRAFFIC = {"k_f64_panel": {"bytes": 876955, "sources": "e4e0c94931480e8b",
+# kernel from one ncu capture, {kernel: {"bytes": B, "files": the csrc files that
+# define and launch it, "sources": their hash then, "note": where}}; reported
+# only while those files still hash to the value the capture was taken at.
+F64_FILES = ["lma_f64.cuh", "lma_kernels.cuh", "lma_types.cuh", "lma_lib.cu"]  # define and launch k_f64_panel
+NCU_TRAFFIC = {"k_f64_panel": {"bytes": 876955, "files": F64_FILES, "sources": "9f0886dd254e9574",
                                "note": "ncu dram bytes read+write per launch, mean of one fit's 66 launches "
                                        "(identical for every N at |S| = 512; profiles/k_f64_panel_s512.md)"}}
 
 
-def sources_hash() -> str:
+def sources_hash(files=None) -> str:
+    """sha256 prefix of the given csrc/ files (default: all sources and the header)."""
     import glob
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
+    if files:
+        paths = [os.path.join(here, "paper_1411_4510_gb300", "csrc", f) for f in files]
+    else:
+        paths = sorted(glob.glob(os.path.join(here, "paper_1411_4510_gb300", "csrc", "*.cu*"))
+                       + glob.glob(os.path.join(here, "include", "*.h")))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(here, "paper_1411_4510_gb300", "csrc", "*.cu*"))
-                    + glob.glob(os.path.join(here, "include", "*.h"))):
+    for f in paths:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -445,7 +452,7 @@ def main():
         roof = roofline_of(dominant, work[dominant] * args.steps, tot_ms, n_l, peaks)
         roof["work_per_step_gflop"] = work[dominant] / 1e9
         t = NCU_TRAFFIC.get(dominant)
-        if t and t["sources"] == sources_hash() and world == 1:
+        if t and t["sources"] == sources_hash(t.get("files")) and world == 1:
             roof["traffic"] = t["bytes"]
             roof["traffic_note"] = t["note"]
     # every modelled kernel of the untimed all-kernel profile (one step)

@@ -94,8 +94,14 @@ typedef struct {
  * Per block m the residual R (Section 3: R = Sigma - Q, Q_BB' =
  * Sigma_BS Sigma_SS^-1 Sigma_SB') over D_m u D^B_m is factorised blanket-first
  * so that its trailing factor is a square root of R-dot_m^-1 (Lemma 1).
- * *out receives a model owned by the library.  Returns LMA_ERR_NOT_PD when a
- * window is not positive definite in the selected precision.               */
+ * *out receives a model owned by the library.  In the mixed form a window
+ * whose FP32 factorisation loses positive definiteness makes the library
+ * redo the fit in the FP64 form (same problem and hyperparameters, no added
+ * jitter); the model is then an FP64 model (lma_model_precision).  The same
+ * holds for lma_fit_local, lma_fit_predict, lma_loglik and lma_loglik_grad.
+ * Returns LMA_ERR_NOT_PD when a window is not positive definite in FP64
+ * either, or when Sigma_SS or I + A (factorised in FP64 in both forms) is
+ * not.                                                                     */
 lma_status lma_fit(const lma_problem* problem, const lma_hyper* hyper,
                    const lma_options* options, lma_model** out);
 
@@ -212,6 +218,10 @@ lma_status lma_window_residual(const lma_problem* problem, const lma_hyper* hype
 int64_t lma_window_rows(const lma_problem* problem, int64_t m);
 
 void lma_model_free(lma_model* model);
+
+/* The form a model was fitted in: the requested one, or LMA_FP64 after the
+ * mixed form's FP64 retry (lma_fit).  LMA_FP64 for NULL.                   */
+lma_precision lma_model_precision(const lma_model* model);
 
 const char* lma_status_string(lma_status status);
 

@@ -300,6 +300,12 @@ if torch is not None:
         return LMALogLik.apply(log_ell, log_sigma_s, log_sigma_n, data)
 
 
+def lma_model_precision(model) -> int:
+    """FP64 or MIXED: the form the model was fitted in (FP64 after the mixed
+    form's FP64 retry of a window that lost positive definiteness in FP32)."""
+    return int(_abi.load().lma_model_precision(model.handle))
+
+
 def profile_start(name_filter: str = "") -> None:
     """Bracket matching kernel launches with CUDA events (see lma_profile_start)."""
     _abi.load().lma_profile_start(name_filter.encode())

@@ -120,6 +120,33 @@ static lma_status guarded(F f) {
   return LMA_OK;
 }
 
+// The mixed form factorises the windows in FP32, which can lose positive
+// definiteness where FP64 does not (a residual whose smallest eigenvalue is
+// below the FP32 rounding of its O(sigma_s^2) entries).  Such a fit is redone
+// in the FP64 form with the same problem and hyperparameters (no jitter is
+// added: that would change R); the model is then an FP64 model
+// (lma_model_precision).  Sigma_SS and I + A (failed block -1 / -2) are
+// factorised in FP64 in both forms and are not retried.
+static bool retry_in_fp64(lma_status st, lma_precision prec) {
+  return st == LMA_ERR_NOT_PD && prec == LMA_MIXED && err().block >= 0;
+}
+
+static void drop_model(lma_model* md) {
+  md->core.keep.release();
+  cudaStreamSynchronize(md->core.st);
+  delete md;
+}
+
+// A fresh model on the caller's stream in the given form.
+static lma_model* new_model(const lma_options* O, lma_precision prec) {
+  lma_model* md = new (std::nothrow) lma_model();
+  if (!md) return nullptr;
+  md->core.prec = prec;
+  md->core.st = (cudaStream_t)O->cuda_stream;
+  md->core.keep.st = md->core.st;
+  return md;
+}
+
 }  // namespace lma
 
 using namespace lma;
@@ -142,10 +169,14 @@ lma_status lma_fit(const lma_problem* P, const lma_hyper* H, const lma_options* 
     else
       Impl<double>::fit(md->core, P, H);
   });
+  if (retry_in_fp64(st, O->precision)) {
+    drop_model(md);
+    md = new_model(O, LMA_FP64);
+    if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+    st = guarded([&] { Impl<double>::fit(md->core, P, H); });
+  }
   if (st != LMA_OK) {
-    md->core.keep.release();
-    cudaStreamSynchronize(md->core.st);
-    delete md;
+    drop_model(md);
     return st;
   }
   *out = md;
@@ -174,10 +205,17 @@ lma_status lma_fit_local(const lma_problem* P, const lma_hyper* H, const lma_opt
       Impl<double>::check(md->core, false, 0, true);
     }
   });
+  if (retry_in_fp64(st, O->precision)) {
+    drop_model(md);
+    md = new_model(O, LMA_FP64);
+    if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+    st = guarded([&] {
+      Impl<double>::fit_local(md->core, P, H, win_begin, own_begin, own_end);
+      Impl<double>::check(md->core, false, 0, true);
+    });
+  }
   if (st != LMA_OK) {
-    md->core.keep.release();
-    cudaStreamSynchronize(md->core.st);
-    delete md;
+    drop_model(md);
     return st;
   }
   *out = md;
@@ -264,10 +302,16 @@ lma_status lma_fit_predict(const lma_problem* P, const lma_hyper* H, const lma_o
     else
       Impl<double>::fit_predict(md->core, P, H, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
   });
+  if (retry_in_fp64(st, O->precision)) {  // the outputs are written again by the FP64 run
+    drop_model(md);
+    md = new_model(O, LMA_FP64);
+    if (!md) return fail(LMA_ERR_OOM, "host allocation failed");
+    st = guarded([&] {
+      Impl<double>::fit_predict(md->core, P, H, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
+    });
+  }
   if (st != LMA_OK || !out) {
-    md->core.keep.release();
-    cudaStreamSynchronize(md->core.st);
-    delete md;
+    drop_model(md);
     return st;
   }
   *out = md;
@@ -332,8 +376,19 @@ lma_status lma_loglik_grad(const lma_problem* P, const lma_hyper* H, const lma_o
   });
   mc.keep.release();
   cudaStreamSynchronize(mc.st);
+  if (retry_in_fp64(st, O->precision)) {
+    ModelCore m64;
+    m64.prec = LMA_FP64;
+    m64.st = mc.st;
+    m64.keep.st = mc.st;
+    st = guarded([&] { Impl<double>::loglik_grad(m64, P, H, ll, grad); });
+    m64.keep.release();
+    cudaStreamSynchronize(m64.st);
+  }
   return st;
 }
+
+lma_precision lma_model_precision(const lma_model* md) { return md ? md->core.prec : LMA_FP64; }
 
 lma_status lma_model_summary(const lma_model* md, double* A_out, double* y_out, double* sc) {
   if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");

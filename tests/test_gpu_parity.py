@@ -199,6 +199,30 @@ def test_c2_shaped_fit_predict(L, B):
         assert rel(var, v) <= tol_v, (prec, rel(var, v))
 
 
+def test_mixed_window_failure_retries_in_fp64(L):
+    """Duplicated training points with sigma_n^2 = 1e-10: each duplicate pair
+    gives the residual an eigenvalue near 2 sigma_n^2, far below the FP32
+    rounding of its O(sigma_s^2) entries and far above FP64's, so the mixed
+    form's FP32 window factorisation fails and the fit is redone in FP64."""
+    from workloads import make_random_problem
+    p = make_random_problem(7, (60, 60, 60), d=2, s=20, B=1, test_sizes=(5, 5, 5))
+    X = p.X.copy()
+    X[1::2] = X[0::2]
+    p.X = X
+    p.log_sigma_n = -11.5
+    args = L.problem_args(p)
+    m64 = L.lma_fit(precision=L.FP64, **args)
+    assert L.lma_model_precision(m64) == L.FP64
+    mean64, var64 = L.lma_predict(m64, p.XU, p.test_block_ptr)
+    mm = L.lma_fit(precision=L.MIXED, **args)
+    assert L.lma_model_precision(mm) == L.FP64
+    mean, var = L.lma_predict(mm, p.XU, p.test_block_ptr)
+    assert np.array_equal(mean, mean64) and np.array_equal(var, var64)
+    mean2, var2 = L.lma_fit_predict(XU=p.XU, test_block_ptr=p.test_block_ptr, precision=L.MIXED, **args)
+    assert np.array_equal(mean2, mean64) and np.array_equal(var2, var64)
+    assert L.lma_loglik(precision=L.MIXED, **args) == L.lma_model_loglik(m64)
+
+
 def test_single_block_and_tiny_sizes(L):
     from workloads import make_random_problem
     for case in [((37,), 0, 1, 1, (5,)), ((1, 1, 1), 1, 1, 1, (1, 0, 2)), ((3, 200), 1, 2, 3, (0, 4))]:
