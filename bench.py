@@ -312,6 +312,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--dominant", default="auto")
+    ap.add_argument("--trace", default=None,
+                    help="write the per-launch trace (kernel, start ms, end ms; CUDA events around every launch, "
+                         "all streams) of the untimed profiled step to this JSON file (rank 0)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "lma" else args.warmup
 
@@ -373,7 +376,9 @@ def main():
     if world > 1:  # equal shards: each rank does one draw's share
         work = {k: v / world for k, v in work.items()}
 
-    def timed(nsteps, prec=L.MIXED, host=None, profile=None):
+    trace = []
+
+    def timed(nsteps, prec=L.MIXED, host=None, profile=None, keep_trace=False):
         evs = []
         n0 = L.lma_kernel_launch_count()
         if world > 1:
@@ -391,6 +396,8 @@ def main():
             b.record(st)
             evs.append((a, b))
         torch.cuda.synchronize()
+        if profile and keep_trace:
+            trace[:] = L.profile_trace()
         prof = L.profile_stop() if profile else None
         if world > 1:
             dist.barrier()
@@ -399,7 +406,10 @@ def main():
 
     # pick the dominant kernel from an untimed all-kernel profile of one step,
     # then bracket only its launches inside the timed region
-    _, _, prof_all, _ = timed(1, profile="k_")
+    _, _, prof_all, _ = timed(1, profile="k_", keep_trace=bool(args.trace))
+    if args.trace and rank == 0:
+        with open(args.trace, "w") as fh:
+            json.dump([{"kernel": k, "start_ms": a, "end_ms": b} for k, a, b in trace], fh)
     dominant = args.dominant
     if dominant == "auto":
         known = {k: v for k, v in prof_all.items() if k in work}
