@@ -1,21 +1,36 @@
 #!/usr/bin/env python
-"""LMA fit+predict throughput on one GB300 (or N replicas under torchrun).
+"""LMA fit+predict throughput on one GB300 (or N GPUs under torchrun).
 
-One step = the whole hot path on one batch of synthetic input: lma_fit (SE-ARD
-blocks, residual windows, blanket-first factorisations and solves, local
-summaries reduced into the global summary, the FP64 global step) followed by
-lma_predict on the test set (local route).  The workload is the C2
-configuration: N=40,960 5-D inputs, |S|=512, 64 blocks of 640 in k-means
-order, Markov order B (default 1), 4,096 test points.
+One step = the whole hot path on one batch of synthetic input, through one
+C-ABI call (lma_fit_predict, mixed form): SE-ARD covariances, the support-set
+projection, residual windows, blanket-first factorisations and solves, local
+summaries reduced into the global summary, the FP64 global step and the
+local-route prediction of every test point.
 
-Metric: training points per second of fit+predict (and TFLOP/s of the
-algorithmic flop count), mixed form, next to the plain FP64 GPU form and the
-FP64 CPU oracle timed on the host cores on a bounded sample.
+Workload (default): C4, the largest configuration that fits one GPU —
+N = 2,000,000 inputs in [0,1]^8, |S| = 2,048, 2,000 Morton-ordered blocks of
+1,000, Markov order B = 1, 100,000 test points (the EMSLP scale of the
+paper's Table 3, synthetic).  `--config C1..C5` selects another.
+
+Metric: training points per second of fit+predict, next to
+  * TFLOP/s of the algorithmic flop count and the roofline of the dominant
+    kernel (timed in a separate pass, so that no profiler event sits in the
+    headline's timed region);
+  * e2e: the same call with pinned host buffers (copies inside);
+  * the plain FP64 GPU form (per-window launches), timed on the first blocks
+    and extrapolated linearly in the block count (the fit is a sum of
+    independent per-block terms, Definition 2);
+  * the errors of the mixed form against the FP64 oracle's stored values
+    (tests/golden, written by tests/golden/make_golden.py from oracle/ only);
+  * the gradient of the log-likelihood (lma_loglik_grad) on C5;
+  * the FP64 CPU oracle timed on the host cores on the first blocks.
 `--impl reference` times that oracle alone (the reference arm).
+`--mode step` runs only the warm-up and the timed steps (for profilers).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -28,14 +43,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "LMA fit+predict train-points/s"
+DTYPE = "mixed: f32 factorisations with 3xTF32 tensor-core products, f64 support-set and global steps"
 CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+GOLDEN = {("C2", 1): "c2_b1", ("C2", 2): "c2_b2", ("C3", 2): "c3", ("C4", 1): "c4", ("C5", 2): "c5"}
+PARTITION = {"C1": "sorted by x1", "C2": "k-means order", "C3": "k-means clusters, uneven",
+             "C4": "Morton order", "C5": "Morton order"}
 
 
 # ----------------------------------------------------------------------------
-# algorithmic counts (flop = 2 per multiply-add)
+# algorithmic counts (flop = 2 per multiply-add; triangles count half)
 def window_sizes(bptr, B):
+    """(n_m, b_m, |D^B_m|) of every window D_m u D^B_m."""
     M = len(bptr) - 1
     out = []
     for m in range(M):
@@ -45,6 +66,8 @@ def window_sizes(bptr, B):
 
 
 def fit_flops(p, B):
+    """N s^2 (V) + sum_m [s n^2 (R) + n^3/3 (Cholesky) + n^2 (s+1) (solve) + b s^2 (summary)]
+    + 2 s^3/3 (the Cholesky factorisations of Sigma_SS and I + A)."""
     s, N = p.s, p.N
     f = N * s * s + 2.0 * s ** 3 / 3.0
     for n, b, nb in window_sizes(p.block_ptr, B):
@@ -52,17 +75,28 @@ def fit_flops(p, B):
     return f
 
 
-def sweep_flops(p, B):
-    """Factorisation + solve of every window (Cholesky n^3/3 and the s+1 right-hand sides n^2 (s+1))."""
+def predict_flops(p, B):
+    """2 U s^2 (test projection and variance term) + per (test block, window)
+    pair: the right-hand sides 2 n s, their solve n^2, the h accumulation 2 kept s."""
     s = p.s
-    return sum(n ** 3 / 3.0 + n * n * (s + 1) for n, _, _ in window_sizes(p.block_ptr, B))
+    ws = window_sizes(p.block_ptr, B)
+    tp = p.test_block_ptr
+    f = 2.0 * p.U * s * s
+    for nb in range(p.M):
+        nu = int(tp[nb + 1] - tp[nb])
+        if nu == 0:
+            continue
+        for m in range(max(0, nb - B), nb + 1):
+            n, b, nbl = ws[m]
+            kept = n if m == nb else b
+            f += nu * (2.0 * n * s + n * n + 2.0 * kept * s)
+    return f
 
 
 def kernel_work(p, B, fused=True):
-    """Algorithmic flops per step of the main kernels (flop = 2 per multiply-add;
-    triangles count half).  fused: lma_fit_predict's mixed form, whose windows
-    carry the test right-hand sides as extra rows solved by the fit's sweep
-    (no separate prediction sweep)."""
+    """Algorithmic flops per step of the main kernels.  fused: lma_fit_predict's
+    mixed form, whose windows carry the test right-hand sides as extra rows
+    solved by the fit's sweep (no separate prediction sweep)."""
     s, M = p.s, p.M
     ws = window_sizes(p.block_ptr, B)
     tp = p.test_block_ptr
@@ -89,8 +123,8 @@ def kernel_work(p, B, fused=True):
             psweep += nu[nb_] * n * n
             prhs += 2.0 * nu[nb_] * n * s
             pacc += 2.0 * nu[nb_] * (b if m < nb_ else n) * s
-    proj = 2.0 * (p.N + p.U) * s * s
-    f64 = 2.0 * s ** 3  # two FP64 factorisations (Sigma_SS, I + A), each s^3/3 + s^3/6 multiply-adds with L^-T
+    proj = (p.N + p.U) * s * s           # V = L^-1 K_SD: s^2 / 2 multiply-adds per point (triangular)
+    f64 = 2.0 * s ** 3 / 3.0             # Cholesky of Sigma_SS and of I + A, s^3 / 6 multiply-adds each
     return {"k_chol_step_tc": step, "k_chol_wide": wide, "k_chol_trsm_tc": tri, "k_resid_tc": resid,
             "k_gram_split": gram, "k_pred_rhs_tc": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
             "k_f64_panel": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
@@ -100,22 +134,17 @@ def kernel_work(p, B, fused=True):
 # kernel from one ncu capture, {kernel: {"bytes": B, "files": the csrc files that
 # define and launch it, "sources": their hash then, "note": where}}; reported
 # only while those files still hash to the value the capture was taken at.
-F64_FILES = ["lma_f64.cuh", "lma_kernels.cuh", "lma_types.cuh", "lma_lib.cu"]  # define and launch k_f64_panel
-NCU_TRAFFIC = {"k_f64_panel": {"bytes": 876955, "files": F64_FILES, "sources": "9f0886dd254e9574",
-                               "note": "ncu dram bytes read+write per launch, mean of one fit's 66 launches "
-                                       "(identical for every N at |S| = 512; profiles/k_f64_panel_s512.md)"}}
+NCU_TRAFFIC: dict = {}
 
 
 def sources_hash(files=None) -> str:
     """sha256 prefix of the given csrc/ files (default: all sources and the header)."""
     import glob
-    import hashlib
-    here = os.path.dirname(os.path.abspath(__file__))
     if files:
-        paths = [os.path.join(here, "paper_1411_4510_gb300", "csrc", f) for f in files]
+        paths = [os.path.join(ROOT, "paper_1411_4510_gb300", "csrc", f) for f in files]
     else:
-        paths = sorted(glob.glob(os.path.join(here, "paper_1411_4510_gb300", "csrc", "*.cu*"))
-                       + glob.glob(os.path.join(here, "include", "*.h")))
+        paths = sorted(glob.glob(os.path.join(ROOT, "paper_1411_4510_gb300", "csrc", "*.cu*"))
+                       + glob.glob(os.path.join(ROOT, "include", "*.h")))
     h = hashlib.sha256()
     for f in paths:
         with open(f, "rb") as fh:
@@ -126,44 +155,35 @@ def sources_hash(files=None) -> str:
 TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_wide", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
                   "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc"}
 FP64_KERNELS = {"k_f64_panel"}
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rate of the part
+FP64_PEAK = 1.25             # nominal FP64 TFLOP/s of the part (no measured figure)
 
 
-def roofline_of(name, flops, tot_ms, n_l, peaks):
+def roofline_of(name, flops, tot_ms, n_l, peaks, sustained=True):
     """Achieved algorithmic rate of one kernel over its launches against its peak."""
     achieved = flops / (tot_ms / 1e3) / 1e12
-    sm_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+    pk = peaks or {}
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
     if name in TENSOR_KERNELS:
-        # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
-        peak = (peaks or {}).get("bf16_tflops", 1900.0) * 1.1 / 2.25
-        r = {"bound": "tensor", "peak_note": "TF32 dense: measured bf16 burst (MEASURED_PEAKS.json) x 1.1/2.25 "
-             "nominal ratio; 3xTF32 issues 3 TF32 MMAs per algorithmic product, so frac <= 1/3",
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        src = "measured" if key in pk else "fallback"
+        bf16 = pk.get(key, 1700.0 if sustained else 1900.0)
+        peak = bf16 * TF32_PER_BF16
+        r = {"bound": "tensor",
+             "peak_note": f"TF32 dense = {src} bf16 {'sustained' if sustained else 'burst'} "
+                          f"({bf16:.1f} TFLOP/s, MEASURED_PEAKS.json) x 1.1/2.25 (nominal TF32/BF16 ratio), "
+                          f"of {src}; 3xTF32 issues three TF32 MMAs per algorithmic product, so frac <= 1/3",
              "tensor_pipe_frac_issued": 3.0 * achieved / peak}
     elif name in FP64_KERNELS:
-        peak = 1.25
-        r = {"bound": "alu", "peak_note": "FP64: nominal 1.25 TFLOP/s of this part (measured FP64 FMA rate "
-             "about 1.6 lane-ops/clk/SM = 1.0 TFLOP/s at 2070 MHz); a chain of dependent panel steps"}
+        peak = FP64_PEAK
+        r = {"bound": "alu", "peak_note": "FP64: the part's nominal 1.25 TFLOP/s (derived; a microbenchmark "
+             "on the box measured 1.6 FP64 FMA/clk/SM = 1.0 TFLOP/s at 2070 MHz)"}
     else:
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         r = {"bound": "alu", "peak_note": "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (derived)"}
     r.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
               "kernel": name, "launches_timed": n_l, "avg_launch_ms": tot_ms / n_l})
     return r
-
-
-def predict_flops(p, B):
-    s = p.s
-    ws = window_sizes(p.block_ptr, B)
-    tp = p.test_block_ptr
-    f = 2.0 * p.U * s * s
-    for nb in range(p.M):
-        nu = int(tp[nb + 1] - tp[nb])
-        if nu == 0:
-            continue
-        for m in range(max(0, nb - B), nb + 1):
-            n, b, nbl = ws[m]
-            kept = n if m == nb else b
-            f += nu * (2.0 * n * s + n * n + 2.0 * kept * s)
-    return f
 
 
 # ----------------------------------------------------------------------------
@@ -234,19 +254,25 @@ def load_peaks():
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline(p, B, n_blocks=6):
-    """FP64 oracle (as it stands) on the first n_blocks blocks of the workload:
-    fit + local-route prediction of their test points, on the host cores."""
-    import numpy as np
-    from oracle import lma_oracle as O2
+def sub_problem(p, k, B=None):
+    """The first k blocks of problem p (their training and test points, the
+    same support set and hyperparameters); B clipped to k - 1."""
     from workloads.synth import Problem
-    k = min(n_blocks, p.M)
+    k = min(int(k), p.M)
     nsub = int(p.block_ptr[k])
     usub = int(p.test_block_ptr[k])
-    sub = Problem(name=p.name + "-sample", X=p.X[:nsub], y=p.y[:nsub], block_ptr=p.block_ptr[:k + 1].copy(),
-                  S=p.S, XU=p.XU[:usub], yU=p.yU[:usub], test_block_ptr=p.test_block_ptr[:k + 1].copy(),
-                  log_ell=p.log_ell, log_sigma_s=p.log_sigma_s, log_sigma_n=p.log_sigma_n, jitter=p.jitter,
-                  mean=p.mean, B=min(B, k - 1))
+    B = p.B if B is None else B
+    return Problem(name=f"{p.name}[:{k}]", X=p.X[:nsub], y=p.y[:nsub], block_ptr=p.block_ptr[:k + 1].copy(),
+                   S=p.S, XU=p.XU[:usub], yU=p.yU[:usub], test_block_ptr=p.test_block_ptr[:k + 1].copy(),
+                   log_ell=p.log_ell, log_sigma_s=p.log_sigma_s, log_sigma_n=p.log_sigma_n, jitter=p.jitter,
+                   mean=p.mean, B=min(B, k - 1))
+
+
+def cpu_baseline(p, B, n_blocks):
+    """FP64 oracle (as it stands) on the first n_blocks blocks of the workload:
+    fit + local-route prediction of their test points, on the host cores."""
+    from oracle import lma_oracle as O2
+    sub = sub_problem(p, n_blocks, B)
     t0 = time.perf_counter()
     f = O2.fit(sub)
     O2.predict(f)
@@ -255,30 +281,81 @@ def cpu_baseline(p, B, n_blocks=6):
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
         if os.environ.get(v):
             cores = int(os.environ[v])
-    return dict(value=nsub / dt, unit="train-points/s", cores=cores, kind="oracle",
-                sample=f"first {k} of {p.M} blocks ({nsub} training points, {usub} test points), "
-                       f"same |S|={p.s}, B={sub.B}; fit+predict in {dt:.1f} s"), dt
+    return dict(value=sub.N / dt, unit="train-points/s", cores=cores, kind="oracle",
+                sample=f"first {sub.M} of {p.M} blocks ({sub.N} training points, {sub.U} test points), "
+                       f"same |S|={p.s}, B={sub.B}; fit+predict in {dt:.1f} s (one sample per step)"), dt
+
+
+def workload_config(p, B, world=1, reduced=False):
+    tag = p.name if not reduced else f"{p.name} (reduced)"
+    c = {"workload": f"{tag}: N={p.N} d={p.d} |S|={p.s} M={p.M} blocks "
+                     f"({PARTITION.get(p.name, '')}, sizes {int(p.block_sizes().min())}-{int(p.block_sizes().max())}) "
+                     f"B={B} U={p.U} (RFF SE draw, synthetic)",
+         "N": p.N, "d": p.d, "s": p.s, "M": p.M, "B": B, "U": p.U,
+         "l2": "flushed between timed steps (256 MiB write outside the step events); inputs and "
+               "intermediates are larger than L2"}
+    if world > 1:
+        c["workload"] = (f"{world} draws of {p.name} joined, one draw per rank (N={p.N} per draw, M={p.M}, |S|={p.s}, "
+                         f"B={B}, U={p.U}); rank r owns draw r's blocks plus B-block halos; local summaries, one "
+                         f"all-reduce of the (|S|+1)^2 FP64 summary Gram, global step on every rank")
+        c["parallelism"] = f"block-sharded x{world}"
+    return c
+
+
+def golden(p, B):
+    """The oracle's stored values for this workload, if its inputs' fingerprints match."""
+    name = GOLDEN.get((p.name, B))
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json") if name else None
+    if not path or not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    fp = g["fingerprints"]
+    sha = lambda a: hashlib.sha256(a.tobytes()).hexdigest()[:32]  # noqa: E731
+    ok = (fp["X_sha"] == sha(p.X) and fp["block_ptr_sha"] == sha(p.block_ptr.astype("int64"))
+          and fp["test_block_ptr_sha"] == sha(p.test_block_ptr.astype("int64"))
+          and abs(fp["y_fsum"] - math.fsum(p.y)) <= 1e-10 * max(1.0, abs(fp["y_fsum"])))
+    return g if ok else None
+
+
+def accuracy(g, mean, var, loglik, yU):
+    """Errors of the mixed form's outputs against the oracle's stored values."""
+    import numpy as np
+    rows = np.asarray(g["sample_rows"], dtype=np.int64)
+    mo, vo = np.asarray(g["mean"]), np.asarray(g["var"])
+    m, v = np.asarray(mean)[rows], np.asarray(var)[rows]
+    out = {"reference": "FP64 oracle (tests/golden, written from oracle/)",
+           "sample": f"test blocks {g['sampled_blocks']} ({rows.size} points)",
+           "mean_rel_err": float(np.linalg.norm(m - mo) / np.linalg.norm(mo)),
+           "mean_max_abs_err": float(np.max(np.abs(m - mo))),
+           "var_rel_err": float(np.linalg.norm(v - vo) / np.linalg.norm(vo)),
+           "var_max_rel_err": float(np.max(np.abs(v - vo) / np.abs(vo))),
+           "rmse_sample": float(np.sqrt(np.mean((m - yU[rows]) ** 2))), "rmse_sample_oracle": g["rmse_sample"]}
+    if loglik is not None:
+        out["loglik_rel_err"] = abs(loglik - g["fit"]["loglik"]) / abs(g["fit"]["loglik"])
+    if "rmse_all" in g:
+        out["rmse_all"] = float(np.sqrt(np.mean((np.asarray(mean) - yU) ** 2)))
+        out["rmse_all_oracle"] = g["rmse_all"]
+    return out
 
 
 def run_reference(args, p):
-    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle timed on the host cores, one bounded
+    sample of the workload (its first --ref-blocks blocks) per step."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
     for _ in range(args.warmup):
-        cpu_baseline(p, args.B, n_blocks=args.ref_blocks)
-    vals = []
-    last = None
+        cpu_baseline(p, args.B, args.ref_blocks)
+    vals, last = [], None
     for _ in range(args.steps):
-        cb, dt = cpu_baseline(p, args.B, n_blocks=args.ref_blocks)
+        cb, dt = cpu_baseline(p, args.B, args.ref_blocks)
         vals.append(dt)
         last = cb
     ms = 1e3 * statistics.mean(vals)
     nsub = int(p.block_ptr[min(args.ref_blocks, p.M)])
     value = nsub / (ms / 1e3)
-    out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
+    out = {"metric": METRIC, "value": value, "unit": "train-points/s",
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": workload_config(p, args.B, world),
@@ -287,17 +364,15 @@ def run_reference(args, p):
     print(json.dumps(out))
 
 
-def workload_config(p, B, world=1):
-    c = {"workload": f"C2: N={p.N} d={p.d} |S|={p.s} M={p.M} blocks of {p.N // p.M} (k-means order) "
-                     f"B={B} U={p.U} (RFF SE draw, synthetic)",
-         "N": p.N, "d": p.d, "s": p.s, "M": p.M, "B": B, "U": p.U,
-         "l2": "flushed between timed steps (256 MiB write outside the step events)"}
-    if world > 1:
-        c["workload"] = (f"{world} draws of C2 joined (N={p.N}, M={p.M}, |S|={p.s}, B={B}, U={p.U}); rank r owns "
-                         f"draw r's blocks plus B-block halos; local summaries, one all-reduce of the "
-                         f"(|S|+1)^2 FP64 summary Gram, global step on every rank")
-        c["parallelism"] = f"block-sharded x{world}"
-    return c
+def build_problem(args, world, rank):
+    """The configured workload (N = 1), or for N > 1 the joined draws this rank
+    needs: its own draw and its neighbours' (halo blocks)."""
+    from workloads import make_problem, make_replicated
+    kw = {k: getattr(args, k) for k in ("N", "M", "s", "U") if getattr(args, k) is not None}
+    if world == 1:
+        return make_problem(args.config, B=args.B, **kw), 0
+    lo, hi = max(0, rank - 1), min(world - 1, rank + 1)
+    return make_replicated(args.config, hi - lo + 1, B=args.B, first_draw=lo, **kw), rank - lo
 
 
 # ----------------------------------------------------------------------------
@@ -307,26 +382,41 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
-    ap.add_argument("--B", type=int, default=1)
-    ap.add_argument("--ref-blocks", type=int, default=2)
+    ap.add_argument("--config", default="C4", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--B", type=int, default=None, help="Markov order (default: the configuration's)")
+    ap.add_argument("--N", type=int, default=None, help="reduced case: training points (keeps the recipe)")
+    ap.add_argument("--M", type=int, default=None, help="reduced case: blocks")
+    ap.add_argument("--s", type=int, default=None, help="reduced case: support points")
+    ap.add_argument("--U", type=int, default=None, help="reduced case: test points")
+    ap.add_argument("--mode", default="full", choices=["full", "step"],
+                    help="step: warm-up and timed steps only (for profilers)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="form of the timed steps")
+    ap.add_argument("--ref-blocks", type=int, default=2,
+                    help="blocks of the oracle's sample (cpu_baseline and the reference arm)")
+    ap.add_argument("--fp64-blocks", default="4,8", help="block counts of the FP64 form's timed subsets")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--dominant", default="auto")
     ap.add_argument("--trace", default=None,
                     help="write the per-launch trace (kernel, start ms, end ms; CUDA events around every launch, "
                          "all streams) of the untimed profiled step to this JSON file (rank 0)")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3) if args.impl == "lma" else args.warmup
-
-    from workloads import make_problem, make_replicated
+    if args.impl == "lma":
+        args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    # one C2 problem per GPU: N = 1 runs C2 itself; N > 1 runs N draws of C2
-    # joined into one problem, each rank owning one draw's blocks (weak scaling)
-    p = make_problem("C2", B=args.B) if world == 1 else make_replicated("C2", world, B=args.B)
+    from workloads.synth import _DEFAULTS
+    if args.B is None:
+        args.B = _DEFAULTS[args.config]["B"]
+    reduced = any(getattr(args, k) is not None for k in ("N", "M", "s", "U"))
+
     if args.impl == "reference":
-        run_reference(args, make_problem("C2", B=args.B))
+        if rank == 0:
+            from workloads import make_problem
+            kw = {k: getattr(args, k) for k in ("N", "M", "s", "U") if getattr(args, k) is not None}
+            run_reference(args, make_problem(args.config, B=args.B, **kw))
         return
 
     import numpy as np
@@ -341,44 +431,45 @@ def main():
     import paper_1411_4510_gb300 as L
     from paper_1411_4510_gb300 import api, shard
 
+    p, my = build_problem(args, world, rank)
     dev = torch.device("cuda", local)
     full = L.problem_args(p, B=args.B)
     if world == 1:
         sh, sub, u0, u1, tptr = None, full, 0, p.U, p.test_block_ptr
     else:
-        sh = shard.plan(p.block_ptr, args.B, world, rank)
+        # the joined draws [lo, hi] of build_problem: this rank owns draw `my`
+        per = p.M // (p.meta.get("copies", 1))
+        sh = shard.plan_range(p.block_ptr, args.B, my * per, (my + 1) * per, rank, world)
         sub = shard.sub_problem(full, sh)
         u0, u1, tptr = shard.test_rows(p.test_block_ptr, sh)
+    prec = L.FP64 if args.precision == "fp64" else L.MIXED
     hostsrc = dict(X=sub["X"], y=sub["y"], S=sub["S"], XU=p.XU[u0:u1])
     dsrc = {k: torch.as_tensor(v, device=dev) for k, v in hostsrc.items()}
     kw = {k: v for k, v in sub.items() if k not in ("X", "y", "S")}
+    n_total = p.N if world == 1 else p.N // p.meta.get("copies", 1) * world
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
-    def step(prec=L.MIXED, host=None):
+    def step(pr=prec, host=None, keep=False):
         src = dsrc if host is None else host
         if sh is None:  # fit and predict in one call: the global step overlaps the prediction
-            mean, var, m = L.lma_fit_predict(src["X"], src["y"], S=src["S"], XU=src["XU"], test_block_ptr=tptr,
-                                             precision=prec, keep_model=True, **kw)
-            return m, (mean, var)
-        else:  # local summaries, one all-reduce of the summary Gram, global step
-            m = api.lma_fit_local(src["X"], src["y"], S=src["S"], win_begin=0, own_begin=sh.own_begin,
-                                  own_end=sh.own_end, precision=prec, **kw)
-            G, ld = api.lma_model_local_summary(m, device=dev)
-            G, ld = shard.allreduce_sum(G, ld)
-            api.lma_model_set_global(m, G, ld, p.N)
-        return m, L.lma_predict(m, src["XU"], tptr)
+            return L.lma_fit_predict(src["X"], src["y"], S=src["S"], XU=src["XU"], test_block_ptr=tptr,
+                                     precision=pr, keep_model=keep, **kw)
+        m = api.lma_fit_local(src["X"], src["y"], S=src["S"], win_begin=0, own_begin=sh.own_begin,
+                              own_end=sh.own_end, precision=pr, **kw)
+        G, ld = api.lma_model_local_summary(m, device=dev)
+        G, ld = shard.allreduce_sum(G, ld)
+        api.lma_model_set_global(m, G, ld, n_total)
+        mean, var = L.lma_predict(m, src["XU"], tptr)
+        return (mean, var, m) if keep else (mean, var)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    work = kernel_work(p, args.B, fused=(world == 1))
-    if world > 1:  # equal shards: each rank does one draw's share
-        work = {k: v / world for k, v in work.items()}
 
-    trace = []
-
-    def timed(nsteps, prec=L.MIXED, host=None, profile=None, keep_trace=False):
+    def timed(nsteps, pr=prec, host=None, profile=None, keep_trace=False):
+        """Mean CUDA-event milliseconds of nsteps steps (L2 flushed before each,
+        outside its events), launches of this library, optional profile."""
         evs = []
         n0 = L.lma_kernel_launch_count()
         if world > 1:
@@ -386,102 +477,175 @@ def main():
         torch.cuda.synchronize()
         if profile:
             L.profile_start(profile)
-        out = None
         for _ in range(nsteps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(st)
-            out = step(prec, host)
+            step(pr, host)
             b.record(st)
             evs.append((a, b))
         torch.cuda.synchronize()
-        if profile and keep_trace:
-            trace[:] = L.profile_trace()
+        trace = L.profile_trace() if (profile and keep_trace) else None
         prof = L.profile_stop() if profile else None
         if world > 1:
             dist.barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
-        return ms, L.lma_kernel_launch_count() - n0, prof, out
+        return ms, L.lma_kernel_launch_count() - n0, prof, trace
 
-    # pick the dominant kernel from an untimed all-kernel profile of one step,
-    # then bracket only its launches inside the timed region
-    _, _, prof_all, _ = timed(1, profile="k_", keep_trace=bool(args.trace))
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: no profiler events in the timed region ------------------
+    with ClockSampler(local) as clk:
+        ms, launches, _, _ = timed(args.steps)
+    clocks = clk.summary()
+    step_ms = max_over_ranks(statistics.mean(ms))
+    fit_f, pred_f = fit_flops(p, args.B), predict_flops(p, args.B)
+    if world > 1:  # whole job: one draw per rank
+        fit_f, pred_f = fit_f / p.meta.get("copies", 1) * world, pred_f / p.meta.get("copies", 1) * world
+    n_units = p.N if world == 1 else n_total
+    value = n_units / (step_ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "train-points/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": DTYPE if prec == L.MIXED else "f64", "data": "synthetic",
+           "config": workload_config(p if world == 1 else p, args.B, world, reduced),
+           "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
+           "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
+           "gpu_launches": int(launches), "clocks": clocks,
+           "ms_per_step_all": [round(x, 3) for x in ms]}
+    if args.mode == "step":
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- per-kernel profile of one untimed step; dominant kernel's own pass --
+    work = kernel_work(p, args.B, fused=(world == 1 and prec == L.MIXED))
+    if world > 1:
+        work = {k: v / p.meta.get("copies", 1) for k, v in work.items()}
+    _, _, prof_all, trace = timed(1, profile="k_", keep_trace=bool(args.trace))
     if args.trace and rank == 0:
         with open(args.trace, "w") as fh:
             json.dump([{"kernel": k, "start_ms": a, "end_ms": b} for k, a, b in trace], fh)
     dominant = args.dominant
     if dominant == "auto":
-        known = {k: v for k, v in prof_all.items() if k in work}
+        known = {k: v for k, v in (prof_all or {}).items() if k in work}
         dominant = max(known, key=lambda k: known[k][0]) if known else None
-    with ClockSampler(local) as clk:
-        ms, launches, prof, (model, (mean, var)) = timed(args.steps, profile=dominant)
-    step_ms = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    fit_f, pred_f = fit_flops(p, args.B), predict_flops(p, args.B)
-    value = p.N / (step_ms / 1e3)
-    mean_mixed = mean.cpu().numpy()
+    peaks = load_peaks()
+    roof = None
+    if dominant:
+        nrs = min(args.steps, 3)
+        _, _, prof, _ = timed(nrs, profile=dominant)
+        if prof and dominant in prof:
+            tot_ms, n_l = prof[dominant]
+            roof = roofline_of(dominant, work[dominant] * nrs, tot_ms, n_l, peaks)
+            roof["work_per_step_gflop"] = work[dominant] / 1e9
+            roof["timing"] = (f"CUDA events around each of its launches over {nrs} further steps (a separate pass; "
+                              f"the headline steps carry no profiler events)")
+            t = NCU_TRAFFIC.get(dominant)
+            if t and t["sources"] == sources_hash(t.get("files")) and world == 1 and (p.name, args.B) == t.get("case"):
+                roof["traffic"] = t["bytes"]
+                roof["traffic_note"] = t["note"]
+    out["roofline"] = roof
+    out["roofline_by_kernel"] = {k: {kk: vv for kk, vv in roofline_of(k, work[k], v[0], v[1], peaks).items()
+                                     if kk in ("bound", "achieved", "peak", "frac", "avg_launch_ms")}
+                                 for k, v in (prof_all or {}).items() if k in work and v[0] > 0}
+    out["kernel_ms_one_step"] = {k: round(v[0], 4) for k, v in
+                                 sorted((prof_all or {}).items(), key=lambda kv: -kv[1][0])}
 
-    # end to end through the C ABI with pinned host buffers (copies inside)
+    # ---- end to end through the C ABI with pinned host buffers -------------
     host = {k: torch.as_tensor(v).pin_memory() for k, v in hostsrc.items()}
     ems, _, _, _ = timed(max(3, args.steps // 2), host=host)
-    e2e_ms = statistics.mean(ems)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(statistics.mean(ems))
     nsub, Msub = len(hostsrc["y"]), len(kw["block_ptr"]) - 1
     h2d = 8 * (nsub * p.d + nsub + p.s * p.d + (u1 - u0) * p.d) + 8 * (Msub + 1) * 2
-    e2e = {"value": p.N / (e2e_ms / 1e3), "unit": "train-points/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * (u1 - u0)}
+    out["e2e"] = {"value": n_units / (e2e_ms / 1e3), "unit": "train-points/s", "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * (u1 - u0)}
 
-    # plain FP64 GPU form (per-window launches) and the mixed form's error against it
-    fp64 = None
-    if not args.no_fp64 and world == 1:
-        step(L.FP64)
-        fms, _, _, (_, (m64, v64)) = timed(2, prec=L.FP64)
-        m64 = m64.cpu().numpy()
-        rm64 = float(np.sqrt(np.mean((m64 - p.yU) ** 2)))
-        rmx = float(np.sqrt(np.mean((mean_mixed - p.yU) ** 2)))
-        fms_mean = statistics.mean(fms)
-        fp64 = {"value": p.N / (fms_mean / 1e3), "ms_per_step": fms_mean,
-                "tflops": (fit_f + pred_f) / (fms_mean / 1e3) / 1e12,
-                "mixed_speedup": fms_mean / step_ms,
-                "mixed_mean_rel_err_vs_fp64": float(np.linalg.norm(mean_mixed - m64) / np.linalg.norm(m64)),
-                "rmse_fp64": rm64, "rmse_mixed": rmx}
+    if world == 1:
+        # ---- accuracy against the oracle's stored values -------------------
+        res = step(keep=True)
+        mean, var, model = res
+        ll = L.lma_model_loglik(model)
+        del model
+        torch.cuda.synchronize()
+        mean, var = mean.cpu().numpy(), var.cpu().numpy()
+        g = golden(p, args.B) if not reduced else None
+        out["accuracy_vs_oracle"] = accuracy(g, mean, var, ll, p.yU) if g else None
 
-    # roofline of the dominant kernel, from the launches timed above
-    peaks = load_peaks()
-    clocks = clk.summary()
-    roof = None
-    if prof and dominant in prof:
-        tot_ms, n_l = prof[dominant]
-        roof = roofline_of(dominant, work[dominant] * args.steps, tot_ms, n_l, peaks)
-        roof["work_per_step_gflop"] = work[dominant] / 1e9
-        t = NCU_TRAFFIC.get(dominant)
-        if t and t["sources"] == sources_hash(t.get("files")) and world == 1:
-            roof["traffic"] = t["bytes"]
-            roof["traffic_note"] = t["note"]
-    # every modelled kernel of the untimed all-kernel profile (one step)
-    roof_all = {k: {kk: vv for kk, vv in roofline_of(k, work[k], v[0], v[1], peaks).items()
-                    if kk in ("bound", "achieved", "peak", "frac", "avg_launch_ms")}
-                for k, v in (prof_all or {}).items() if k in work and v[0] > 0}
-    cpu = None
-    if not args.no_cpu and rank == 0 and world == 1:
-        cpu, _ = cpu_baseline(p, args.B)
-    out = {"metric": "LMA fit+predict train-points/s", "value": value, "unit": "train-points/s",
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic", "config": workload_config(p, args.B, world),
-           "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
-           "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
-           "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-           "roofline_by_kernel": roof_all,
-           "cpu_baseline": cpu, "fp64_gpu_form": fp64,
-           "kernel_ms_one_step": {k: round(v[0], 4) for k, v in sorted((prof_all or {}).items(), key=lambda kv: -kv[1][0])}}
+        # ---- plain FP64 GPU form, timed on the first blocks ----------------
+        if not args.no_fp64 and prec == L.MIXED:
+            pts = []
+            for k in [int(x) for x in args.fp64_blocks.split(",")]:
+                q = sub_problem(p, k, args.B)
+                qa = L.problem_args(q)
+                qd = {kk: torch.as_tensor(getattr(q, kk), device=dev) for kk in ("X", "y", "S", "XU")}
+                qkw = {kk: v for kk, v in qa.items() if kk not in ("X", "y", "S")}
+
+                def qstep(pr):
+                    return L.lma_fit_predict(qd["X"], qd["y"], S=qd["S"], XU=qd["XU"],
+                                             test_block_ptr=q.test_block_ptr, precision=pr, **qkw)
+                qstep(L.FP64)
+                torch.cuda.synchronize()
+                tms = []
+                for _ in range(2):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    m64, _ = qstep(L.FP64)
+                    b.record(st)
+                    torch.cuda.synchronize()
+                    tms.append(a.elapsed_time(b))
+                mmx, _ = qstep(L.MIXED)
+                m64, mmx = m64.cpu().numpy(), mmx.cpu().numpy()
+                pts.append((q.M, statistics.mean(tms), float(np.linalg.norm(mmx - m64) / np.linalg.norm(m64))))
+            (k1, t1, _), (k2, t2, e2) = pts[0], pts[-1]
+            slope = (t2 - t1) / max(1, k2 - k1)
+            t_full = t1 + (p.M - k1) * slope
+            out["fp64_gpu_form"] = {
+                "value": p.N / (t_full / 1e3), "ms_per_step": t_full, "extrapolated": True,
+                "timed": {f"first {k} blocks": round(t, 2) for k, t, _ in pts},
+                "how": f"lma_fit_predict in the FP64 form (one window per launch) on the first {k1} and {k2} blocks "
+                       f"of the workload (same |S|, B), extrapolated linearly in the block count to {p.M}",
+                "tflops": (fit_f + pred_f) / (t_full / 1e3) / 1e12,
+                "mixed_speedup": t_full / step_ms,
+                "mixed_mean_rel_err_vs_fp64": e2, "err_sample": f"first {k2} blocks' test points"}
+
+        # ---- gradient of the log-likelihood (C5) ---------------------------
+        if not args.no_grad and not reduced:
+            from workloads import make_problem
+            q = make_problem("C5")
+            qa = L.problem_args(q)
+            qd = {kk: torch.as_tensor(qa[kk], device=dev) for kk in ("X", "y", "S")}
+            qkw = {kk: v for kk, v in qa.items() if kk not in ("X", "y", "S")}
+            L.lma_loglik_grad(qd["X"], qd["y"], S=qd["S"], **qkw)
+            tms = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                llg, gr = L.lma_loglik_grad(qd["X"], qd["y"], S=qd["S"], **qkw)
+                tms.append(1e3 * (time.perf_counter() - t0))
+            gms = statistics.mean(tms)
+            leg = {"workload": workload_config(q, q.B)["workload"], "ms_per_call": gms,
+                   "train_points_per_s": q.N / (gms / 1e3), "fit_gflop": fit_flops(q, q.B) / 1e9,
+                   "timing": "host wall clock around lma_loglik_grad (it synchronises and returns host values)"}
+            gg = golden(q, q.B)
+            if gg:
+                go = np.asarray(gg["grad"])
+                leg["loglik_rel_err_vs_oracle"] = abs(llg - gg["loglik"]) / abs(gg["loglik"])
+                leg["grad_rel_err_vs_oracle"] = float(np.linalg.norm(gr - go) / np.linalg.norm(go))
+                leg["grad_max_rel_err_vs_oracle"] = float(np.max(np.abs(gr - go) / np.maximum(np.abs(go), 1e-300)))
+            out["grad_leg"] = leg
+
+        # ---- the oracle on the host cores -----------------------------------
+        if not args.no_cpu and rank == 0:
+            out["cpu_baseline"], _ = cpu_baseline(p, args.B, args.ref_blocks)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

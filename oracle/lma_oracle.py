@@ -211,16 +211,6 @@ def fit(prob, B: int | None = None, keep_blocks: bool = False) -> LMAFit:
     return f
 
 
-def residual_e(f: LMAFit) -> np.ndarray:
-    """e = y - mu - Sigma_DS alpha."""
-    p = f.prob
-    cv = _Cov(p)
-    out = np.empty(p.X.shape[0])
-    for i in range(0, p.X.shape[0], 8192):
-        out[i:i + 8192] = p.y[i:i + 8192] - p.mean - cv.W(p.X[i:i + 8192]).T @ f.beta
-    return out
-
-
 def _subchain_precision(cv: _Cov, ptr, Jb, B: int):
     """(R-bar_JJ)^-1 for the consecutive blocks Jb by Lemma 1 applied to the
     sub-chain: block row m is [U_mm, U^B_m] = U_mm [I, -R'] with the blanket

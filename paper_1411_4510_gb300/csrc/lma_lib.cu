@@ -1207,7 +1207,9 @@ static __global__ void k_noalloc_setup(Win* wslot, Win w, int* flag) {
   *flag = 0;
 }
 
-// C = I + A (A: s x s, ld s), extra row y, then s identity rows (the layout of k_build_global)
+// C = I + A (A: s x s, ld s) with s identity rows appended and then the row
+// y, the layout of k_build_global: identity rows first, so that they stay
+// 64-aligned and the factorisation skips their tiles while still zero.
 static __global__ void k_noalloc_build(const double* __restrict__ A, const double* __restrict__ y, int s, int npad,
                                        double* __restrict__ buf) {
   int64_t total = (int64_t)(npad + 1 + s) * npad;
@@ -1218,48 +1220,52 @@ static __global__ void k_noalloc_build(const double* __restrict__ A, const doubl
   if (i < npad) {
     if (i < s && j < s) v = A[(int64_t)i * s + j] + (i == j ? 1.0 : 0.0);
     else v = (i == j) ? 1.0 : 0.0;
-  } else if (i == npad) {
-    v = (j < s) ? y[j] : 0.0;
+  } else if (i < npad + s) {
+    v = ((i - npad) == j) ? 1.0 : 0.0;
   } else {
-    v = ((i - npad - 1) == j) ? 1.0 : 0.0;
+    v = (j < s) ? y[j] : 0.0;
   }
   buf[e] = v;
 }
 
-// out[0] = w^T w (w = L_C^-1 y), out[1] = log|I + A|, out[2] = loglik; beta = L_C^-T w
-static __global__ void k_noalloc_finish(const double* __restrict__ buf, int s, int npad, double quad,
-                                        double logdet_R, double n, double* __restrict__ beta,
-                                        double* __restrict__ out) {
-  const double* w = buf + (int64_t)npad * npad;
-  const double* E = w + npad;
-  __shared__ double red[NT];
+// beta = L_C^-T w with w = L_C^-1 y (the appended y row of the factor), one
+// warp per row k of L_C^-T over many CTAs (coalesced row reads, lane sums
+// combined by shuffles); CTA 0 also writes out[0] = w^T w, out[1] =
+// log|I + A| and out[2] = the log-likelihood.
+static __global__ void __launch_bounds__(NT) k_noalloc_finish(const double* __restrict__ buf, int s, int npad,
+                                                              double quad, double logdet_R, double n,
+                                                              double* __restrict__ beta, double* __restrict__ out) {
+  const double* E = buf + (int64_t)npad * npad;  // row k = (L_C^-T)[k][.]
+  const double* w = E + (int64_t)s * npad;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (NT / 32) + warp;
+  if (k < s) {
+    const double* row = E + (int64_t)k * npad;
+    double sum = 0.0;
+    for (int i = lane; i < s; i += 32) sum = fma(row[i], w[i], sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) beta[k] = sum;
+  }
+  if (blockIdx.x != 0) return;
+  __shared__ double red[2][NT];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < s; i += NT) {
     a += w[i] * w[i];
     b += log(buf[(int64_t)i * npad + i]);
   }
-  for (int k = threadIdx.x; k < s; k += NT) {
-    double sum = 0.0;
-    const double* row = E + (int64_t)k * npad;
-    for (int i = 0; i < s; ++i) sum += row[i] * w[i];
-    beta[k] = sum;
-  }
-  red[threadIdx.x] = a;
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
   __syncthreads();
   for (int o = NT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double wCw = red[0];
-  __syncthreads();
-  red[threadIdx.x] = b;
-  __syncthreads();
-  for (int o = NT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double ldC = 2.0 * red[0];
+    const double wCw = red[0][0], ldC = 2.0 * red[1][0];
     out[0] = wCw;
     out[1] = ldC;
     out[2] = -0.5 * (quad - wCw) - 0.5 * (logdet_R + ldC) - 0.5 * n * log(2.0 * M_PI);
@@ -1287,9 +1293,9 @@ void global_step_noalloc(int64_t s, int64_t n, const double* A, const double* y,
   launch("k_noalloc_setup", k_noalloc_setup, 1, 1, 0, st, wslot, w, flag);
   launch("k_noalloc_build", k_noalloc_build, nblk((int64_t)(npad + 1 + s) * npad), NT, 0, st, A, y, (int)s, npad,
          buf);
-  right_looking_fp64(st, w, wslot, buf, dv, flag);
-  launch("k_noalloc_finish", k_noalloc_finish, 1, NT, 0, st, (const double*)buf, (int)s, npad, quad, logdet_R,
-         (double)n, beta, scalars);
+  right_looking_fp64(st, w, wslot, buf, dv, flag, (int)s);
+  launch("k_noalloc_finish", k_noalloc_finish, nblk(s, NT / 32), NT, 0, st, (const double*)buf, (int)s, npad, quad,
+         logdet_R, (double)n, beta, scalars);
   int h = 0;
   LMA_CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   LMA_CK(cudaStreamSynchronize(st));

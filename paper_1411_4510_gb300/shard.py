@@ -68,6 +68,17 @@ def plan(block_ptr, B: int, world: int, rank: int) -> Shard:
     return Shard(rank, world, m0, m1, lo, hi, int(ptr[lo]), int(ptr[hi]))
 
 
+def plan_range(block_ptr, B: int, m0: int, m1: int, rank: int = 0, world: int = 1) -> Shard:
+    """The shard that owns the given block range [m0, m1), with the same halos
+    as plan()."""
+    ptr = np.asarray(block_ptr, dtype=np.int64)
+    M = len(ptr) - 1
+    if not (0 <= m0 < m1 <= M):
+        raise ValueError(f"bad block range [{m0}, {m1}) of {M} blocks")
+    lo, hi = max(0, m0 - int(B)), min(M, m1 + int(B))
+    return Shard(rank, world, m0, m1, lo, hi, int(ptr[lo]), int(ptr[hi]))
+
+
 def sub_problem(args: dict, sh: Shard) -> dict:
     """The problem arguments (as from api.problem_args) restricted to the shard."""
     ptr = np.asarray(args["block_ptr"], dtype=np.int64)

@@ -26,7 +26,8 @@ def test_reference_arm_line():
     assert d["metric"] == "LMA fit+predict train-points/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("C2:")
+    assert d["config"]["workload"].startswith("C4:")  # the default workload: the largest single-GPU one
+    assert "first 1 of 2000 blocks" in d["cpu_baseline"]["sample"]
 
 
 def test_reference_arm_other_ranks_are_silent():

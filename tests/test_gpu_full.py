@@ -1,0 +1,162 @@
+"""GPU parity at the full configuration sizes against the FP64 oracle's stored
+values (tests/golden/*.json, written by tests/golden/make_golden.py, which
+calls only oracle/ and workloads/).
+
+Cases, each through lma_fit_predict (the call bench.py times) on device inputs:
+  C2 at B = 1 and B = 2 (N = 40,960, |S| = 512, 64 k-means blocks of 640),
+  C3 (N = 49,152, |S| = 1,024, 96 uneven k-means blocks, B = 2),
+  C4 (N = 2,000,000, |S| = 2,048, 2,000 Morton blocks of 1,000, B = 1; mixed
+      form only: the plain FP64 form would take minutes),
+and the gradient of the log-likelihood at C5 (N = 65,536, |S| = 1,024,
+128 Morton blocks of 512, B = 2) against the oracle's hand adjoint and its
+central differences (h = 1e-4 in log space).
+
+Compared: the predictive mean and variance of the sampled test blocks (the
+first two, a middle one and the last two; every test point's RMSE at C2),
+the log-likelihood and entries of the global summary (Definition 2, whitened
+support coordinates: the first 16 entries of y-ddot and of diag A, tr A,
+log|I + A|, quad = sum y-dot^T R-dot y-dot, log|R-bar|).
+
+Tolerances.  FP64 form: 1e-9 relative, norm-wise and element-wise (the
+spec figure).  Mixed form: predictive mean 1e-4 norm-wise and RMSE
+within 0.1 % of the oracle's (spec figures); the element-wise,
+variance, log-likelihood, summary and gradient bounds are about three
+times the largest error measured on the GB300 at these workloads, so that a
+regression costing one digit fails.
+
+The inputs are rebuilt from their seeds and compared with the fingerprints
+the oracle's run recorded (exact hashes of X, S, XU and both partitions; the
+outputs y to 1e-10 relative, since the random-Fourier-feature cosines may
+differ in the last bit between machines).
+"""
+import hashlib
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from _parity import check, check_scalar
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+TOL_FP64 = 1e-9
+MEAN_NORM_MIXED = 1e-4          # north star
+MEAN_ELEM_MIXED = 2e-4          # max |dmean| / max |mean|
+VAR_NORM_MIXED = 3e-4
+VAR_ELEM_MIXED = 1e-3           # max |dvar| / var
+LL_MIXED = 5e-5
+SUMMARY_MIXED = 5e-4            # global-summary entries (norm-wise over the probes)
+RMSE_MIXED = 1e-3               # spec: RMSE within 0.1 % of the oracle's
+GRAD_FP64 = 1e-8                # see test_gpu_grad.py: one digit of cancellation in the window contractions
+GRAD_MIXED = 3e-4
+FD_TOL = 1e-6                   # central differences with h = 1e-4: truncation ~h^2 relative
+
+
+def load_golden(name, p):
+    path = os.path.join(HERE, "golden", f"{name}.json")
+    assert os.path.exists(path), f"missing {path}: run tests/golden/make_golden.py {name}"
+    g = json.load(open(path))
+    fp = g["fingerprints"]
+    sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()[:32]  # noqa: E731
+    assert fp["X_sha"] == sha(p.X), "training inputs differ from the oracle run's"
+    assert fp["S_sha"] == sha(p.S), "support set differs from the oracle run's"
+    assert fp["XU_sha"] == sha(p.XU), "test inputs differ from the oracle run's"
+    assert fp["block_ptr_sha"] == sha(p.block_ptr.astype(np.int64)), "partition differs"
+    assert fp["test_block_ptr_sha"] == sha(p.test_block_ptr.astype(np.int64)), "test partition differs"
+    assert abs(fp["y_fsum"] - math.fsum(p.y)) <= 1e-10 * max(1.0, abs(fp["y_fsum"])), "outputs differ"
+    return g
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    from paper_1411_4510_gb300 import build
+    build.build()
+    import paper_1411_4510_gb300 as L
+    torch.cuda.set_device(0)
+    return L
+
+
+def _dev_args(L, p):
+    import torch
+    dev = torch.device("cuda:0")
+    a = L.problem_args(p)
+    a.update(X=torch.as_tensor(p.X, device=dev), y=torch.as_tensor(p.y, device=dev),
+             S=torch.as_tensor(p.S, device=dev))
+    return a, torch.as_tensor(p.XU, device=dev)
+
+
+def _fit_predict(L, p, prec):
+    import torch
+    a, XU = _dev_args(L, p)
+    mean, var, model = L.lma_fit_predict(XU=XU, test_block_ptr=p.test_block_ptr, precision=prec,
+                                         keep_model=True, **a)
+    torch.cuda.synchronize()
+    summ = L.lma_model_summary(model)
+    del model
+    return mean.cpu().numpy(), var.cpu().numpy(), summ
+
+
+def _compare(test, p, g, mean, var, summ, fp64):
+    rows = np.asarray(g["sample_rows"], dtype=np.int64)
+    tm = (TOL_FP64, TOL_FP64) if fp64 else (MEAN_NORM_MIXED, MEAN_ELEM_MIXED)
+    tv = (TOL_FP64, TOL_FP64) if fp64 else (VAR_NORM_MIXED, VAR_ELEM_MIXED)
+    check(test, "mean", mean[rows], g["mean"], *tm)
+    check(test, "var", var[rows], g["var"], *tv, positive=True)
+    f = g["fit"]
+    check_scalar(test, "loglik", summ["loglik"], f["loglik"], TOL_FP64 if fp64 else LL_MIXED)
+    ts = TOL_FP64 if fp64 else SUMMARY_MIXED
+    check_scalar(test, "quad", summ["quad"], f["quad"], ts)
+    check_scalar(test, "logdet_R", summ["logdet_R"], f["logdet_R"], ts)
+    check_scalar(test, "logdet_C", summ["logdet_C"], f["logdet_C"], ts)
+    check_scalar(test, "A_trace", float(np.trace(summ["A"])), f["A_trace"], ts)
+    check(test, "ydd_head", summ["y"][:16], f["ydd_head"], ts, ts)
+    check(test, "A_diag_head", np.diag(summ["A"])[:16], f["A_diag_head"], ts, ts, positive=True)
+    if "rmse_all" in g:
+        rm = float(np.sqrt(np.mean((mean - p.yU) ** 2)))
+        check_scalar(test, "rmse_all", rm, g["rmse_all"], TOL_FP64 if fp64 else RMSE_MIXED)
+    rs = float(np.sqrt(np.mean((mean[rows] - p.yU[rows]) ** 2)))
+    check_scalar(test, "rmse_sample", rs, g["rmse_sample"], TOL_FP64 if fp64 else RMSE_MIXED)
+
+
+PRED = [("C2", 1, "c2_b1"), ("C2", 2, "c2_b2"), ("C3", 2, "c3"), ("C4", 1, "c4")]
+
+
+@pytest.mark.parametrize("case", PRED, ids=[c[2] for c in PRED])
+def test_full_size_mixed_matches_oracle(L, case):
+    from workloads import make_problem
+    name, B, gname = case
+    p = make_problem(name, B=B)
+    g = load_golden(gname, p)
+    mean, var, summ = _fit_predict(L, p, L.MIXED)
+    _compare(f"full_{gname}_mixed", p, g, mean, var, summ, fp64=False)
+
+
+@pytest.mark.parametrize("case", PRED[:3], ids=[c[2] for c in PRED[:3]])
+def test_full_size_fp64_matches_oracle(L, case):
+    from workloads import make_problem
+    name, B, gname = case
+    p = make_problem(name, B=B)
+    g = load_golden(gname, p)
+    mean, var, summ = _fit_predict(L, p, L.FP64)
+    _compare(f"full_{gname}_fp64", p, g, mean, var, summ, fp64=True)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_full_c5_gradient(L, prec):
+    from workloads import make_problem
+    p = make_problem("C5")
+    g = load_golden("c5", p)
+    a, _ = _dev_args(L, p)
+    ll, gr = L.lma_loglik_grad(precision=getattr(L, prec), **a)
+    test = f"full_c5_grad_{prec.lower()}"
+    fp64 = prec == "FP64"
+    check_scalar(test, "loglik", ll, g["loglik"], TOL_FP64 if fp64 else LL_MIXED)
+    tg = GRAD_FP64 if fp64 else GRAD_MIXED
+    check(test, "grad", gr, g["grad"], tg, tg)
+    for k, fd in g["fd"].items():
+        check_scalar(test, f"grad[{k}] vs central difference", float(gr[int(k)]), fd, FD_TOL if fp64 else GRAD_MIXED)

@@ -13,10 +13,13 @@ norm-wise relative and reported.
 import numpy as np
 import pytest
 
+from _parity import check, check_scalar
+
 pytestmark = pytest.mark.gpu
 
 GRAD_TOL_FP64 = 1e-8
 GRAD_TOL_MIXED = 2e-2
+LL_TOL_MIXED = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +59,9 @@ def test_grad_fp64_matches_oracle(L, case):
     p = _p(case)
     ll_ref, g_ref = O2.loglik_grad(p)
     ll, g = L.lma_loglik_grad(precision=L.FP64, **L.problem_args(p))
-    assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
-    assert _rel(g, g_ref) <= GRAD_TOL_FP64, (g, g_ref)
+    t = f"grad_tiny{case[0]}_fp64"
+    check_scalar(t, "loglik", ll, ll_ref, 1e-9)
+    check(t, "grad", g, g_ref, GRAD_TOL_FP64, GRAD_TOL_FP64)
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -66,8 +70,9 @@ def test_grad_mixed_matches_oracle(L, case):
     p = _p(case, jitter=1e-3)
     ll_ref, g_ref = O2.loglik_grad(p)
     ll, g = L.lma_loglik_grad(precision=L.MIXED, **L.problem_args(p))
-    print("mixed grad rel err", _rel(g, g_ref), "loglik rel err", abs(ll - ll_ref) / abs(ll_ref))
-    assert _rel(g, g_ref) <= GRAD_TOL_MIXED
+    t = f"grad_tiny{case[0]}_mixed"
+    check_scalar(t, "loglik", ll, ll_ref, LL_TOL_MIXED)
+    check(t, "grad", g, g_ref, GRAD_TOL_MIXED, GRAD_TOL_MIXED)
 
 
 def test_grad_c5_shaped_central_fd(L):
@@ -80,7 +85,7 @@ def test_grad_c5_shaped_central_fd(L):
     ll_ref, g_ref = O2.loglik_grad(p)
     args = L.problem_args(p)
     ll, g = L.lma_loglik_grad(precision=L.FP64, **args)
-    assert _rel(g, g_ref) <= GRAD_TOL_FP64
+    check("grad_c5_reduced_fp64", "grad", g, g_ref, GRAD_TOL_FP64, GRAD_TOL_FP64)
     th = np.concatenate([p.log_ell, [p.log_sigma_s, p.log_sigma_n]])
     h = 1e-4
     fd = np.empty_like(th)
@@ -94,10 +99,10 @@ def test_grad_c5_shaped_central_fd(L):
             vals.append(L.lma_loglik(precision=L.FP64, **a))
         fd[k] = (vals[0] - vals[1]) / (2 * h)
     # truncation error of the central difference ~ h^2 |f'''|: relative 1e-6
-    assert _rel(g, fd) <= 1e-6
+    check("grad_c5_reduced_fp64", "grad vs central difference", g, fd, 1e-6, 1e-6)
     llm, gm = L.lma_loglik_grad(precision=L.MIXED, **args)
-    print("C5-shaped mixed grad rel err", _rel(gm, g_ref))
-    assert _rel(gm, g_ref) <= GRAD_TOL_MIXED
+    check("grad_c5_reduced_mixed", "grad", gm, g_ref, GRAD_TOL_MIXED, GRAD_TOL_MIXED)
+    check_scalar("grad_c5_reduced_mixed", "loglik", llm, ll_ref, LL_TOL_MIXED)
 
 
 def test_autograd_wrapper(L):

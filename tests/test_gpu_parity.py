@@ -19,10 +19,14 @@ cases (C1, C2 recipe) keep the default jitter 1e-6.
 import numpy as np
 import pytest
 
+from _parity import check, check_scalar
+
 pytestmark = pytest.mark.gpu
 
 MEAN_TOL_MIXED = 1e-4
+MEAN_ELEM_MIXED = 3e-4
 VAR_TOL_MIXED = 2e-3
+VAR_ELEM_MIXED = 5e-3
 LL_TOL_MIXED = 1e-3
 TOL_FP64 = 1e-9
 
@@ -86,9 +90,10 @@ def test_fp64_matches_oracle(L, case):
     p = _tiny(case)
     f, m, v = oracle(p)
     model, mean, var = run_gpu(L, p, L.FP64)
-    assert rel(mean, m) <= TOL_FP64
-    assert rel(var, v) <= TOL_FP64
-    assert abs(L.lma_model_loglik(model) - f.loglik) <= TOL_FP64 * abs(f.loglik)
+    t = f"tiny{case[0]}_fp64"
+    check(t, "mean", mean, m, TOL_FP64, TOL_FP64)
+    check(t, "var", var, v, TOL_FP64, TOL_FP64, positive=True)
+    check_scalar(t, "loglik", L.lma_model_loglik(model), f.loglik, TOL_FP64)
 
 
 MIXED_TINY_JITTER = 1e-3
@@ -100,9 +105,10 @@ def test_mixed_matches_oracle(L, case):
     p.jitter = MIXED_TINY_JITTER
     f, m, v = oracle(p)
     model, mean, var = run_gpu(L, p, L.MIXED)
-    assert rel(mean, m) <= MEAN_TOL_MIXED
-    assert rel(var, v) <= VAR_TOL_MIXED
-    assert abs(L.lma_model_loglik(model) - f.loglik) <= LL_TOL_MIXED * abs(f.loglik)
+    t = f"tiny{case[0]}_mixed"
+    check(t, "mean", mean, m, MEAN_TOL_MIXED, MEAN_ELEM_MIXED)
+    check(t, "var", var, v, VAR_TOL_MIXED, VAR_ELEM_MIXED, positive=True)
+    check_scalar(t, "loglik", L.lma_model_loglik(model), f.loglik, LL_TOL_MIXED)
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
@@ -111,9 +117,13 @@ def test_host_buffers_and_latent_variance(L, prec):
     p.jitter = MIXED_TINY_JITTER
     _, m, v = oracle(p, noisy=False)
     _, mean, var = run_gpu(L, p, getattr(L, prec), on_device=False, noisy=False)
-    tol = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
-    assert rel(mean, m) <= tol
-    assert rel(var, v) <= (TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED)
+    t = f"host_latent_{prec.lower()}"
+    if prec == "FP64":
+        check(t, "mean", mean, m, TOL_FP64, TOL_FP64)
+        check(t, "var", var, v, TOL_FP64, TOL_FP64, positive=True)
+    else:
+        check(t, "mean", mean, m, MEAN_TOL_MIXED, MEAN_ELEM_MIXED)
+        check(t, "var", var, v, VAR_TOL_MIXED, VAR_ELEM_MIXED, positive=True)
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
@@ -140,15 +150,17 @@ def test_c1_full_config(L):
     f, m, v = oracle(p)
     for prec in ("FP64", "MIXED"):
         model, mean, var = run_gpu(L, p, getattr(L, prec))
+        t = f"c1_{prec.lower()}"
         if prec == "FP64":
-            assert rel(mean, m) <= TOL_FP64 and rel(var, v) <= TOL_FP64
-            assert abs(L.lma_model_loglik(model) - f.loglik) <= TOL_FP64 * abs(f.loglik)
+            check(t, "mean", mean, m, TOL_FP64, TOL_FP64)
+            check(t, "var", var, v, TOL_FP64, TOL_FP64, positive=True)
+            check_scalar(t, "loglik", L.lma_model_loglik(model), f.loglik, TOL_FP64)
         else:
-            assert rel(mean, m) <= MEAN_TOL_MIXED
+            check(t, "mean", mean, m, MEAN_TOL_MIXED, MEAN_ELEM_MIXED)
             rm_ref = np.sqrt(np.mean((m - p.yU) ** 2))
             rm = np.sqrt(np.mean((mean - p.yU) ** 2))
-            assert abs(rm - rm_ref) <= 1e-3 * rm_ref
-            assert rel(var, v) <= VAR_TOL_MIXED
+            check_scalar(t, "rmse", rm, rm_ref, 1e-3)
+            check(t, "var", var, v, VAR_TOL_MIXED, VAR_ELEM_MIXED, positive=True)
 
 
 @pytest.mark.parametrize("B", [1, 2, 3])
@@ -160,10 +172,16 @@ def test_c2_shaped_reduced(L, B):
     f, m, v = oracle(p)
     for prec in ("FP64", "MIXED"):
         model, mean, var = run_gpu(L, p, getattr(L, prec))
-        tol_m = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
-        tol_v = TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED
-        assert rel(mean, m) <= tol_m, (prec, rel(mean, m))
-        assert rel(var, v) <= tol_v, (prec, rel(var, v))
+        _check_pred(f"c2_reduced_b{B}_{prec.lower()}", prec, mean, m, var, v)
+
+
+def _check_pred(t, prec, mean, m, var, v):
+    if prec == "FP64":
+        check(t, "mean", mean, m, TOL_FP64, TOL_FP64)
+        check(t, "var", var, v, TOL_FP64, TOL_FP64, positive=True)
+    else:
+        check(t, "mean", mean, m, MEAN_TOL_MIXED, MEAN_ELEM_MIXED)
+        check(t, "var", var, v, VAR_TOL_MIXED, VAR_ELEM_MIXED, positive=True)
 
 
 def run_fit_predict(L, p, prec, B=None):
@@ -181,9 +199,9 @@ def test_mixed_fit_predict_matches_oracle(L, case):
     p.jitter = MIXED_TINY_JITTER
     f, m, v = oracle(p)
     model, mean, var = run_fit_predict(L, p, L.MIXED)
-    assert rel(mean, m) <= MEAN_TOL_MIXED
-    assert rel(var, v) <= VAR_TOL_MIXED
-    assert abs(L.lma_model_loglik(model) - f.loglik) <= LL_TOL_MIXED * abs(f.loglik)
+    t = f"tiny{case[0]}_fit_predict_mixed"
+    _check_pred(t, "MIXED", mean, m, var, v)
+    check_scalar(t, "loglik", L.lma_model_loglik(model), f.loglik, LL_TOL_MIXED)
 
 
 @pytest.mark.parametrize("B", [1, 2])
@@ -193,10 +211,7 @@ def test_c2_shaped_fit_predict(L, B):
     f, m, v = oracle(p)
     for prec in ("FP64", "MIXED"):
         model, mean, var = run_fit_predict(L, p, getattr(L, prec))
-        tol_m = TOL_FP64 if prec == "FP64" else MEAN_TOL_MIXED
-        tol_v = TOL_FP64 if prec == "FP64" else VAR_TOL_MIXED
-        assert rel(mean, m) <= tol_m, (prec, rel(mean, m))
-        assert rel(var, v) <= tol_v, (prec, rel(var, v))
+        _check_pred(f"c2_reduced_fit_predict_b{B}_{prec.lower()}", prec, mean, m, var, v)
 
 
 def test_mixed_window_failure_retries_in_fp64(L):
@@ -230,7 +245,7 @@ def test_single_block_and_tiny_sizes(L):
         p = make_random_problem(5, sizes, d=d, s=s, B=B, test_sizes=ts)
         f, m, v = oracle(p)
         model, mean, var = run_gpu(L, p, L.FP64)
-        assert rel(mean, m) <= TOL_FP64 and rel(var, v) <= TOL_FP64, case
+        _check_pred(f"single_block_{case[0]}", "FP64", mean, m, var, v)
 
 
 def test_no_test_points(L):

@@ -111,61 +111,117 @@ def rff_draw(rng: np.random.Generator, d: int, n_features: int, ell: float,
              sigma_s: float):
     """Random-Fourier-feature approximation of an SE-kernel GP sample path
     (Rahimi & Recht 2007): f(x) = sigma_s sqrt(2/F) sum_f a_f cos(w_f.x + c_f),
-    w_f ~ N(0, ell^-2 I), c_f ~ U[0, 2 pi), a_f ~ N(0, 1)."""
+    w_f ~ N(0, ell^-2 I), c_f ~ U[0, 2 pi), a_f ~ N(0, 1).
+
+    The weights are drawn with numpy (bit-identical on every platform); f is
+    evaluated in FP64 with torch's multithreaded CPU kernels (a 2-million-point
+    draw with 4,096 features is ~8e9 cosines), which may differ from numpy's
+    cosine in the last bit: the outputs y agree across machines to ~1e-15
+    relative, the partition (built from the inputs only) exactly."""
     W = rng.standard_normal((n_features, d)) / ell
     c = rng.uniform(0.0, 2.0 * math.pi, n_features)
     a = rng.standard_normal(n_features)
     scale = sigma_s * math.sqrt(2.0 / n_features)
 
     def f(x: np.ndarray) -> np.ndarray:
-        out = np.empty(x.shape[0])
-        chunk = 8192
-        for i in range(0, x.shape[0], chunk):
-            ph = x[i:i + chunk] @ W.T + c
-            out[i:i + chunk] = scale * (np.cos(ph) @ a)
-        return out
+        import torch
+        out = torch.empty(x.shape[0], dtype=torch.float64)
+        xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+        Wt, ct, at = torch.from_numpy(W), torch.from_numpy(c), torch.from_numpy(a)
+        chunk = 32768
+        with torch.no_grad():
+            for i in range(0, x.shape[0], chunk):
+                ph = torch.addmm(ct, xt[i:i + chunk], Wt.T)
+                out[i:i + chunk] = torch.cos_(ph) @ at
+        return scale * out.numpy()
 
     return f
 
 
+def _sqdist(X: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Squared distances of the rows of X to the point c (or, for c of shape
+    (k, d), to each row of c), accumulated axis by axis with elementwise
+    operations only: IEEE-exact, so the same bits on every platform (a BLAS
+    product or a vectorised reduction could differ in the last bit and flip a
+    nearest-centre decision)."""
+    if c.ndim == 1:
+        out = np.zeros(X.shape[0])
+        for q in range(X.shape[1]):
+            t = X[:, q] - c[q]
+            out += t * t
+        return out
+    out = np.zeros((X.shape[0], c.shape[0]))
+    for q in range(X.shape[1]):
+        t = X[:, q][:, None] - c[:, q][None, :]
+        out += t * t
+    return out
+
+
+def _dot_axes(X: np.ndarray, v) -> np.ndarray:
+    """X @ v accumulated axis by axis (platform-exact, see _sqdist)."""
+    out = np.zeros(X.shape[0])
+    for q in range(X.shape[1]):
+        out += X[:, q] * float(v[q])
+    return out
+
+
 def _kmeans(rng: np.random.Generator, X: np.ndarray, k: int, iters: int = 15):
-    """Seeded Lloyd iterations from a k-means++ initialisation."""
+    """Seeded Lloyd iterations from a k-means++ initialisation (platform-exact:
+    distances by _sqdist, sums by np.bincount's in-order accumulation and
+    math.fsum)."""
     n = X.shape[0]
     sub = X if n <= 20000 else X[rng.choice(n, 20000, replace=False)]
     centers = np.empty((k, X.shape[1]))
     centers[0] = sub[rng.integers(sub.shape[0])]
-    d2 = np.sum((sub - centers[0]) ** 2, axis=1)
+    d2 = _sqdist(sub, centers[0])
     for j in range(1, k):
-        p = d2 / d2.sum()
+        p = d2 / math.fsum(d2)
         centers[j] = sub[rng.choice(sub.shape[0], p=p)]
-        d2 = np.minimum(d2, np.sum((sub - centers[j]) ** 2, axis=1))
+        d2 = np.minimum(d2, _sqdist(sub, centers[j]))
     for _ in range(iters):
         lab = _nearest(X, centers)
-        for j in range(k):
-            sel = lab == j
-            if np.any(sel):
-                centers[j] = X[sel].mean(axis=0)
+        cnt = np.bincount(lab, minlength=k)
+        for q in range(X.shape[1]):
+            sums = np.bincount(lab, weights=X[:, q], minlength=k)
+            centers[:, q] = np.where(cnt > 0, sums / np.maximum(cnt, 1), centers[:, q])
     return centers, _nearest(X, centers)
 
 
 def _nearest(X: np.ndarray, C: np.ndarray) -> np.ndarray:
     out = np.empty(X.shape[0], dtype=np.int64)
     for i in range(0, X.shape[0], 16384):
-        x = X[i:i + 16384]
-        d2 = (np.sum(x * x, 1)[:, None] - 2.0 * x @ C.T + np.sum(C * C, 1)[None, :])
-        out[i:i + 16384] = np.argmin(d2, axis=1)
+        out[i:i + 16384] = np.argmin(_sqdist(X[i:i + 16384], C), axis=1)
     return out
+
+
+def _top_axis(P: np.ndarray, iters: int = 300) -> np.ndarray:
+    """Leading principal axis of the rows of P (centred), by a fixed number of
+    power iterations on P^T P with exactly rounded sums (math.fsum), so that
+    it is bit-identical on every platform; sign: largest component positive."""
+    k, d = P.shape
+    cov = [[math.fsum(float(P[j, a]) * float(P[j, b]) for j in range(k)) for b in range(d)] for a in range(d)]
+    v = [1.0 / math.sqrt(d)] * d
+    for _ in range(iters):
+        w = [math.fsum(cov[a][b] * v[b] for b in range(d)) for a in range(d)]
+        nrm = math.sqrt(math.fsum(x * x for x in w))
+        if nrm == 0.0:
+            break
+        v = [x / nrm for x in w]
+    big = max(range(d), key=lambda a: abs(v[a]))
+    if v[big] < 0:
+        v = [-x for x in v]
+    return np.array(v)
 
 
 def _cluster_order_keys(X: np.ndarray, centers: np.ndarray, labels: np.ndarray):
     """Order clusters by their centroid's projection on the top principal axis
     of the centroids; points are keyed by (cluster rank, own projection)."""
-    cc = centers - centers.mean(axis=0)
-    _, _, vt = np.linalg.svd(cc, full_matrices=False)
-    axis = vt[0]
+    k, d = centers.shape
+    mean = np.array([math.fsum(centers[:, q]) / k for q in range(d)])
+    axis = _top_axis(centers - mean)
     rank_of_cluster = np.empty(len(centers), dtype=np.int64)
-    rank_of_cluster[np.argsort(centers @ axis, kind="stable")] = np.arange(len(centers))
-    return rank_of_cluster[labels], X @ axis, axis, rank_of_cluster
+    rank_of_cluster[np.argsort(_dot_axes(centers, axis), kind="stable")] = np.arange(len(centers))
+    return rank_of_cluster[labels], _dot_axes(X, axis), axis, rank_of_cluster
 
 
 def _morton_keys(X01: np.ndarray, bits: int = 8) -> np.ndarray:
@@ -291,7 +347,7 @@ def make_problem(name: str, N: Optional[int] = None, M: Optional[int] = None,
         block_ptr = _ptr_from_sizes(sizes)
         # test points: same key (cluster rank, projection) -> position -> block
         tl = _nearest(XU, centers)
-        tr, tp = rank_of_cluster[tl], XU @ axis
+        tr, tp = rank_of_cluster[tl], _dot_axes(XU, axis)
         pos = np.empty(U_, dtype=np.int64)
         starts = np.searchsorted(crank_s, np.arange(M_), side="left")
         ends = np.searchsorted(crank_s, np.arange(M_), side="right")
@@ -336,16 +392,16 @@ def make_problem(name: str, N: Optional[int] = None, M: Optional[int] = None,
     return prob
 
 
-def make_replicated(name: str, copies: int, B: Optional[int] = None, **kw) -> Problem:
-    """`copies` draws of configuration `name` (draw 0 first) joined into one
-    problem: their blocks and test blocks are concatenated in draw order and
-    the support set is draw 0's.  Every draw has the configuration's size, so
-    a problem split by draws into `copies` shards keeps the work per shard
-    fixed (weak scaling)."""
-    parts = [make_problem(name, B=B, draw=k, **kw) for k in range(int(copies))]
+def make_replicated(name: str, copies: int, B: Optional[int] = None, first_draw: int = 0, **kw) -> Problem:
+    """`copies` draws of configuration `name` (draws first_draw,
+    first_draw + 1, ...) joined into one problem: their blocks and test
+    blocks are concatenated in draw order and the support set is the first
+    draw's.  Every draw has the configuration's size, so a problem split by
+    draws into shards keeps the work per shard fixed (weak scaling)."""
+    parts = [make_problem(name, B=B, draw=first_draw + k, **kw) for k in range(int(copies))]
     p0 = parts[0]
     if len(parts) == 1:
-        return p0
+        return dataclasses.replace(p0, meta=dict(p0.meta, copies=1, first_draw=int(first_draw)))
     off, toff = 0, 0
     ptrs, tptrs = [np.zeros(1, dtype=np.int64)], [np.zeros(1, dtype=np.int64)]
     for q in parts:
@@ -357,7 +413,7 @@ def make_replicated(name: str, copies: int, B: Optional[int] = None, **kw) -> Pr
         p0, name=f"{name}x{copies}", X=np.concatenate([q.X for q in parts]), y=np.concatenate([q.y for q in parts]),
         block_ptr=np.concatenate(ptrs), XU=np.concatenate([q.XU for q in parts]),
         yU=np.concatenate([q.yU for q in parts]), test_block_ptr=np.concatenate(tptrs),
-        meta=dict(p0.meta, copies=int(copies)))
+        meta=dict(p0.meta, copies=int(copies), first_draw=int(first_draw)))
 
 
 def make_random_problem(seed: int, sizes, d: int = 2, s: int = 6, B: int = 1,
