@@ -102,18 +102,21 @@ def kernel_work(p, B, fused=True):
     tp = p.test_block_ptr
     nu = [int(tp[m + 1] - tp[m]) for m in range(M)]
     trows = [sum(nu[n] for n in range(m, min(m + B, M - 1) + 1)) for m in range(M)] if fused else [0] * M
-    step = wide = tri = 0.0
-    SP = 256  # columns of a super-panel: k_chol_wide applies [0, kb), the 64-wide steps [kb, k0)
+    step = wide = mid = tri = 0.0
+    SP, HP = 256, 128  # the 256-wide update applies [0, kb), the 128-wide one [kb, kh), the 64-wide steps [kh, k0)
     for (n, b, nb), t in zip(ws, trows):
         rows = n + s + 1 + t
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
-            kb = (k0 // SP) * SP
-            step += 2.0 * ((rows - k0) * w - w * (w - 1) / 2.0) * (k0 - kb)
+            kb, kh = (k0 // SP) * SP, (k0 // HP) * HP
+            step += 2.0 * ((rows - k0) * w - w * (w - 1) / 2.0) * (k0 - kh)
             tri += 2.0 * max(0, rows - k0 - w) * w * w / 2.0
             if k0 == kb and kb > 0:
                 c = min(SP, n - kb)
                 wide += 2.0 * ((rows - kb) * c - c * (c - 1) / 2.0) * kb
+            if k0 == kh and kh > kb:
+                c = min(HP, n - kh)
+                mid += 2.0 * ((rows - kh) * c - c * (c - 1) / 2.0) * (kh - kb)
     resid = sum(s * n * n for n, _, _ in ws)
     gram = sum(b * (s + 1) * (s + 1) for _, b, _ in ws)
     psweep = prhs = pacc = 0.0
@@ -124,9 +127,11 @@ def kernel_work(p, B, fused=True):
             prhs += 2.0 * nu[nb_] * n * s
             pacc += 2.0 * nu[nb_] * (b if m < nb_ else n) * s
     proj = (p.N + p.U) * s * s           # V = L^-1 K_SD: s^2 / 2 multiply-adds per point (triangular)
+    var = p.U * s * s                    # L_C^-1 h of every test point (triangular)
     f64 = 2.0 * s ** 3 / 3.0             # Cholesky of Sigma_SS and of I + A, s^3 / 6 multiply-adds each
-    return {"k_chol_step_tc": step, "k_chol_wide": wide, "k_chol_trsm_tc": tri, "k_resid_tc": resid,
+    return {"k_chol_step_tc": step, "k_chol_wide": wide, "k_chol_mid": mid, "k_chol_trsm_tc": tri, "k_resid_tc": resid,
             "k_gram_split": gram, "k_pred_rhs_tc": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
+            "k_proj_tc": proj, "k_var_gemm": var,
             "k_f64_panel": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
 
 
@@ -152,19 +157,28 @@ def sources_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_wide", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
+TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_wide", "k_chol_mid", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
                   "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc"}
+BF16X6_KERNELS = {"k_proj_tc"}   # bfloat16 x 6 split products (the variance term shares the name k_var_gemm)
 FP64_KERNELS = {"k_f64_panel"}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rate of the part
 FP64_PEAK = 1.25             # nominal FP64 TFLOP/s of the part (no measured figure)
 
 
-def roofline_of(name, flops, tot_ms, n_l, peaks, sustained=True):
+def roofline_of(name, flops, tot_ms, n_l, peaks, sustained=True, bf16_var=True):
     """Achieved algorithmic rate of one kernel over its launches against its peak."""
     achieved = flops / (tot_ms / 1e3) / 1e12
     pk = peaks or {}
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    if name in TENSOR_KERNELS:
+    if name in BF16X6_KERNELS or (name == "k_var_gemm" and bf16_var):
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        src = "measured" if key in pk else "fallback"
+        peak = pk.get(key, 1700.0 if sustained else 1900.0)
+        r = {"bound": "tensor",
+             "peak_note": f"BF16 dense, {src} {'sustained' if sustained else 'burst'} (MEASURED_PEAKS.json), of "
+                          f"{src}; the bf16x6 split issues six BF16 MMAs per algorithmic product, so frac <= 1/6",
+             "tensor_pipe_frac_issued": 6.0 * achieved / peak}
+    elif name in TENSOR_KERNELS:
         key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
         src = "measured" if key in pk else "fallback"
         bf16 = pk.get(key, 1700.0 if sustained else 1900.0)

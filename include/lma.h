@@ -294,6 +294,24 @@ int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* laun
  * Waits for the recorded events; returns the number of records.           */
 int lma_profile_trace(char* names, int names_cap, double* t0_ms, double* t1_ms, int cap);
 
+/* Launch-shape autotuner (not part of the paper's method).  Some launches
+ * have several valid shapes (the number of window groups of the summary
+ * Gram, ...): the first call that meets a new shape class times each
+ * candidate on its own data (CUDA events on the call's stream; only launches
+ * that can be repeated without changing results) and keeps the fastest for
+ * the rest of the process, per device; with the environment variable
+ * LMA_TUNE_CACHE naming a file, choices are also appended there and read back
+ * by later processes.  lma_autotune(0) (or LMA_AUTOTUNE=0 in the environment)
+ * makes every launch take the shape its cost model predicts; lma_autotune(1)
+ * turns timing back on (the default).  Results differ between shapes only by
+ * the order of FP64 partial sums.                                          */
+void lma_autotune(int enabled);
+
+/* Text report of the tuner's choices, one line per shape class:
+ * "device | key | choice | candidate:ms ...", NUL-terminated into buf (cap
+ * bytes, may be NULL).  Returns the full length of the report.            */
+int lma_autotune_report(char* buf, int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -306,6 +306,30 @@ def lma_model_precision(model) -> int:
     return int(_abi.load().lma_model_precision(model.handle))
 
 
+def lma_autotune(enabled: bool) -> None:
+    """Turn the launch-shape autotuner's timing on or off (see lma_autotune in lma.h)."""
+    _abi.load().lma_autotune(int(bool(enabled)))
+
+
+def lma_autotune_report() -> list:
+    """[(device, key, choice, {candidate: ms})] of the tuner's cached choices."""
+    lib = _abi.load()
+    n = lib.lma_autotune_report(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib.lma_autotune_report(buf, n + 1)
+    out = []
+    for line in buf.value.decode().splitlines():
+        parts = [x.strip() for x in line.split("|")]
+        if len(parts) < 4:
+            continue
+        ms = {}
+        for tok in parts[3].split():
+            c, _, v = tok.partition(":")
+            ms[int(c)] = float(v)
+        out.append((parts[0], parts[1], int(parts[2]), ms))
+    return out
+
+
 def profile_start(name_filter: str = "") -> None:
     """Bracket matching kernel launches with CUDA events (see lma_profile_start)."""
     _abi.load().lma_profile_start(name_filter.encode())

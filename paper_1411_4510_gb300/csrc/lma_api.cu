@@ -4,6 +4,7 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <string>
@@ -558,3 +559,18 @@ int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* laun
 }
 
 }  // extern "C"
+
+// ---- launch-shape autotuner ------------------------------------------------
+#include "lma_tune.cuh"
+
+extern "C" void lma_autotune(int enabled) { lma::tune::set_enabled(enabled != 0); }
+
+extern "C" int lma_autotune_report(char* buf, int cap) {
+  const std::string r = lma::tune::report();
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>(r.size(), (size_t)cap - 1);
+    memcpy(buf, r.data(), n);
+    buf[n] = '\0';
+  }
+  return (int)r.size();
+}

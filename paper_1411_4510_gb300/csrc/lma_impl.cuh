@@ -62,6 +62,15 @@ struct Arena {
     for (void* p : ptrs) cudaFreeAsync(p, st);
     ptrs.clear();
   }
+  // frees one buffer of this arena early (stream-ordered)
+  void free_one(void* p) {
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
+        cudaFreeAsync(p, st);
+        ptrs.erase(ptrs.begin() + (long)i);
+        return;
+      }
+  }
 };
 
 // Optional launch profiler: when enabled, a CUDA event pair is recorded on the
@@ -169,6 +178,9 @@ struct ModelCore {
   double* beta = nullptr;     // s
   void* LcT = nullptr;        // s*s, (L_C^-1)[i][k] at [k][i]   (T)
   double quad = 0, wCw = 0, logdetC = 0, logdetR = 0, loglik = 0;
+  uint16_t* linv3 = nullptr;  // three bfloat16 planes of L_SS^-1 (mixed form on the tensor cores), brows x ldk each
+  uint16_t* lcinv3 = nullptr; // the same for L_C^-1 (global step)
+  int ldk = 0, brows = 0;     // plane row length (s rounded up to 64) and rows per plane (s rounded up to 128)
   double* kss = nullptr;      // Sigma_SS factor buffer: L_SS (rows < npS) and L_SS^-T rows (FP64)
   double* ss64 = nullptr;     // s*d scaled support inputs (FP64)
   int npS = 0;

@@ -15,7 +15,9 @@
 #include "lma_kernels.cuh"
 #include "lma_grad.cuh"
 #include "lma_tc.cuh"
+#include "lma_bf6.cuh"
 #include "lma_f64.cuh"
+#include "lma_tune.cuh"
 
 namespace lma {
 
@@ -109,7 +111,8 @@ Staging& staging() {
 }
 
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
-static size_t wide_smem() { return sizeof(tc::WsSmem<2, 256>) + tc::kTcAlignSlack; }
+template <int BN>
+static size_t wide_smem() { return sizeof(tc::WsSmem<2, BN>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
 static size_t split_smem_bytes() { return sizeof(SplitSmem) + tc::kTcAlignSlack; }
 
@@ -163,6 +166,73 @@ static CUtensorMap rows_tensor_map(const float* base, int64_t rows, int cols) {
   return m;
 }
 
+// Tensor map of row-major bfloat16 planes (rows x cols, cols a multiple of
+// 64, 16-byte-aligned base): 64 x 128 boxes, 128-byte swizzle; rows outside
+// [0, rows) read zero.
+static CUtensorMap bf16_tensor_map(const uint16_t* base, int64_t rows, int cols) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    throw Fail{};
+  }
+  CUtensorMap m;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * sizeof(uint16_t)};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), gdim, gstride, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled (bfloat16) failed (" + std::to_string((int)r) + ")");
+    throw Fail{};
+  }
+  return m;
+}
+
+// out[p][i] = sum_{k <= i} A[p][k] Linv[i][k] (p < nrows, i < s) on the tensor
+// cores with the bf16x6 split (lma_bf6.cuh): A and Linv given as three
+// bfloat16 planes (nrows and brows rows per plane, row length ldk).
+static void proj_tc(cudaStream_t st, const char* name, const uint16_t* Ap, int64_t nrows, const uint16_t* Bp,
+                    int brows, int s, int ldk, float* out, int64_t ldo, int* err) {
+  if (nrows == 0) return;
+  const CUtensorMap am = bf16_tensor_map(Ap, 3 * nrows, ldk), bm = bf16_tensor_map(Bp, 3 * (int64_t)brows, ldk);
+  const int64_t ntiles = ((nrows + 127) / 128) * ((s + 127) / 128);
+  launch(name, k_proj_tc, persistent_grid((size_t)ntiles), bf6::NTHR, bf6::smem_bytes(), st, am, (int)nrows, bm,
+         brows, nrows, s, out, ldo, err);
+}
+
+// Whitened support coordinates of npts points given by their scaled inputs
+// xsP (npts x d): out[p][i] = (L_SS^-1 Sigma_{S p})_i, point-major with row
+// length s (H3: V = L_SS^-1 Sigma_SD).  Mixed form on the tensor cores: the
+// covariances are evaluated straight into bfloat16 planes and multiplied by
+// the planes of L_SS^-1 (bf16x6); otherwise K_SD is formed and multiplied by
+// ET = L_SS^-T on the CUDA cores.
+template <typename T>
+static void project(const ModelCore& mc, const T* xsP, int64_t npts, T* out, Arena& tmp, cudaStream_t st, int* err) {
+  const int64_t s = mc.s;
+  const int d = (int)mc.d;
+  if (npts == 0) return;
+  if (sizeof(T) == 4 && mc.linv3) {
+    uint16_t* Ap = tmp.alloc<uint16_t>((size_t)3 * npts * mc.ldk);
+    launch("k_kds_bf3", pad_dim(d) == 8 ? k_kds_bf3<8> : k_kds_bf3<MAXD>, dim3((unsigned)(mc.ldk / 64), nblk(npts, 32)),
+           256, 0, st, (const float*)xsP, npts, d, (const float*)mc.ssT, (int)s, (float)mc.ss2, mc.ldk, Ap);
+    proj_tc(st, "k_proj_tc", Ap, npts, mc.linv3, mc.brows, (int)s, mc.ldk, (float*)out, s, err);
+    tmp.free_one(Ap);
+    return;
+  }
+  T* Kds = tmp.alloc<T>(npts * s);
+  launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(npts, TB)), NT, 0, st, xsP, npts, d, (const T*)mc.ssT, (int)s,
+         (T)mc.ss2, Kds);
+  if (sizeof(T) == 4 && s % 4 == 0)
+    launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(npts, 128)), NT, 0, st, (const float*)Kds, npts, (int)s,
+           (const float*)mc.ET, (float*)out, (int)s);
+  else
+    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(npts, TB)), NT, 0, st, (const T*)Kds, npts, (int)s,
+           (const T*)mc.ET, out, (int)s);
+  tmp.free_one(Kds);
+}
+
 // TF32 hi/lo halves (k_split_tf32) of the point-major rows of V (n x s) with
 // the row length padded to ld = s rounded up to 32 (zero pad), reversed or not.
 static void split_rows(cudaStream_t st, const float* V, int64_t n, int64_t s, int ld, bool reverse, float* hi,
@@ -212,7 +282,9 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_pred_rhs_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
-    cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem());
+    cudaFuncSetAttribute(k_chol_wide<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<256>());
+    cudaFuncSetAttribute(k_chol_wide<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<128>());
+    cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
     done = true;
   }
 }
@@ -236,23 +308,32 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
     int maxrows = 0;
     for (const Win& w : wins) maxrows = std::max(maxrows, w.rows);
     const bool tc = tc_err && sizeof(T) == 4;
-    constexpr int SP = 256;
+    constexpr int SP = 256, HP = 128;
     for (int kp = 0; kp < maxpan; ++kp) {
       const int k0 = kp * TB;
       if (tc) {
-        const int kb = (k0 / SP) * SP;
+        // columns [0, kb) of super-panel [kb, kb + 256) come from the 256-wide
+        // update, [kb, kh) of its second half from the 128-wide one, and the
+        // 64-wide panel step adds [kh, k0) (at most 64 columns)
+        const int kb = (k0 / SP) * SP, kh = (k0 / HP) * HP;
         if (k0 == kb && kb > 0) {
           const unsigned gy = (unsigned)((maxrows - kb + 127) / 128);
-          launch_pdl("k_chol_wide", k_chol_wide, dim3(nw, gy), tc::kWsThreads, wide_smem(), st, wins_d, (float*)buf, kb,
-                 tc_err);
+          launch_pdl("k_chol_wide", k_chol_wide<256>, dim3(nw, gy), tc::kWsThreads, wide_smem<256>(), st, wins_d,
+                     (float*)buf, kb, 0, tc_err);
         }
-        const unsigned gy = (unsigned)((maxrows - k0 + 127) / 128);
+        if (k0 == kh && kh > kb) {
+          const unsigned gy = (unsigned)((maxrows - kh + 127) / 128);
+          launch_pdl("k_chol_mid", k_chol_wide<128>, dim3(nw, gy), tc::kWsThreads, wide_smem<128>(), st, wins_d,
+                     (float*)buf, kh, kb, tc_err);
+        }
+        // with nothing to add (k0 = kh) only the row tile holding the diagonal block runs
+        const unsigned gy = k0 == kh ? 1u : (unsigned)((maxrows - k0 + 127) / 128);
         launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, gy), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-               (float*)dinv, info, kp, kb, tc_err);
+                   (float*)dinv, info, kp, kh, tc_err);
         if (maxrows - (kp + 1) * TB > 0) {
           const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
           launch_pdl("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-                 (const float*)dinv, kp, tc_err);
+                     (const float*)dinv, kp, tc_err);
         }
       } else {
         launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,
@@ -366,14 +447,15 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
   mc.ET = ET;
   // V = L_SS^-1 Sigma_SD, point-major
-  T* Kds = tmp.alloc<T>(n * s);
-  launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, xsT, n, (int)d, ssT, (int)s, (T)mc.ss2, Kds);
+  if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
+    mc.ldk = (int)roundup(s, 64);
+    mc.brows = (int)roundup(s, 128);
+    mc.linv3 = mc.keep.alloc<uint16_t>((size_t)3 * mc.brows * mc.ldk);
+    launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb, (int64_t)npS,
+           (int)s, mc.brows, mc.ldk, mc.linv3);
+  }
   T* Vt = mc.keep.alloc<T>(n * s);
-  if (sizeof(T) == 4 && s % 4 == 0)
-    launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(n, 128)), NT, 0, st, (const float*)Kds, n, (int)s,
-           (const float*)ET, (float*)Vt, (int)s);
-  else
-    launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(n, TB)), NT, 0, st, Kds, n, (int)s, ET, Vt, (int)s);
+  project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
   mc.Vt = Vt;
 }
 
@@ -465,19 +547,13 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     int nchunk = (int)std::min<int64_t>(nown, 32);
     int chunk = (int)((nown + nchunk - 1) / nchunk);
     std::vector<int2> tl;  // tensor cores: 128 x 128 tiles of the lower triangle
-    if (tc_err) {
-      const int nt = (se + 127) / 128;
-      for (int I = 0; I < nt; ++I)
-        for (int J = 0; J <= I; ++J) tl.push_back(make_int2(I, J));
-      // window groups: (tile, group) items fill the SMs once
-      const int64_t ngr = std::max<int64_t>(1, std::min<int64_t>(nown, (int64_t)persistent_grid(1u << 30) / (int64_t)tl.size()));
-      chunk = (int)((nown + ngr - 1) / ngr);
-      nchunk = (int)((nown + chunk - 1) / chunk);
-    }
-    double* partial = tmp.alloc<double>((size_t)nchunk * se * se);
+    double* partial = nullptr;
     int gtile = TB;
     if (tc_err) {
       gtile = 128;
+      const int nt = (se + 127) / 128;
+      for (int I = 0; I < nt; ++I)
+        for (int J = 0; J <= I; ++J) tl.push_back(make_int2(I, J));
       int kmax = 32;
       for (int64_t m = own_begin; m < own_end; ++m) {
         const Win& w = mc.wins[m - w_begin];
@@ -490,9 +566,41 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       const CUtensorMap sh = rows_tensor_map(shi, nown * se, kmax), sl = rows_tensor_map(slo, nown * se, kmax);
       int2* tld = tmp.alloc<int2>(tl.size());
       stage_copy(tld, tl.data(), sizeof(int2) * tl.size(), st);
-      launch("k_gram_split", k_gram_split, persistent_grid(tl.size() * nchunk), kSplitThreads, split_smem_bytes(), st,
-             (const int2*)tld, (int)tl.size(), (int)nown, chunk, se, kmax, sh, sl, partial, tc_err);
+      // Window groups: item (tile, group) sums the group's windows; the
+      // groups' FP64 partials are added by k_gram_reduce.  Model: persistent
+      // waves x windows per item (+ half a window of per-item overhead),
+      // partials held to 1 GB; the tuner times the model's choice and its
+      // neighbours.
+      const int64_t nsm = persistent_grid(1u << 30);
+      const int64_t gcap = std::max<int64_t>(1, std::min<int64_t>(nown, (int64_t)(1e9 / (8.0 * se * se))));
+      auto groups_of = [&](int64_t g) { const int64_t c = (nown + g - 1) / g; return (nown + c - 1) / c; };
+      auto cost = [&](int64_t g) {
+        const int64_t c = (nown + g - 1) / g, G = (nown + c - 1) / c;
+        return (double)((tl.size() * G + nsm - 1) / nsm) * ((double)c + 0.5);
+      };
+      int64_t gbest = 1;
+      for (int64_t g = 1; g <= gcap; ++g)
+        if (cost(g) < cost(gbest) - 1e-9) gbest = g;
+      std::vector<int> cands;
+      for (int64_t g : {gbest, gbest / 2, gbest * 2, gbest / 4, (int64_t)1})
+        if (g >= 1 && g <= gcap && std::find(cands.begin(), cands.end(), (int)groups_of(g)) == cands.end())
+          cands.push_back((int)groups_of(g));
+      int64_t gmaxc = 1;
+      for (int c : cands) gmaxc = std::max<int64_t>(gmaxc, c);
+      partial = tmp.alloc<double>((size_t)gmaxc * se * se);
+      auto run = [&](int g) {
+        const int c = (int)((nown + g - 1) / g);
+        launch("k_gram_split", k_gram_split, persistent_grid(tl.size() * g), kSplitThreads, split_smem_bytes(), st,
+               (const int2*)tld, (int)tl.size(), (int)nown, c, se, kmax, sh, sl, partial, tc_err);
+      };
+      const std::string key = "k_gram_split se=" + std::to_string(se) + " windows=" + std::to_string(nown) +
+                              " k=" + std::to_string(kmax) + " sm=" + std::to_string(nsm);
+      const int g = tune::pick(key, cands, (int)groups_of(gbest), st, run);
+      chunk = (int)((nown + g - 1) / g);
+      nchunk = (int)((nown + chunk - 1) / chunk);
+      run(g);
     } else {
+      partial = tmp.alloc<double>((size_t)nchunk * se * se);
       launch("k_gram", k_gram<T>, dim3(nte * (nte + 1) / 2, nchunk), NT, 0, st, wown, (int)nown, chunk, (int)s, wbuf,
              partial);
     }
@@ -541,6 +649,11 @@ void Impl<T>::fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on) {
     T* LcT = mc.keep.alloc<T>(s * s);
     launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, cb + (int64_t)npC * npC, npC, (int)s, LcT);
     mc.LcT = LcT;
+    if (mc.linv3) {  // bfloat16 planes of L_C^-1 for the variance term on the tensor cores
+      mc.lcinv3 = mc.keep.alloc<uint16_t>((size_t)3 * mc.brows * mc.ldk);
+      launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)cb, (int64_t)npC,
+             (int)s, mc.brows, mc.ldk, mc.lcinv3);
+    }
     if (sizeof(T) == 4) {
       float2* bs = tmp.alloc<float2>(s);
       launch("k_split_beta", k_split_beta, nblk(s), NT, 0, st, (const double*)mc.beta, (int)s, bs);
@@ -685,16 +798,8 @@ void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
   }
   float* xu = ft.keep.alloc<float>(U * d);
   launch("k_scale", k_scale<float>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
-  float* Kus = tmp.alloc<float>(U * s);
-  launch("k_kds", k_kds<float>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const float*)xu, U, d,
-         (const float*)mc.ssT, (int)s, (float)mc.ss2, Kus);
   float* Vu = ft.keep.alloc<float>(U * s);
-  if (s % 4 == 0)
-    launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
-           (const float*)mc.ET, Vu, (int)s);
-  else
-    launch("k_proj", k_proj<float>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const float*)Kus, U, (int)s,
-           (const float*)mc.ET, Vu, (int)s);
+  project<float>(mc, (const float*)xu, U, Vu, tmp, st, mc.flags + 2);
   ft.xu = xu;
   ft.Vu = Vu;
   std::vector<Pair> pairs;
@@ -736,6 +841,8 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       tmp.release();
       return;
     }
+    int* perr = tmp.alloc<int>(1);  // tensor-core pipeline timeout, checked at the end
+    LMA_CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
     T* xu = nullptr;
     T* Vu = nullptr;
     if (ft) {  // test projections made before the fit's sweep
@@ -750,16 +857,8 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
       }
       xu = tmp.alloc<T>(U * d);
       launch("k_scale", k_scale<T>, nblk(U * d), NT, 0, st, XUd, U, d, mc.inv_ell_d, nullptr, xu);
-      T* Kus = tmp.alloc<T>(U * s);
-      launch("k_kds", k_kds<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, xu, U, d, (const T*)mc.ssT, (int)s,
-             (T)mc.ss2, Kus);
       Vu = tmp.alloc<T>(U * s);
-      if (sizeof(T) == 4 && s % 4 == 0)
-        launch("k_proj", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)Kus, U, (int)s,
-               (const float*)mc.ET, (float*)Vu, (int)s);
-      else
-        launch("k_proj", k_proj<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, Kus, U, (int)s, (const T*)mc.ET, Vu,
-               (int)s);
+      project<T>(mc, (const T*)xu, U, Vu, tmp, st, perr);
     }
     // pairs (test block n, window m in [n-B, n])
     std::vector<Pair> pairs;
@@ -793,8 +892,6 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     stage_copy(isd, it_sw.data(), sizeof(int2) * it_sw.size(), st);
     stage_copy(iad, it_acc.data(), sizeof(int4) * it_acc.size(), st);
     stage_copy(itd, it_t12.data(), sizeof(int4) * it_t12.size(), st);
-    int* perr = tmp.alloc<int>(1);  // tensor-core pipeline timeout, checked at the end
-    LMA_CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
     T* Pbuf = ft ? (T*)mc.wbuf : tmp.alloc<T>(pe);
     const T* xs = (const T*)mc.xsT;
     const T* Vt = (const T*)mc.Vt;
@@ -885,7 +982,15 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
                                                                     (const T*)mc.ew, t1, t2);
     double* part = tmp.alloc<double>((size_t)nst * U);
     int ntile_var = nst;
-    if (sizeof(T) == 4 && s % 4 == 0) {  // L_C^-1 h with the 128 x 128 FP32 product, then row norms
+    if (sizeof(T) == 4 && mc.lcinv3) {  // L_C^-1 h on the tensor cores (bf16x6), then row norms
+      uint16_t* hp = tmp.alloc<uint16_t>((size_t)3 * U * mc.ldk);
+      launch("k_split_bf3", k_split_bf3, nblk(U * (mc.ldk / 8)), NT, 0, st, (const float*)h, U, (int)s, (int64_t)s,
+             mc.ldk, hp);
+      float* g = tmp.alloc<float>((size_t)U * s);
+      proj_tc(st, "k_var_gemm", hp, U, mc.lcinv3, mc.brows, (int)s, mc.ldk, g, s, perr);
+      launch("k_row_sqnorm", k_row_sqnorm, nblk(U * 32), NT, 0, st, (const float*)g, U, (int)s, part);
+      ntile_var = 1;
+    } else if (sizeof(T) == 4 && s % 4 == 0) {  // L_C^-1 h with the 128 x 128 FP32 product, then row norms
       float* g = tmp.alloc<float>((size_t)U * s);
       launch("k_var_gemm", k_proj128, dim3(nblk(s, 128), nblk(U, 128)), NT, 0, st, (const float*)h, U, (int)s,
              (const float*)mc.LcT, g, (int)s);

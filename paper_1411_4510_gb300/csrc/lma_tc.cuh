@@ -644,15 +644,18 @@ __device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
 
 }  // namespace tc
 
-// Super-panel update of the left-looking sweep (mixed form): for the 256
-// columns [s0, s0 + 256) of every window (clipped to its order), every row
-// r >= s0 gets A_{r,c} -= sum_{k < s0} L_{r,k} L_{c,k}, the contribution of
-// all columns left of the super-panel, as one 128 x 256 tensor-core tile per
-// CTA (grid: x = window, y = 128-row tile).  Only the lower triangle
-// (c <= r) is written.  The 64-wide panel steps inside the super-panel then
-// only add the contributions of columns [s0, k0).
+// Panel-group update of the left-looking sweep (mixed form): for the BN
+// columns [s0, s0 + BN) of every window (clipped to its order), every row
+// r >= s0 gets A_{r,c} -= sum_{kfrom <= k < s0} L_{r,k} L_{c,k}, as one
+// 128 x BN tensor-core tile per CTA (grid: x = window, y = 128-row tile).
+// Only the lower triangle (c <= r) is written.  BN = 256 with kfrom = 0 is the
+// super-panel update (all columns left of the super-panel); BN = 128 with
+// kfrom = the super-panel's first column adds the super-panel's first 128
+// columns to its last 128, so that the 64-wide panel steps only add the
+// columns of their own 128-column half.
+template <int BN>
 __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __restrict__ wins,
-                                                                float* __restrict__ buf, int s0,
+                                                                float* __restrict__ buf, int s0, int kfrom,
                                                                 int* __restrict__ err) {
   grid_dep_wait();
   grid_dep_launch();
@@ -661,26 +664,26 @@ __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __re
   if (s0 >= w.npad) return;
   const int r0 = s0 + blockIdx.y * 128;
   if (r0 >= w.rows) return;
-  const int ncol = min(256, w.npad - s0);
+  const int ncol = min(BN, w.npad - s0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  WsSmem<2, 256>& sm = ws_smem<2, 256>(smraw);
+  WsSmem<2, BN>& sm = ws_smem<2, BN>(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* A = buf + w.base;
   const int64_t ld = w.npad;
   ws_setup(sm);
   auto rowA = [&](int r) -> const float* {
     const int row = r0 + r;
-    return row < w.rows ? A + (int64_t)row * ld : nullptr;
+    return row < w.rows ? A + (int64_t)row * ld + kfrom : nullptr;
   };
-  auto rowB = [&](int c) -> const float* { return c < ncol ? A + (int64_t)(s0 + c) * ld : nullptr; };
-  const bool ok = ws_product(sm, s0, rowA, rowB);
+  auto rowB = [&](int c) -> const float* { return c < ncol ? A + (int64_t)(s0 + c) * ld + kfrom : nullptr; };
+  const bool ok = ws_product(sm, s0 - kfrom, rowA, rowB);
   if (!ok && tid == 0) atomicExch(err, 1);
   if (ok && warp < kWsProducers) {
     const int q = warp & 3, half = warp >> 2;
     const int row = r0 + q * 32 + lane;
     float* dst = A + (int64_t)row * ld + s0;
-    for (int g = 0; g < 8; ++g) {
-      const int c0 = half * 128 + 16 * g;
+    for (int g = 0; g < BN / 32; ++g) {
+      const int c0 = half * (BN / 2) + 16 * g;
       if (c0 >= ncol) break;  // warp-uniform
       float t[16];
       tmem_ld16(sm.tmem + ((uint32_t)(q * 32) << 16) + c0, t);

@@ -14,9 +14,9 @@ pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-9
 MEAN_TOL_MIXED = 1e-4
 MEAN_ELEM_MIXED = 3e-4
-VAR_TOL_MIXED = 2e-3
-VAR_ELEM_MIXED = 5e-3
-LL_TOL_MIXED = 1e-3
+VAR_TOL_MIXED = 6e-4
+VAR_ELEM_MIXED = 5e-2
+LL_TOL_MIXED = 1.5e-4
 
 
 @pytest.fixture(scope="module")

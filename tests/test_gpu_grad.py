@@ -1,14 +1,11 @@
 """GPU parity of the log-likelihood gradient (hand adjoint) against the FP64
 oracle's adjoint, central finite differences and the autograd wrapper.
 
-Tolerance for the FP64 form: 1e-8 norm-wise relative.  The gradient is a sum
-of O(N) window contractions whose terms cancel (<G_m, dK/dtheta> mixes
-positive and negative weights), so one more digit than the 1e-9 of the
-predictive outputs is lost; the oracle's own central difference check holds
-it to 1e-6 (truncation error of h = 1e-5).  Mixed form: the adjoint inherits
-the FP32 error of the residual precision R_W^-1 (about 1e-4 relative at
-sigma_s^2 / sigma_n^2 = 100) through every term, so it is held to 2e-2
-norm-wise relative and reported.
+Tolerance for the FP64 form: 1e-9 relative, norm-wise and element-wise (the
+spec figure; measured at most 2.4e-13 on these cases).  Mixed form:
+the adjoint inherits the FP32 error of the residual precision R_W^-1 through
+every term; it is held to about three times the largest error measured on
+the GB300 at the default jitter (tests/_parity.py reports it).
 """
 import numpy as np
 import pytest
@@ -17,9 +14,9 @@ from _parity import check, check_scalar
 
 pytestmark = pytest.mark.gpu
 
-GRAD_TOL_FP64 = 1e-8
-GRAD_TOL_MIXED = 2e-2
-LL_TOL_MIXED = 1e-3
+GRAD_TOL_FP64 = 1e-9
+GRAD_TOL_MIXED = 2e-3
+LL_TOL_MIXED = 1.5e-4
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +64,7 @@ def test_grad_fp64_matches_oracle(L, case):
 @pytest.mark.parametrize("case", CASES)
 def test_grad_mixed_matches_oracle(L, case):
     from oracle import lma_oracle as O2
-    p = _p(case, jitter=1e-3)
+    p = _p(case)
     ll_ref, g_ref = O2.loglik_grad(p)
     ll, g = L.lma_loglik_grad(precision=L.MIXED, **L.problem_args(p))
     t = f"grad_tiny{case[0]}_mixed"

@@ -1,20 +1,23 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances.  FP64 form: 1e-9 relative (norm-wise for mean and variance,
-absolute-over-|ref| for the log-likelihood).  Mixed form: predictive mean
-1e-4 norm-wise relative and RMSE within 0.1% of the oracle's; the variance
-and log-likelihood bounds below follow from FP32 rounding of R = K - Q, whose
-entries are O(sigma_s^2) while its smallest eigenvalue is O(sigma_n^2): a
-relative perturbation of ~1e-7 sigma_s^2 / sigma_n^2 in the residual
-precision (about 4e-5 at sigma_n = 0.05) reaches the variance and the
-log-likelihood nearly undamped.
+Every check is norm-wise and element-wise (tests/_parity.py; LMA_PARITY_REPORT
+records the measured errors).
 
-The mixed form's error also grows with sqrt(cond(Sigma_SS)): V = L_SS^-1
-Sigma_SD is formed in FP32 and its cancellation is of size |L_SS^-1|.  The
-tiny structural cases below pack up to 100 support points into a unit cube,
-which drives cond(Sigma_SS) to ~4e7 at the default jitter; for the mixed
-form they therefore use jitter 1e-3 (cond <= ~4e4).  The configuration-shaped
-cases (C1, C2 recipe) keep the default jitter 1e-6.
+Tolerances.  FP64 form: 1e-9 relative (the benchmark spec's figure), norm-wise and
+element-wise.  Mixed form: predictive mean 1e-4 norm-wise relative and RMSE
+within 0.1 % of the oracle's (spec figures); the other bounds are about
+three times the largest error measured on the GB300 over these cases at the
+default jitter 1e-6 (cond(Sigma_SS) up to 4e7):
+  mean element-wise (max |dmean| / max |mean|)   measured 7.5e-5 -> 3e-4
+  variance norm-wise                             measured 1.8e-4 -> 6e-4
+  variance element-wise (max |dvar| / var)       measured 1.5e-2 -> 5e-2
+  log-likelihood                                 measured 4.7e-5 -> 1.5e-4
+The element-wise variance bound is the loosest because the variance of a
+test point next to the training data is close to sigma_n^2 while the terms
+that produce it (sigma_s^2, |Vu|^2, the window solves' sum of squares) are
+O(sigma_s^2): the FP32 window solves (condition ~1e5 at sigma_s^2 /
+sigma_n^2 = 100 to 400) leave an absolute error of ~4e-5 on such a point,
+which is 1.5e-2 of a variance of 2.5e-3.
 """
 import numpy as np
 import pytest
@@ -25,9 +28,9 @@ pytestmark = pytest.mark.gpu
 
 MEAN_TOL_MIXED = 1e-4
 MEAN_ELEM_MIXED = 3e-4
-VAR_TOL_MIXED = 2e-3
-VAR_ELEM_MIXED = 5e-3
-LL_TOL_MIXED = 1e-3
+VAR_TOL_MIXED = 6e-4
+VAR_ELEM_MIXED = 5e-2
+LL_TOL_MIXED = 1.5e-4
 TOL_FP64 = 1e-9
 
 
@@ -96,13 +99,9 @@ def test_fp64_matches_oracle(L, case):
     check_scalar(t, "loglik", L.lma_model_loglik(model), f.loglik, TOL_FP64)
 
 
-MIXED_TINY_JITTER = 1e-3
-
-
 @pytest.mark.parametrize("case", TINY)
 def test_mixed_matches_oracle(L, case):
     p = _tiny(case)
-    p.jitter = MIXED_TINY_JITTER
     f, m, v = oracle(p)
     model, mean, var = run_gpu(L, p, L.MIXED)
     t = f"tiny{case[0]}_mixed"
@@ -114,7 +113,6 @@ def test_mixed_matches_oracle(L, case):
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
 def test_host_buffers_and_latent_variance(L, prec):
     p = _tiny(TINY[0])
-    p.jitter = MIXED_TINY_JITTER
     _, m, v = oracle(p, noisy=False)
     _, mean, var = run_gpu(L, p, getattr(L, prec), on_device=False, noisy=False)
     t = f"host_latent_{prec.lower()}"
@@ -196,7 +194,6 @@ def run_fit_predict(L, p, prec, B=None):
 @pytest.mark.parametrize("case", TINY)
 def test_mixed_fit_predict_matches_oracle(L, case):
     p = _tiny(case)
-    p.jitter = MIXED_TINY_JITTER
     f, m, v = oracle(p)
     model, mean, var = run_fit_predict(L, p, L.MIXED)
     t = f"tiny{case[0]}_fit_predict_mixed"
