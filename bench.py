@@ -646,7 +646,11 @@ def main():
                 llg, gr = L.lma_loglik_grad(qd["X"], qd["y"], S=qd["S"], **qkw)
                 tms.append(1e3 * (time.perf_counter() - t0))
             gms = statistics.mean(tms)
+            L.profile_start("k_")
+            L.lma_loglik_grad(qd["X"], qd["y"], S=qd["S"], **qkw)
+            gprof = L.profile_stop()
             leg = {"workload": workload_config(q, q.B)["workload"], "ms_per_call": gms,
+                   "kernel_ms_one_call": {k: round(v[0], 3) for k, v in sorted(gprof.items(), key=lambda kv: -kv[1][0])},
                    "train_points_per_s": q.N / (gms / 1e3), "fit_gflop": fit_flops(q, q.B) / 1e9,
                    "timing": "host wall clock around lma_loglik_grad (it synchronises and returns host values)"}
             gg = golden(q, q.B)

@@ -83,8 +83,9 @@ __device__ __forceinline__ Smem& smem_of(unsigned char* raw) {
 }
 inline size_t smem_bytes() { return sizeof(Smem) + 1024; }
 
-// Persistent loop over output tiles t = blockIdx.x, blockIdx.x + gridDim.x,
-// ... < ntiles.  Tile t accumulates, over its chunks c < chunks(t), the
+// Persistent loop over output tiles: the CTA's k-th tile is order(k) (a
+// negative value ends the loop; every role walks the same sequence).  Tile t
+// accumulates, over its chunks c < chunks(t), the
 // product of the 128 x 64 boxes at (x, ya) of A and (x, yb) of B with
 // (x, ya, yb) = at(coords(t), c); plane q of an operand is the box at row
 // offset q * (plane rows) of its tensor map.  Workers drain the two
@@ -92,9 +93,9 @@ inline size_t smem_bytes() { return sizeof(Smem) + 1024; }
 // row 32 (w mod 4) + lane and columns 32 (w / 4) + j in acc[j].  Every wait
 // has an iteration limit; on a timeout all roles stop, no copy is left
 // landing, and false is returned in every thread.
-template <class Chunks, class Coords, class At, class After>
+template <class Order, class Chunks, class Coords, class At, class After>
 __device__ bool persistent(Smem& sm, const CUtensorMap* amap, int arows, const CUtensorMap* bmap, int brows,
-                           int ntiles, Chunks chunks, Coords coords, At at, After after) {
+                           Order order, Chunks chunks, Coords coords, At at, After after) {
   using namespace tc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &sm.abort;
@@ -103,7 +104,9 @@ __device__ bool persistent(Smem& sm, const CUtensorMap* amap, int arows, const C
     const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
     int G = 0;  // chunks drained so far by this CTA
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int k = 0;; ++k) {
+      const int t = order(k);
+      if (t < 0) break;
       float acc[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0.f;
@@ -140,7 +143,9 @@ __device__ bool persistent(Smem& sm, const CUtensorMap* amap, int arows, const C
     const uint32_t idesc = idesc_bf16(128, 128);
     int C = 0;  // chunks issued so far by this CTA
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int k = 0; ok; ++k) {
+      const int t = order(k);
+      if (t < 0) break;
       const int nchunk = chunks(t);
       for (int c = 0; c < nchunk; ++c, ++C) {
         const int s = C % NST, a = C & 1;
@@ -188,7 +193,9 @@ __device__ bool persistent(Smem& sm, const CUtensorMap* amap, int arows, const C
     // TMA producer: the whole warp runs the loops, lane 0 waits and issues
     int C = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int k = 0; ok; ++k) {
+      const int t = order(k);
+      if (t < 0) break;
       const int4 base = coords(t);
       const int nchunk = chunks(t);
       for (int c = 0; c < nchunk; ++c, ++C) {
@@ -389,7 +396,23 @@ __global__ void __launch_bounds__(bf6::NTHR, 1) k_proj_tc(const __grid_constant_
         if (c0 + j < s) dst[j] = acc[j];
     }
   };
-  const bool ok = bf6::persistent(sm, &amap, arows, &bmap, brows, ntiles, chunks, coords, at, after);
+  // Tile order: with an even number of column tiles, the CTA's tiles come in
+  // pairs (column tile j, column tile nct - 1 - j) of one row block, which
+  // have the same number of K chunks together (the product is triangular),
+  // so all CTAs advance at the same rate and those working at the same time
+  // share a few row blocks' A boxes in L2.
+  auto order = [&](int k) -> int {
+    if (nct & 1) {
+      const int64_t t = blockIdx.x + (int64_t)k * gridDim.x;
+      return t < ntiles ? (int)t : -1;
+    }
+    const int P = nct / 2;
+    const int64_t u = blockIdx.x + (int64_t)(k >> 1) * gridDim.x;
+    if (u >= nrt * P) return -1;
+    const int pt = (int)(u / P), j = (int)(u % P);
+    return pt * nct + ((k & 1) ? nct - 1 - j : j);
+  };
+  const bool ok = bf6::persistent(sm, &amap, arows, &bmap, brows, order, chunks, coords, at, after);
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   bf6::teardown(sm);
 }

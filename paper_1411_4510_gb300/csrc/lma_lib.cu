@@ -197,8 +197,9 @@ static void proj_tc(cudaStream_t st, const char* name, const uint16_t* Ap, int64
                     int brows, int s, int ldk, float* out, int64_t ldo, int* err) {
   if (nrows == 0) return;
   const CUtensorMap am = bf16_tensor_map(Ap, 3 * nrows, ldk), bm = bf16_tensor_map(Bp, 3 * (int64_t)brows, ldk);
-  const int64_t ntiles = ((nrows + 127) / 128) * ((s + 127) / 128);
-  launch(name, k_proj_tc, persistent_grid((size_t)ntiles), bf6::NTHR, bf6::smem_bytes(), st, am, (int)nrows, bm,
+  const int64_t nct = (s + 127) / 128, ntiles = ((nrows + 127) / 128) * nct;
+  const int64_t nitems = (nct % 2) ? ntiles : ntiles / 2;  // tiles come in pairs when nct is even (k_proj_tc)
+  launch(name, k_proj_tc, persistent_grid((size_t)nitems), bf6::NTHR, bf6::smem_bytes(), st, am, (int)nrows, bm,
          brows, nrows, s, out, ldo, err);
 }
 
@@ -282,6 +283,7 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_pred_rhs_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
+    cudaFuncSetAttribute(k_pred_accum_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<256>());
     cudaFuncSetAttribute(k_chol_wide<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<128>());
     cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
@@ -961,15 +963,50 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     }
     T* h = tmp.alloc<T>(U * s);
     if (mc.prec == LMA_MIXED && sizeof(T) == 4 && use_tensor_cores()) {
-      std::vector<int4> it_a;
-      for (const int4& t : tb)
-        for (int ut = 0; ut < (t.w + 127) / 128; ++ut)
-          for (int kt = 0; kt < (s + RB - 1) / RB; ++kt) it_a.push_back(make_int4(t.x, t.y, ut, kt));
-      int4* iat = tmp.alloc<int4>(it_a.size());
-      stage_copy(iat, it_a.data(), sizeof(int4) * it_a.size(), st);
-      launch("k_pred_accum_tc", k_pred_accum_tc, (unsigned)it_a.size(), comp_threads<RB>(), tc_resid_smem(), st, pd,
-             (const int4*)iat, mc.wins_d, (const float*)wbuf, (const float*)Pbuf, (const float*)Vu, (int)s, (float*)h,
-             perr);
+      // per window: its pairs (n, m) in increasing n, their partial rows, items
+      const int64_t nwin = (int64_t)mc.wins.size();
+      std::vector<std::vector<int>> byw((size_t)nwin);
+      for (size_t pi = 0; pi < pairs.size(); ++pi) byw[pairs[pi].win].push_back((int)pi);
+      std::vector<int> wp;
+      std::vector<int4> it_w;
+      std::vector<int64_t> wrow, prow(pairs.size(), 0);
+      int64_t hrows = 0;
+      for (int64_t m = 0; m < nwin; ++m) {
+        if (byw[m].empty()) continue;
+        const int off = (int)wp.size();
+        int rows = 0;
+        for (int pi : byw[m]) {
+          wp.push_back(pi);
+          prow[pi] = hrows + rows;
+          rows += pairs[pi].nu;
+        }
+        for (int ut = 0; ut < (rows + 127) / 128; ++ut)
+          for (int kt = 0; kt < (s + RB - 1) / RB; ++kt) {
+            it_w.push_back(make_int4(off, (int)byw[m].size(), ut, kt));
+            wrow.push_back(hrows);
+          }
+        hrows += rows;
+      }
+      int* wpd = tmp.alloc<int>(wp.size());
+      int4* iwd = tmp.alloc<int4>(it_w.size());
+      int64_t* wrd = tmp.alloc<int64_t>(wrow.size());
+      int64_t* prd = tmp.alloc<int64_t>(prow.size());
+      int4* tbd = tmp.alloc<int4>(tb.size());
+      stage_copy(wpd, wp.data(), sizeof(int) * wp.size(), st);
+      stage_copy(iwd, it_w.data(), sizeof(int4) * it_w.size(), st);
+      stage_copy(wrd, wrow.data(), sizeof(int64_t) * wrow.size(), st);
+      stage_copy(prd, prow.data(), sizeof(int64_t) * prow.size(), st);
+      stage_copy(tbd, tb.data(), sizeof(int4) * tb.size(), st);
+      float* hw = tmp.alloc<float>((size_t)hrows * s);
+      if (!it_w.empty())
+        launch("k_pred_accum_tc", k_pred_accum_win, (unsigned)it_w.size(), comp_threads<RB>(), tc_resid_smem(), st, pd,
+               (const int*)wpd, (const int4*)iwd, (const int64_t*)wrd, mc.wins_d, (const float*)wbuf,
+               (const float*)Pbuf, (int)s, hw, perr);
+      int maxnu = 1;
+      for (const int4& t : tb) maxnu = std::max(maxnu, t.w);
+      if (!tb.empty())
+        launch("k_pred_hsum", k_pred_hsum, dim3(nblk((int64_t)maxnu * s), (unsigned)tb.size()), NT, 0, st,
+               (const int4*)tbd, (const int64_t*)prd, (const float*)hw, (const float*)Vu, (int)s, (float*)h);
     } else {
       launch("k_pred_accum", k_pred_accum<T>, (unsigned)it_acc.size(), NT, 0, st, pd, iad, mc.wins_d, wbuf, Pbuf, Vu,
              (int)s, h);

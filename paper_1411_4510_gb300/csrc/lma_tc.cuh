@@ -301,7 +301,7 @@ __device__ __forceinline__ bool tc_drain(TcSmem<BN>& sm, TcPipe& p, int s) {
 // a register ring (DEPTH x 24 KB per CTA for BN = 64), so with two CTAs per
 // SM several chunks are in flight while the current one is split into TF32
 // hi/lo, stored to the swizzled stage and multiplied.
-template <int BN, int DEPTH = 3, class RA, class RB>
+template <int BN, int DEPTH = 3, bool CGB = false, class RA, class RB>
 __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB, int nacc = 1) {
   constexpr int NA = 128 * 8 / 256;          // float4 of A per thread per chunk
   constexpr int NB = (BN * 8 + 255) / 256;   // float4 of B per thread per chunk
@@ -321,7 +321,10 @@ __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA
     for (int j = 0; j < NB; ++j) {
       const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
       const float* src = (i < BN * 8) ? rowB(row) : nullptr;
-      xb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (CGB)  // B written by another CTA of this launch: read it from L2
+        xb[j] = src ? __ldcg(reinterpret_cast<const float4*>(src + k0 + c4 * 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      else
+        xb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
 #pragma unroll
@@ -1523,6 +1526,106 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_tc(const P
       if (kg + j < s) h[row * s + kg + j] = (hi[j] + lo[j]) - Vu[row * s + kg + j];
   }
   comp_teardown(sm);
+}
+
+// The h accumulation per window (mixed form): the test rows that use window m
+// (the pairs (n, m), n = m .. m + B) share its extra rows X_{1+k} as the B
+// operand, so one 128-row tile covers the test points of several blocks.
+// Item x = first index into wp (the window's pairs, increasing n), y = pair
+// count, z = 128-row tile of the window's test rows, w = RB-wide s tile; the
+// partial hw[(prow + r) * s + k] = sum over the pair's kept columns of
+// P[r][c] X_{1+k}[c] (block columns [nB, n) for every row, the blanket
+// columns [0, nB) only for the rows of block m itself), where prow is the
+// window's first partial row (wrow[x]).  k_pred_hsum adds each test point's
+// partials in window order.
+__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_win(const Pair* __restrict__ pairs,
+                                                                        const int* __restrict__ wp,
+                                                                        const int4* __restrict__ items,
+                                                                        const int64_t* __restrict__ wrow,
+                                                                        const Win* __restrict__ wins,
+                                                                        const float* __restrict__ buf,
+                                                                        const float* __restrict__ P, int s,
+                                                                        float* __restrict__ hw, int* __restrict__ err) {
+  using namespace tc;
+  const int4 it = items[blockIdx.x];
+  const int u0 = it.z * 128, k0 = it.w * RB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CompSmem<RB>& sm = comp_smem<RB>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  comp_setup(sm);
+  const Pair p0 = pairs[wp[it.x]];
+  const Win w = wins[p0.win];
+  const float* E = buf + w.base + (int64_t)w.npad * w.npad;
+  const int64_t ld = w.npad;
+  // row r of the tile -> pointer to its P row (nullptr past the window's test
+  // rows) and whether it is a row of block m itself (kept blanket columns)
+  __shared__ const float* rowp[128];
+  __shared__ int rowown[128];
+  __shared__ int s_rows;
+  if (tid < 128) {
+    int rr = u0 + tid;
+    const float* ptr = nullptr;
+    int own = 0;
+    for (int j = 0; j < it.y; ++j) {
+      const Pair pr = pairs[wp[it.x + j]];
+      if (rr < pr.nu) {
+        own = pr.c0 == 0;
+        ptr = P + pr.pbase + (int64_t)rr * ld;
+        break;
+      }
+      rr -= pr.nu;
+    }
+    rowp[tid] = ptr;
+    rowown[tid] = own;
+  }
+  if (tid == 0) {
+    int rows = 0;
+    for (int j = 0; j < it.y; ++j) rows += pairs[wp[it.x + j]].nu;
+    s_rows = rows;
+  }
+  __syncthreads();
+  auto rowB = [&](int c) -> const float* { return (k0 + c < s) ? E + (int64_t)(1 + k0 + c) * ld : nullptr; };
+  CompState cs;
+  float hi[32], lo[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
+  auto rowAll = [&](int r) -> const float* { return rowp[r]; };
+  bool ok = comp_product<RB, true>(sm, cs, w.nB, w.n, rowAll, rowB, hi, lo);
+  if (ok && w.nB > 0) {
+    auto rowOwn = [&](int r) -> const float* { return rowown[r] ? rowp[r] : nullptr; };
+    ok = comp_product<RB, true>(sm, cs, 0, w.nB, rowOwn, rowB, hi, lo);
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int rows = s_rows;
+  const int q = warp & 3, half = warp >> 2;
+  const int rr = u0 + q * 32 + lane;
+  const int kg = k0 + half * 32;
+  if (ok && warp < RB / 8 && rr < rows) {
+    float* dst = hw + (wrow[it.x] + rr) * (int64_t)s;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (kg + j < s) dst[kg + j] = hi[j] + lo[j];
+  }
+  comp_teardown(sm);
+}
+
+// h[u][k] = sum over the pairs (n, m) of u's test block n, in window order, of
+// hw[(prow of the pair + u - u0) * s + k] (added in FP64), minus Vu[u][k].
+// Grid: y = test block (tb: x = its first pair, y = pair count, z = first test
+// row, w = rows), x covers the block's rows x s elements; prow[pair] = the
+// pair's first partial row.
+__global__ void k_pred_hsum(const int4* __restrict__ tb, const int64_t* __restrict__ prow,
+                            const float* __restrict__ hw, const float* __restrict__ Vu, int s,
+                            float* __restrict__ h) {
+  const int4 t = tb[blockIdx.y];
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)t.w * s) return;
+  const int64_t r = e / s;
+  const int k = (int)(e - r * s);
+  double acc = 0.0;
+  for (int j = 0; j < t.y; ++j) acc += (double)hw[(prow[t.x + j] + r) * s + k];
+  const int64_t o = (t.z + r) * (int64_t)s + k;
+  h[o] = (float)(acc - (double)Vu[o]);
 }
 
 // Prediction right-hand sides on the tensor cores, one persistent CTA per SM

@@ -22,6 +22,10 @@ Cases (full configuration sizes):
                 the oracle's hand-adjoint gradient and central differences
                 (h = 1e-4 in log space) of the oracle log-likelihood for
                 three components.
+  learn         maximum-likelihood hyperparameters (Sec. 5) of a small
+                C2-shaped problem (N=1,200, |S|=40, 8 blocks, B=1): L-BFGS-B
+                (scipy) on the oracle's log-likelihood and hand adjoint, from
+                a start away from the generating values.
 
 Usage: python tests/golden/make_golden.py c2_b1 c2_b2 c3 c4 c5
 (about 2.5 hours on 8 cores, C4 taking most of it).
@@ -124,12 +128,40 @@ def grad_case() -> dict:
             "fd_h": h, "fd": fd, "oracle_seconds": {"loglik_grad": t_grad}}
 
 
+def learn_case() -> dict:
+    from scipy.optimize import minimize
+    p = make_problem("C2", N=1200, M=8, s=40, U=0, B=1)
+    d = p.d
+    gen = np.concatenate([p.log_ell, [p.log_sigma_s, p.log_sigma_n]])
+    th0 = gen + np.concatenate([np.full(d, 0.4), [-0.3, 0.5]])
+    evals = []
+
+    def at(th):
+        return dataclasses.replace(p, log_ell=np.array(th[:d]), log_sigma_s=float(th[d]),
+                                   log_sigma_n=float(th[d + 1]))
+
+    def objective(th):
+        ll, g = O2.loglik_grad(at(th))
+        evals.append(ll)
+        return -ll / p.N, -np.asarray(g) / p.N
+
+    t0 = time.time()
+    res = minimize(objective, th0, jac=True, method="L-BFGS-B", options=dict(maxiter=200, gtol=1e-7))
+    ll, g = O2.loglik_grad(at(res.x))
+    return {"case": "learning, C2 recipe N=1200 M=8 s=40 B=1", "fingerprints": fingerprints(p),
+            "theta0": th0.tolist(), "theta_generating": gen.tolist(), "theta": np.asarray(res.x).tolist(),
+            "loglik": ll, "grad": np.asarray(g).tolist(), "loglik0": evals[0], "iterations": int(res.nit),
+            "evaluations": int(res.nfev), "converged": bool(res.success), "optimizer": "scipy L-BFGS-B, "
+            "objective -loglik/N, gtol 1e-7", "oracle_seconds": time.time() - t0}
+
+
 CASES = {
     "c2_b1": lambda: pred_case("C2", 1, True),
     "c2_b2": lambda: pred_case("C2", 2, True),
     "c3": lambda: pred_case("C3", 2, False),
     "c4": lambda: pred_case("C4", 1, False),
     "c5": grad_case,
+    "learn": learn_case,
 }
 
 

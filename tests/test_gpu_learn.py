@@ -2,7 +2,9 @@
 C2-shaped synthetic problem: started away from the generating values, it
 climbs above the starting log-likelihood, ends at least as high as the
 generating point, and recovers the generating noise level and length-scale;
-the mixed and FP64 forms agree."""
+the mixed and FP64 forms agree.  On a smaller problem it also reaches the
+optimum that the same optimiser finds on the FP64 oracle's log-likelihood
+and adjoint from the same start (tests/golden/learn.json)."""
 import numpy as np
 import pytest
 
@@ -55,3 +57,24 @@ def test_mixed_and_fp64_agree(runs):
     a, b = out["FP64"][0], out["MIXED"][0]
     assert np.max(np.abs(a.theta - b.theta)) < 0.05
     assert abs(a.loglik - b.loglik) < 1e-3 * abs(a.loglik)
+
+
+@pytest.mark.parametrize("prec,tol_theta,tol_ll", [("FP64", 1e-3, 1e-7), ("MIXED", 2e-2, 1e-4)])
+def test_learning_reaches_oracle_optimum(L, prec, tol_theta, tol_ll):
+    import json
+    import os
+    from paper_1411_4510_gb300 import learn
+    from workloads import make_problem
+    from _parity import report
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "learn.json")))
+    p = make_problem("C2", N=1200, M=8, s=40, U=0, B=1)
+    assert g["fingerprints"]["N"] == p.N and g["fingerprints"]["s"] == p.s
+    args = L.problem_args(p)
+    r = learn.learn_hyperparameters(args, theta0=np.asarray(g["theta0"]), precision=getattr(L, prec), max_iter=200,
+                                    gtol=1e-7)
+    dth = float(np.max(np.abs(r.theta - np.asarray(g["theta"]))))
+    dll = abs(r.loglik - g["loglik"]) / abs(g["loglik"])
+    report(f"learn_{prec.lower()}", "theta", "max_abs", dth, tol_theta)
+    report(f"learn_{prec.lower()}", "loglik", "scalar", dll, tol_ll)
+    assert dth <= tol_theta, (r.theta, g["theta"])
+    assert dll <= tol_ll

@@ -1,11 +1,30 @@
-"""GPU side of the partitioned fit: two shards run one after the other on
-one GPU (lma_fit_local on each sub-problem, the Grams summed on the device,
-lma_model_set_global on each) must reproduce the whole fit's log-likelihood
-and, shard by shard, its predictions of the test blocks each shard owns."""
+"""GPU side of the partitioned fit: two or three shards run one after the
+other on one GPU (lma_fit_local on each sub-problem, the Grams summed on the
+device, lma_model_set_global on each) must reproduce the whole fit's
+log-likelihood and, shard by shard, its predictions of the test blocks each
+shard owns; both are also checked directly against the FP64 oracle (Remark
+1: the machines' local summaries add up to Definition 2's global summary),
+with the FP64 bound 1e-9 and the mixed bounds of test_gpu_parity.py."""
 import numpy as np
 import pytest
 
+from _parity import check, check_scalar
+
 pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def _oracle(B):
+    """FP64 oracle fit and prediction of the shard tests' problem (cached per B)."""
+    if B not in _ORACLE:
+        from oracle import lma_oracle as O2
+        from workloads import make_problem
+        p = make_problem("C2", N=3200, M=16, s=100, U=400, B=B)
+        f = O2.fit(p)
+        m, v = O2.predict(f)
+        _ORACLE[B] = (f.loglik, m, v)
+    return _ORACLE[B]
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +66,16 @@ def test_sharded_equals_whole(L, prec, tol_ll, tol_mean, B, world):
         mean, var = L.lma_predict(m, p.XU[u0:u1], tp)
         assert np.linalg.norm(mean - mean_w[u0:u1]) <= tol_mean * np.linalg.norm(mean_w[u0:u1])
         assert np.linalg.norm(var - var_w[u0:u1]) <= 10 * tol_mean * np.linalg.norm(var_w[u0:u1])
+        ll_o, m_o, v_o = _oracle(B)
+        t = f"shard_b{B}_w{world}_r{sh.rank}_{prec.lower()}"
+        if prec == "FP64":
+            check_scalar(t, "loglik", ll, ll_o, 1e-9)
+            check(t, "mean", mean, m_o[u0:u1], 1e-9, 1e-9)
+            check(t, "var", var, v_o[u0:u1], 1e-9, 1e-9, positive=True)
+        else:
+            check_scalar(t, "loglik", ll, ll_o, 1.5e-4)
+            check(t, "mean", mean, m_o[u0:u1], 1e-4, 3e-4)
+            check(t, "var", var, v_o[u0:u1], 6e-4, 5e-2, positive=True)
 
 
 def test_fit_local_rejects_bad_ranges(L):
