@@ -75,6 +75,21 @@ def fit_flops(p, B):
     return f
 
 
+def grad_flops(p, B):
+    """Algorithmic flops of lma_loglik_grad beyond the fit it repeats: per
+    window W (n = |W|, b = |D_m|, r = 2(s+1) + b right-hand sides) the
+    backward solve r n^2, the matrix G = 1/2 (Phi Phi^T - ...) r n^2 (lower
+    half), G Vt_W 2 n^2 s; over the N points Vt-bar = ... (s^2, triangular) and
+    K_DS-bar = Vt-bar L_SS^-1 (s^2) and their contraction with dK/dtheta
+    (2 N s (d + 2)); L_SS-bar and the Cholesky adjoint 4 s^3 (FP64)."""
+    s, N, d = p.s, p.N, p.d
+    f = 2.0 * N * s * s + 2.0 * N * s * (d + 2) + 4.0 * s ** 3
+    for n, b, nb in window_sizes(p.block_ptr, B):
+        r = 2 * (s + 1) + b
+        f += r * n * n + r * n * n + 2.0 * n * n * s
+    return f
+
+
 def predict_flops(p, B):
     """2 U s^2 (test projection and variance term) + per (test block, window)
     pair: the right-hand sides 2 n s, their solve n^2, the h accumulation 2 kept s."""
@@ -567,6 +582,7 @@ def main():
                 roof["traffic"] = t["bytes"]
                 roof["traffic_note"] = t["note"]
     out["roofline"] = roof
+    out["autotune"] = [{"key": k, "choice": c, "candidates_ms": m} for _, k, c, m in L.lma_autotune_report()]
     out["roofline_by_kernel"] = {k: {kk: vv for kk, vv in roofline_of(k, work[k], v[0], v[1], peaks).items()
                                      if kk in ("bound", "achieved", "peak", "frac", "avg_launch_ms")}
                                  for k, v in (prof_all or {}).items() if k in work and v[0] > 0}
@@ -649,7 +665,11 @@ def main():
             L.profile_start("k_")
             L.lma_loglik_grad(qd["X"], qd["y"], S=qd["S"], **qkw)
             gprof = L.profile_stop()
+            gfl = fit_flops(q, q.B) + grad_flops(q, q.B)
             leg = {"workload": workload_config(q, q.B)["workload"], "ms_per_call": gms,
+                   "tflops": gfl / (gms / 1e3) / 1e12, "algorithmic_gflop": gfl / 1e9,
+                   "flop_note": "fit (fit_flops) + adjoint (grad_flops); the adjoint runs on the CUDA cores in FP32 "
+                                "(FP32 SIMT peak 80.5 TFLOP/s at 2070 MHz) and FP64",
                    "kernel_ms_one_call": {k: round(v[0], 3) for k, v in sorted(gprof.items(), key=lambda kv: -kv[1][0])},
                    "train_points_per_s": q.N / (gms / 1e3), "fit_gflop": fit_flops(q, q.B) / 1e9,
                    "timing": "host wall clock around lma_loglik_grad (it synchronises and returns host values)"}

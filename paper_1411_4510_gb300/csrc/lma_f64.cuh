@@ -149,5 +149,80 @@ __global__ void __launch_bounds__(NTH) k_f64_panel(double* __restrict__ buf, int
   diag_factor<double, TS>(Tj, A, ld, dinv + (int64_t)(kp + 1) * TS * TS, info, c0);
 }
 
+// Two-phase variant (two launches per column panel, no repeated solves):
+// k_f64_solve2 solves every tile of panel kp below the diagonal in place,
+// L_ik = T_ik inv(L_kk)^T (identity-row tiles that are still zero are
+// skipped); k_f64_update2 then applies A_ij -= L_ik L_jk^T to every trailing
+// tile (kp < j <= i < npan, and the appended-row tiles i >= npan, kp < j <
+// npan) from the solved tiles, and its CTA 0 (tile (kp + 1, kp + 1))
+// factorises that diagonal tile.  Each trailing tile thus does one product
+// instead of two solves and a product, which pays at large orders.
+__global__ void __launch_bounds__(NTH) k_f64_solve2(double* __restrict__ buf, int64_t ld, int rows, int npan, int kp,
+                                                    int nid, const double* __restrict__ dinv) {
+  grid_dep_wait();
+  grid_dep_launch();
+  const int i = kp + 1 + blockIdx.x;
+  if (zero_identity_tile(i, npan, kp, nid)) return;
+  __shared__ double Ti[TS][TS + 1], X[TS][TS + 1], Li[TS][TS + 1];
+  load_tile(Ti, buf, ld, i * TS, kp * TS, rows);
+  load_tile(X, dinv + (int64_t)kp * TS * TS, TS, 0, 0, TS);
+  __syncthreads();
+  solve_tile(Li, Ti, X);
+  __syncthreads();
+  for (int q = threadIdx.x; q < TS * TS; q += NTH) {
+    const int r = q / TS, c = q % TS;
+    if (i * TS + r < rows) buf[(int64_t)(i * TS + r) * ld + kp * TS + c] = Li[r][c];
+  }
+}
+
+__global__ void __launch_bounds__(NTH) k_f64_update2(double* __restrict__ buf, int64_t ld, int rows, int npan,
+                                                     int kp, int nid, double* __restrict__ dinv,
+                                                     int* __restrict__ info) {
+  grid_dep_wait();
+  grid_dep_launch();
+  const int napp = (rows + TS - 1) / TS - npan;
+  const int m = npan - kp - 1;
+  const int t1 = m * (m + 1) / 2;
+  const int b = blockIdx.x;
+  int i, j;
+  if (b < t1) {
+    int I = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
+    while (I * (I + 1) / 2 > b) --I;
+    while ((I + 1) * (I + 2) / 2 <= b) ++I;
+    i = kp + 1 + I;
+    j = kp + 1 + (b - I * (I + 1) / 2);
+  } else {
+    const int q = b - t1;
+    if (q >= napp * m) return;
+    i = npan + q / m;
+    j = kp + 1 + q % m;
+  }
+  if (zero_identity_tile(i, npan, kp, nid)) return;
+  __shared__ double Li[TS][TS + 1], Lj[TS][TS + 1], Tj[TS][TS + 1];
+  const int r0 = i * TS, c0 = j * TS, k0 = kp * TS;
+  load_tile(Li, buf, ld, r0, k0, rows);
+  if (i != j) load_tile(Lj, buf, ld, c0, k0, rows);
+  __syncthreads();
+  const double(*LJ)[TS + 1] = (i != j) ? Lj : Li;
+  const int r = threadIdx.x >> 2, p = threadIdx.x & 3;
+  double acc[TS / 4] = {};
+#pragma unroll
+  for (int k = 0; k < TS; ++k) {
+    const double a = Li[r][k];
+#pragma unroll
+    for (int qq = 0; qq < TS / 4; ++qq) acc[qq] = fma(a, LJ[p + 4 * qq][k], acc[qq]);
+  }
+  double* A = buf + (int64_t)r0 * ld + c0;
+  if (b != 0) {
+    if (r0 + r < rows)
+#pragma unroll
+      for (int qq = 0; qq < TS / 4; ++qq) A[(int64_t)r * ld + p + 4 * qq] -= acc[qq];
+    return;
+  }
+#pragma unroll
+  for (int qq = 0; qq < TS / 4; ++qq) Tj[r][p + 4 * qq] = A[(int64_t)r * ld + p + 4 * qq] - acc[qq];
+  diag_factor<double, TS>(Tj, A, ld, dinv + (int64_t)(kp + 1) * TS * TS, info, c0);
+}
+
 }  // namespace f64
 }  // namespace lma

@@ -363,13 +363,29 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
 // Right-looking factorisation of one FP64 matrix on 16 x 16 tiles (see
 // lma_f64.cuh).  nid: number of leading appended rows that are identity rows
 // (0 = none).  wd is unused (kept for the window form's signature).
+// variant 0: one launch per panel (trailing tiles solve their panel tiles
+// themselves; fewest launches, for small orders where the chain is
+// latency-bound); variant 1: a solve launch and an update launch per panel
+// (each panel tile solved once; for large orders where the FP64 work counts).
 static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info,
-                               int nid = 0) {
+                               int nid = 0, int variant = 0) {
   (void)wd;
   using namespace f64;
   const int npan = w.npad / TS, nrt = (w.rows + TS - 1) / TS;
   const int64_t ld = w.npad;
   launch_pdl("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
+  if (variant == 1) {
+    for (int kp = 0; kp < npan; ++kp) {
+      if (nrt - kp - 1 > 0)
+        launch_pdl("k_f64_solve2", k_f64_solve2, (unsigned)(nrt - kp - 1), NTH, 0, st, buf, ld, w.rows, npan, kp,
+                   nid, (const double*)dv);
+      const int m = npan - kp - 1;
+      if (m > 0)
+        launch_pdl("k_f64_panel", k_f64_update2, (unsigned)(m * (m + 1) / 2 + (nrt - npan) * m), NTH, 0, st, buf,
+                   ld, w.rows, npan, kp, nid, dv, info);
+    }
+    return;
+  }
   for (int kp = 0; kp <= npan; ++kp) {
     const int m = npan - kp - 1;
     const int trail = m > 0 ? m * (m + 1) / 2 + (nrt - npan) * m : 0;
@@ -382,7 +398,10 @@ static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* b
 
 // Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
 // `extra` extra rows); the first failing pivot (+1) goes to *info (device),
-// which the caller checks after its next synchronisation.
+// which the caller checks after its next synchronisation.  The launch
+// variant is a tuning site: both are timed on a scratch copy of the matrix
+// (the factorisation works in place), the model's default being the
+// two-launch form from order 1,024 on.
 static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra, int nid,
                                int* info) {
   Win w{};
@@ -390,7 +409,22 @@ static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
   w.npad = npad;
   w.rows = npad + extra;
   double* dv = tmp.alloc<double>((size_t)npad * TB);
-  right_looking_fp64(st, w, nullptr, buf, dv, info, nid);
+  const size_t bytes = (size_t)w.rows * npad * sizeof(double);
+  double* scratch = nullptr;
+  int* sinfo = nullptr;
+  auto run = [&](int v) {
+    if (!scratch) {
+      scratch = tmp.alloc<double>((size_t)w.rows * npad);
+      sinfo = tmp.alloc<int>(1);
+    }
+    LMA_CK(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, st));
+    LMA_CK(cudaMemsetAsync(sinfo, 0, sizeof(int), st));
+    right_looking_fp64(st, w, nullptr, scratch, dv, sinfo, nid, v);
+  };
+  const std::string key = "fp64 factor n=" + std::to_string(n) + " rows=" + std::to_string(w.rows) +
+                          " identity=" + std::to_string(nid);
+  const int v = tune::pick(key, {0, 1}, n >= 1024 ? 1 : 0, st, run);
+  right_looking_fp64(st, w, nullptr, buf, dv, info, nid, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -804,9 +838,27 @@ void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
   project<float>(mc, (const float*)xu, U, Vu, tmp, st, mc.flags + 2);
   ft.xu = xu;
   ft.Vu = Vu;
+  // One item row-range per window: its appended test rows are the test points
+  // of blocks m .. m + B, consecutive both in the test order and in the
+  // window buffer, so a 128-row tile covers the points of several blocks
+  // (the right-hand sides R_{W_m u} of every pair (n, m) of the window).
   std::vector<Pair> pairs;
-  std::vector<int4> tb;
-  make_pairs(mc.wins, mc.w0, mc.M, mc.B, s, ft.tptr, true, pairs, tb, nullptr);
+  const int64_t Mw = (int64_t)mc.wins.size();
+  for (int64_t m = 0; m < Mw; ++m) {
+    const Win& w = mc.wins[m];
+    const int64_t last = std::min<int64_t>(m + mc.B, mc.M - 1);
+    const int64_t u0 = ft.tptr[m], u1 = ft.tptr[last + 1];
+    if (u1 <= u0) continue;
+    Pair p{};
+    p.pbase = w.base + (int64_t)(w.npad + s + 1) * w.npad;
+    p.win = (int)m;
+    p.u0 = (int)u0;
+    p.nu = (int)(u1 - u0);
+    p.c0 = 0;
+    p.c1 = w.n;
+    p.n = (int)m;
+    pairs.push_back(p);
+  }
   if (pairs.empty()) return;
   Pair* pd = tmp.alloc<Pair>(pairs.size());
   stage_copy(pd, pairs.data(), sizeof(Pair) * pairs.size(), st);

@@ -498,6 +498,7 @@ namespace tc {
 // A kind::tf32 MMA instruction occupies the tensor pipe for the same time
 // whatever its N up to 256, so wide tiles (BN = 256) are the efficient ones.
 constexpr int kWsProducers = 8;
+constexpr int kWsDepth = 2;  // K chunks each producer keeps in flight in registers (16 producers with 3 in flight ran 1.4x slower)
 constexpr int kWsThreads = 32 * (kWsProducers + 1);
 
 template <int NS, int BN>
@@ -548,33 +549,35 @@ __device__ __forceinline__ void ws_teardown(WsSmem<NS, BN>& sm) {
 // when a wait timed out.  On return every MMA has completed.
 template <int NS, int BN, class RA, class RB>
 __device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
-  constexpr int NA = 128 * 8 / 256, NB = BN * 8 / 256;  // float4 per producer thread per chunk
+  constexpr int PT = 32 * kWsProducers, D = kWsDepth;
+  constexpr int NA = 128 * 8 / PT, NB = BN * 8 / PT;  // float4 per producer thread per chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nchunk = K / 32;
   volatile int* abort_flag = &sm.abort;
   if (warp < kWsProducers) {
-    float4 ra[2][NA], rb[2][NB];
+    float4 ra[D][NA], rb[D][NB];
     auto load = [&](int c, float4 (&xa)[NA], float4 (&xb)[NB]) {
       const int k0 = c * 32;
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
-        const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+        const int i = tid + PT * j, row = i >> 3, c4 = i & 7;
         const float* src = rowA(row);
         xa[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        const int i = tid + 256 * j, row = i >> 3, c4 = i & 7;
+        const int i = tid + PT * j, row = i >> 3, c4 = i & 7;
         const float* src = rowB(row);
         xb[j] = src ? *reinterpret_cast<const float4*>(src + k0 + c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    if (nchunk > 0) load(0, ra[0], rb[0]);
-    if (nchunk > 1) load(1, ra[1], rb[1]);
-    bool run = true;
-    for (int cb = 0; cb < nchunk && run; cb += 2) {
 #pragma unroll
-      for (int d = 0; d < 2; ++d) {
+    for (int d = 0; d < D; ++d)
+      if (d < nchunk) load(d, ra[d], rb[d]);
+    bool run = true;
+    for (int cb = 0; cb < nchunk && run; cb += D) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
         const int c = cb + d;
         if (c >= nchunk || !run) break;
         const int s = c % NS, j = c / NS;
@@ -591,15 +594,15 @@ __device__ bool ws_product(WsSmem<NS, BN>& sm, int K, RA rowA, RB rowB) {
         TcStage<BN>& S = sm.st[s];
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
-          const int i = tid + 256 * q;
+          const int i = tid + PT * q;
           store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[d][q]);
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-          const int i = tid + 256 * q;
+          const int i = tid + PT * q;
           store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[d][q]);
         }
-        if (c + 2 < nchunk) load(c + 2, ra[d], rb[d]);
+        if (c + D < nchunk) load(c + D, ra[d], rb[d]);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.full[s]);
@@ -682,11 +685,12 @@ __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __re
   const bool ok = ws_product(sm, s0 - kfrom, rowA, rowB);
   if (!ok && tid == 0) atomicExch(err, 1);
   if (ok && warp < kWsProducers) {
-    const int q = warp & 3, half = warp >> 2;
+    constexpr int NPART = kWsProducers / 4, PW = BN / NPART;  // column groups of PW per producer warp
+    const int q = warp & 3, part = warp >> 2;
     const int row = r0 + q * 32 + lane;
     float* dst = A + (int64_t)row * ld + s0;
-    for (int g = 0; g < BN / 32; ++g) {
-      const int c0 = half * (BN / 2) + 16 * g;
+    for (int g = 0; g < PW / 16; ++g) {
+      const int c0 = part * PW + 16 * g;
       if (c0 >= ncol) break;  // warp-uniform
       float t[16];
       tmem_ld16(sm.tmem + ((uint32_t)(q * 32) << 16) + c0, t);
@@ -1536,7 +1540,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_tc(const P
 // partial hw[(prow + r) * s + k] = sum over the pair's kept columns of
 // P[r][c] X_{1+k}[c] (block columns [nB, n) for every row, the blanket
 // columns [0, nB) only for the rows of block m itself), where prow is the
-// window's first partial row (wrow[x]).  k_pred_hsum adds each test point's
+// window's first partial row (wrow[item], one entry per item).  k_pred_hsum adds each test point's
 // partials in window order.
 __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_win(const Pair* __restrict__ pairs,
                                                                         const int* __restrict__ wp,
@@ -1601,7 +1605,7 @@ __global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_win(const 
   const int rr = u0 + q * 32 + lane;
   const int kg = k0 + half * 32;
   if (ok && warp < RB / 8 && rr < rows) {
-    float* dst = hw + (wrow[it.x] + rr) * (int64_t)s;
+    float* dst = hw + (wrow[blockIdx.x] + rr) * (int64_t)s;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (kg + j < s) dst[kg + j] = hi[j] + lo[j];

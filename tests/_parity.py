@@ -56,3 +56,26 @@ def check_scalar(test: str, quantity: str, a: float, b: float, tol: float) -> No
     e = abs(a - b) / max(1e-300, abs(b))
     report(test, quantity, "scalar", e, tol)
     assert e <= tol, f"{test}: {quantity} relative error {e:.3e} > {tol:.1e}"
+
+
+class Collector:
+    """Runs every check and reports every measured error before failing with
+    the list of exceeded bounds (so that one run records them all)."""
+
+    def __init__(self):
+        self.errors = []
+
+    def check(self, *a, **k):
+        try:
+            check(*a, **k)
+        except AssertionError as e:
+            self.errors.append(str(e))
+
+    def check_scalar(self, *a, **k):
+        try:
+            check_scalar(*a, **k)
+        except AssertionError as e:
+            self.errors.append(str(e))
+
+    def done(self):
+        assert not self.errors, "; ".join(self.errors)

@@ -22,7 +22,12 @@ spec figure).  Mixed form: predictive mean 1e-4 norm-wise and RMSE
 within 0.1 % of the oracle's (spec figures); the element-wise,
 variance, log-likelihood, summary and gradient bounds are about three
 times the largest error measured on the GB300 at these workloads, so that a
-regression costing one digit fails.
+regression costing one digit fails.  The summary entries of the mixed form
+(quad, A, y-ddot) carry errors of ~1e-2 that the outputs do not: the FP32
+window solves err along the directions that the support set explains, and
+the same error enters quad, y-ddot and A, so that it cancels in
+quad - y-ddot^T (I + A)^-1 y-ddot and in Theorem 2's mean and variance (the
+log-likelihood agrees to 6e-7 at full C2 while quad is off by 5e-3).
 
 The inputs are rebuilt from their seeds and compared with the fingerprints
 the oracle's run recorded (exact hashes of X, S, XU and both partitions; the
@@ -37,7 +42,7 @@ import os
 import numpy as np
 import pytest
 
-from _parity import check, check_scalar
+from _parity import Collector, check, check_scalar
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +54,8 @@ MEAN_ELEM_MIXED = 2e-4          # max |dmean| / max |mean|
 VAR_NORM_MIXED = 3e-4
 VAR_ELEM_MIXED = 1.5e-2         # max |dvar| / var (measured 3.7e-3 at full C2; see test_gpu_parity.py)
 LL_MIXED = 5e-5
-SUMMARY_MIXED = 5e-4            # global-summary entries (norm-wise over the probes)
+SUMMARY_MIXED = 5e-2            # quad, tr A, y-ddot and diag A entries (measured 1.6e-2 at full C2; see below)
+LOGDET_MIXED = 5e-4             # log|R-bar| and log|I + A| (measured 1.5e-4)
 RMSE_MIXED = 1e-3               # spec: RMSE within 0.1 % of the oracle's
 GRAD_FP64 = 1e-9                # the benchmark spec's figure (measured 2.4e-13 on the reduced cases, test_gpu_grad.py)
 GRAD_MIXED = 3e-4
@@ -102,25 +108,28 @@ def _fit_predict(L, p, prec):
 
 
 def _compare(test, p, g, mean, var, summ, fp64):
+    c = Collector()
     rows = np.asarray(g["sample_rows"], dtype=np.int64)
     tm = (TOL_FP64, TOL_FP64) if fp64 else (MEAN_NORM_MIXED, MEAN_ELEM_MIXED)
     tv = (TOL_FP64, TOL_FP64) if fp64 else (VAR_NORM_MIXED, VAR_ELEM_MIXED)
-    check(test, "mean", mean[rows], g["mean"], *tm)
-    check(test, "var", var[rows], g["var"], *tv, positive=True)
+    c.check(test, "mean", mean[rows], g["mean"], *tm)
+    c.check(test, "var", var[rows], g["var"], *tv, positive=True)
     f = g["fit"]
-    check_scalar(test, "loglik", summ["loglik"], f["loglik"], TOL_FP64 if fp64 else LL_MIXED)
+    c.check_scalar(test, "loglik", summ["loglik"], f["loglik"], TOL_FP64 if fp64 else LL_MIXED)
     ts = TOL_FP64 if fp64 else SUMMARY_MIXED
-    check_scalar(test, "quad", summ["quad"], f["quad"], ts)
-    check_scalar(test, "logdet_R", summ["logdet_R"], f["logdet_R"], ts)
-    check_scalar(test, "logdet_C", summ["logdet_C"], f["logdet_C"], ts)
-    check_scalar(test, "A_trace", float(np.trace(summ["A"])), f["A_trace"], ts)
-    check(test, "ydd_head", summ["y"][:16], f["ydd_head"], ts, ts)
-    check(test, "A_diag_head", np.diag(summ["A"])[:16], f["A_diag_head"], ts, ts, positive=True)
+    c.check_scalar(test, "quad", summ["quad"], f["quad"], ts)
+    tl = TOL_FP64 if fp64 else LOGDET_MIXED
+    c.check_scalar(test, "logdet_R", summ["logdet_R"], f["logdet_R"], tl)
+    c.check_scalar(test, "logdet_C", summ["logdet_C"], f["logdet_C"], tl)
+    c.check_scalar(test, "A_trace", float(np.trace(summ["A"])), f["A_trace"], ts)
+    c.check(test, "ydd_head", summ["y"][:16], f["ydd_head"], ts, ts)
+    c.check(test, "A_diag_head", np.diag(summ["A"])[:16], f["A_diag_head"], ts, ts, positive=True)
     if "rmse_all" in g:
         rm = float(np.sqrt(np.mean((mean - p.yU) ** 2)))
-        check_scalar(test, "rmse_all", rm, g["rmse_all"], TOL_FP64 if fp64 else RMSE_MIXED)
+        c.check_scalar(test, "rmse_all", rm, g["rmse_all"], TOL_FP64 if fp64 else RMSE_MIXED)
     rs = float(np.sqrt(np.mean((mean[rows] - p.yU[rows]) ** 2)))
-    check_scalar(test, "rmse_sample", rs, g["rmse_sample"], TOL_FP64 if fp64 else RMSE_MIXED)
+    c.check_scalar(test, "rmse_sample", rs, g["rmse_sample"], TOL_FP64 if fp64 else RMSE_MIXED)
+    c.done()
 
 
 PRED = [("C2", 1, "c2_b1"), ("C2", 2, "c2_b2"), ("C3", 2, "c3"), ("C4", 1, "c4")]
@@ -155,8 +164,10 @@ def test_full_c5_gradient(L, prec):
     ll, gr = L.lma_loglik_grad(precision=getattr(L, prec), **a)
     test = f"full_c5_grad_{prec.lower()}"
     fp64 = prec == "FP64"
-    check_scalar(test, "loglik", ll, g["loglik"], TOL_FP64 if fp64 else LL_MIXED)
+    c = Collector()
+    c.check_scalar(test, "loglik", ll, g["loglik"], TOL_FP64 if fp64 else LL_MIXED)
     tg = GRAD_FP64 if fp64 else GRAD_MIXED
-    check(test, "grad", gr, g["grad"], tg, tg)
+    c.check(test, "grad", gr, g["grad"], tg, tg)
     for k, fd in g["fd"].items():
-        check_scalar(test, f"grad[{k}] vs central difference", float(gr[int(k)]), fd, FD_TOL if fp64 else GRAD_MIXED)
+        c.check_scalar(test, f"grad[{k}] vs central difference", float(gr[int(k)]), fd, FD_TOL if fp64 else GRAD_MIXED)
+    c.done()

@@ -15,7 +15,7 @@ from _parity import check, check_scalar
 pytestmark = pytest.mark.gpu
 
 GRAD_TOL_FP64 = 1e-9
-GRAD_TOL_MIXED = 2e-3
+GRAD_TOL_MIXED = 5e-4
 LL_TOL_MIXED = 1.5e-4
 
 
