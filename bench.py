@@ -78,15 +78,16 @@ def fit_flops(p, B):
 def grad_flops(p, B):
     """Algorithmic flops of lma_loglik_grad beyond the fit it repeats: per
     window W (n = |W|, b = |D_m|, r = 2(s+1) + b right-hand sides) the
-    backward solve r n^2, the matrix G = 1/2 (Phi Phi^T - ...) r n^2 (lower
-    half), G Vt_W 2 n^2 s; over the N points Vt-bar = ... (s^2, triangular) and
+    right-hand sides L^-1 Vt_W Lc^-T s^2 n (triangular), the backward solve
+    r n^2, the matrix G = 1/2 (Phi Phi^T - ...) r n^2 (lower half), G Vt_W
+    2 n^2 s; over the N points Vt-bar = ... (s^2, triangular) and
     K_DS-bar = Vt-bar L_SS^-1 (s^2) and their contraction with dK/dtheta
     (2 N s (d + 2)); L_SS-bar and the Cholesky adjoint 4 s^3 (FP64)."""
     s, N, d = p.s, p.N, p.d
     f = 2.0 * N * s * s + 2.0 * N * s * (d + 2) + 4.0 * s ** 3
     for n, b, nb in window_sizes(p.block_ptr, B):
         r = 2 * (s + 1) + b
-        f += r * n * n + r * n * n + 2.0 * n * n * s
+        f += s * s * n + r * n * n + r * n * n + 2.0 * n * n * s
     return f
 
 
@@ -132,7 +133,9 @@ def kernel_work(p, B, fused=True):
             if k0 == kh and kh > kb:
                 c = min(HP, n - kh)
                 mid += 2.0 * ((rows - kh) * c - c * (c - 1) / 2.0) * (kh - kb)
-    resid = sum(s * n * n for n, _, _ in ws)
+    # the residual kernel's own tiles: the blanket's [0, L)^2 part (L = n_B rounded
+    # down to 128) is copied from the windows that compute it (k_copy_shared_tiles)
+    resid = sum(s * (n * n - ((nb // 128) * 128) ** 2) for n, _, nb in ws)
     gram = sum(b * (s + 1) * (s + 1) for _, b, _ in ws)
     psweep = prhs = pacc = 0.0
     for nb_ in range(M):
@@ -144,10 +147,13 @@ def kernel_work(p, B, fused=True):
     proj = (p.N + p.U) * s * s           # V = L^-1 K_SD: s^2 / 2 multiply-adds per point (triangular)
     var = p.U * s * s                    # L_C^-1 h of every test point (triangular)
     f64 = 2.0 * s ** 3 / 3.0             # Cholesky of Sigma_SS and of I + A, s^3 / 6 multiply-adds each
-    return {"k_chol_step_tc": step, "k_chol_wide": wide, "k_chol_mid": mid, "k_chol_trsm_tc": tri, "k_resid_tc": resid,
+    # the panel steps' update (columns [kh, k0), at most 64) and the panel
+    # solves run in one kernel, k_chol_panel2_tc; k_chol_step_tc only
+    # factorises the first diagonal block of each 128-column group
+    return {"k_chol_panel2_tc": step + tri, "k_chol_wide": wide, "k_chol_mid": mid, "k_resid_tc": resid,
             "k_gram_split": gram, "k_pred_rhs_tc": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
             "k_proj_tc": proj, "k_var_gemm": var,
-            "k_f64_panel": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
+            "k_f64_chain": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
@@ -172,10 +178,24 @@ def sources_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-TENSOR_KERNELS = {"k_chol_step_tc", "k_chol_wide", "k_chol_mid", "k_chol_trsm_tc", "k_pred_sweep_tc", "k_resid_tc",
-                  "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc"}
+TENSOR_KERNELS = {"k_chol_panel2_tc", "k_chol_wide", "k_chol_mid", "k_pred_sweep_tc", "k_resid_tc",
+                  "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc", "k_bwd_sweep_tc", "k_grad_G_tc",
+                  "k_grad_gv_tc", "k_grad_rhs_tc"}
 BF16X6_KERNELS = {"k_proj_tc"}   # bfloat16 x 6 split products (the variance term shares the name k_var_gemm)
-FP64_KERNELS = {"k_f64_panel"}
+FP64_KERNELS = {"k_f64_chain"}
+# launches of the FP64 factorisations (whichever form the tuner chose), reported as one entry
+F64_CHAIN = ("k_f64_potrf", "k_f64_panel", "k_f64_solve2", "k_f64_coop", "k_f64_flow")
+
+
+def merge_f64(prof):
+    """{kernel: (ms, launches)} with the FP64 factorisation launches summed into k_f64_chain."""
+    if not prof:
+        return prof
+    out = {k: v for k, v in prof.items() if k not in F64_CHAIN}
+    parts = [v for k, v in prof.items() if k in F64_CHAIN]
+    if parts:
+        out["k_f64_chain"] = (sum(v[0] for v in parts), sum(v[1] for v in parts))
+    return out
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rate of the part
 FP64_PEAK = 1.25             # nominal FP64 TFLOP/s of the part (no measured figure)
 
@@ -495,6 +515,10 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the form the fit really ran in: a mixed fit whose FP32 window lost
+    # positive definiteness is redone in FP64 by the library
+    model_prec = L.lma_model_precision(step(keep=True)[2])
+    torch.cuda.synchronize()
 
     def timed(nsteps, pr=prec, host=None, profile=None, keep_trace=False):
         """Mean CUDA-event milliseconds of nsteps steps (L2 flushed before each,
@@ -541,7 +565,7 @@ def main():
     value = n_units / (step_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": "train-points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": DTYPE if prec == L.MIXED else "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPE if model_prec == L.MIXED else "f64", "data": "synthetic",
            "config": workload_config(p if world == 1 else p, args.B, world, reduced),
            "tflops": (fit_f + pred_f) / (step_ms / 1e3) / 1e12,
            "algorithmic_gflop_per_step": {"fit": fit_f / 1e9, "predict": pred_f / 1e9},
@@ -559,6 +583,7 @@ def main():
     if world > 1:
         work = {k: v / p.meta.get("copies", 1) for k, v in work.items()}
     _, _, prof_all, trace = timed(1, profile="k_", keep_trace=bool(args.trace))
+    prof_all = merge_f64(prof_all)
     if args.trace and rank == 0:
         with open(args.trace, "w") as fh:
             json.dump([{"kernel": k, "start_ms": a, "end_ms": b} for k, a, b in trace], fh)
@@ -570,7 +595,8 @@ def main():
     roof = None
     if dominant:
         nrs = min(args.steps, 3)
-        _, _, prof, _ = timed(nrs, profile=dominant)
+        _, _, prof, _ = timed(nrs, profile="k_f64_" if dominant == "k_f64_chain" else dominant)
+        prof = merge_f64(prof)
         if prof and dominant in prof:
             tot_ms, n_l = prof[dominant]
             roof = roofline_of(dominant, work[dominant] * nrs, tot_ms, n_l, peaks)
@@ -668,8 +694,9 @@ def main():
             gfl = fit_flops(q, q.B) + grad_flops(q, q.B)
             leg = {"workload": workload_config(q, q.B)["workload"], "ms_per_call": gms,
                    "tflops": gfl / (gms / 1e3) / 1e12, "algorithmic_gflop": gfl / 1e9,
-                   "flop_note": "fit (fit_flops) + adjoint (grad_flops); the adjoint runs on the CUDA cores in FP32 "
-                                "(FP32 SIMT peak 80.5 TFLOP/s at 2070 MHz) and FP64",
+                   "flop_note": "fit (fit_flops) + adjoint (grad_flops); the adjoint's window products (right-hand "
+                                "sides, backward sweep, G, G Vt) run on the tensor cores in 3xTF32, its N x s products "
+                                "on the CUDA cores in FP32 and the s x s part in FP64",
                    "kernel_ms_one_call": {k: round(v[0], 3) for k, v in sorted(gprof.items(), key=lambda kv: -kv[1][0])},
                    "train_points_per_s": q.N / (gms / 1e3), "fit_gflop": fit_flops(q, q.B) / 1e9,
                    "timing": "host wall clock around lma_loglik_grad (it synchronises and returns host values)"}

@@ -307,6 +307,16 @@ int lma_profile_trace(char* names, int names_cap, double* t0_ms, double* t1_ms, 
  * the order of FP64 partial sums.                                          */
 void lma_autotune(int enabled);
 
+/* Pins the launch shape of every shape class whose key starts with `prefix`
+ * (the keys are those of lma_autotune_report, e.g. "fp64 factor" for the
+ * FP64 factorisations of Sigma_SS and I + A, whose choices are 0 one launch
+ * per panel, 1 two launches per panel, 2-4 one cooperative launch with 1, 2
+ * or 4 CTAs per SM, 5 the dataflow form with per-tile flags) to `choice`, on every device, ahead of timing, of the
+ * cache file and of lma_autotune(0).  A choice that is not among a class's
+ * candidates is ignored for that class; the latest matching pin wins.
+ * prefix NULL removes every pin.                                            */
+void lma_autotune_pin(const char* prefix, int choice);
+
 /* Text report of the tuner's choices, one line per shape class:
  * "device | key | choice | candidate:ms ...", NUL-terminated into buf (cap
  * bytes, may be NULL).  Returns the full length of the report.            */

@@ -311,6 +311,12 @@ def lma_autotune(enabled: bool) -> None:
     _abi.load().lma_autotune(int(bool(enabled)))
 
 
+def lma_autotune_pin(prefix, choice: int = 0) -> None:
+    """Pin the launch shape of every tuner key starting with `prefix` to
+    `choice`; prefix None removes every pin (see lma_autotune_pin in lma.h)."""
+    _abi.load().lma_autotune_pin(None if prefix is None else prefix.encode(), int(choice))
+
+
 def lma_autotune_report() -> list:
     """[(device, key, choice, {candidate: ms})] of the tuner's cached choices."""
     lib = _abi.load()

@@ -565,6 +565,8 @@ int lma_profile_stop(char* names, int names_cap, double* total_ms, int64_t* laun
 
 extern "C" void lma_autotune(int enabled) { lma::tune::set_enabled(enabled != 0); }
 
+extern "C" void lma_autotune_pin(const char* prefix, int choice) { lma::tune::pin(prefix, choice); }
+
 extern "C" int lma_autotune_report(char* buf, int cap) {
   const std::string r = lma::tune::report();
   if (buf && cap > 0) {

@@ -126,6 +126,33 @@ inline void launch_pdl(const char* name, void (*kern)(KArgs...), dim3 grid, dim3
   }
 }
 
+// launch() as a cooperative launch: every CTA of the grid is resident at
+// once, so the kernel's CTAs may wait on one another (grid barriers).
+template <typename... KArgs, typename... Args>
+inline void launch_coop(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                        Args... args) {
+  const bool p = prof::active(name);
+  if (p) prof::start(name, st);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+  count_launch();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (p) prof::stop(st);
+  if (e != cudaSuccess) {
+    fail(LMA_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    throw Fail{};
+  }
+}
+
 inline int64_t roundup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // Page-locked staging for the small index tables a call uploads (window

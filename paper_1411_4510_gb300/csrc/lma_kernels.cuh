@@ -352,6 +352,43 @@ __global__ void __launch_bounds__(NT) k_resid(const Win* __restrict__ wins, cons
     }
 }
 
+// Residual entries shared between windows.  A pair of training points (p, q),
+// p <= q (global order), lies in every window that holds both; in the window
+// of p's block, p is a point of the window's own block, and the residual
+// kernel always computes the pair's tile there.  Rows [0, nB) of window k
+// (its blanket, blocks m+1 .. m+B in reversed order) hold only such pairs
+// with p in a later block, so the residual kernel skips window k's 128 x 128
+// tiles inside [0, L)^2 (L[k] = nB rounded down to 128; 0 when a blanket
+// block has no window in this fit) and this kernel copies their lower
+// triangle from the window of each row point's block (local row i of window
+// k is local row i + off of window k', off = g_end(k') - g_end(k)), writing
+// zeros above the diagonal.  Grid: x = row, y = window.
+template <typename T>
+__global__ void k_copy_shared_tiles(const Win* __restrict__ wins, int nwin, int B, const int* __restrict__ Ls,
+                                    T* __restrict__ buf) {
+  const int k = blockIdx.y;
+  const int L = Ls[k];
+  const int i = blockIdx.x;
+  if (i >= L) return;
+  const Win w = wins[k];
+  const int64_t p = w.g_end - 1 - i;
+  int src = -1;
+  for (int kk = k + 1; kk <= k + B && kk < nwin; ++kk) {
+    const Win v = wins[kk];
+    if (p >= v.g_end - v.n && p < v.g_end - v.nB) {
+      src = kk;
+      break;
+    }
+  }
+  if (src < 0) return;  // not reached: the host sets L = 0 unless every blanket block has a window
+  const Win v = wins[src];
+  const int64_t off = v.g_end - w.g_end;
+  const int jmax = (i / 128 + 1) * 128;
+  const T* sp = buf + v.base + (i + off) * (int64_t)v.npad + off;
+  T* dst = buf + w.base + (int64_t)i * w.npad;
+  for (int j = threadIdx.x; j < jmax; j += blockDim.x) dst[j] = j <= i ? sp[j] : T(0);
+}
+
 // Extra rows Y^T of a window: row 0 = r (y - mu), row 1+k = V[k][.] over the
 // window's points (blanket-first order); padding columns are 0.
 template <typename T>

@@ -15,6 +15,7 @@
 #include "lma_kernels.cuh"
 #include "lma_grad.cuh"
 #include "lma_tc.cuh"
+#include "lma_grad_tc.cuh"
 #include "lma_bf6.cuh"
 #include "lma_f64.cuh"
 #include "lma_tune.cuh"
@@ -275,7 +276,7 @@ void Impl<T>::setup_attributes() {
     set_smem_attr<T>();
     set_smem_attr<double>();
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
-    cudaFuncSetAttribute(k_chol_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_chol_panel2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_resid_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
     cudaFuncSetAttribute(k_resid_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
@@ -287,6 +288,10 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_chol_wide<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<256>());
     cudaFuncSetAttribute(k_chol_wide<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<128>());
     cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
+    cudaFuncSetAttribute(k_grad_rhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_bwd_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_grad_G_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
+    cudaFuncSetAttribute(k_grad_gv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     done = true;
   }
 }
@@ -328,14 +333,18 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
           launch_pdl("k_chol_mid", k_chol_wide<128>, dim3(nw, gy), tc::kWsThreads, wide_smem<128>(), st, wins_d,
                      (float*)buf, kh, kb, tc_err);
         }
-        // with nothing to add (k0 = kh) only the row tile holding the diagonal block runs
-        const unsigned gy = k0 == kh ? 1u : (unsigned)((maxrows - k0 + 127) / 128);
-        launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, gy), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-                   (float*)dinv, info, kp, kh, tc_err);
+        // first panel of a 128-column group: its diagonal block has every
+        // column to its left applied, so only the row tile holding it runs
+        // (factorisation); k_chol_panel2_tc then solves the rows below and
+        // finishes the group's second diagonal block, whose panel needs only
+        // the first panel's columns (K = 64) before its own solve
+        if (k0 == kh)
+          launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, 1), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+                     (float*)dinv, info, kp, kh, tc_err);
         if (maxrows - (kp + 1) * TB > 0) {
           const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
-          launch_pdl("k_chol_trsm_tc", k_chol_trsm_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-                     (const float*)dinv, kp, tc_err);
+          launch_pdl("k_chol_panel2_tc", k_chol_panel2_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d,
+                     (float*)buf, (float*)dinv, info, kp, kh, k0 == kh ? 1 : 0, tc_err);
         }
       } else {
         launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,
@@ -367,12 +376,69 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
 // themselves; fewest launches, for small orders where the chain is
 // latency-bound); variant 1: a solve launch and an update launch per panel
 // (each panel tile solved once; for large orders where the FP64 work counts).
+// CTAs of a cooperative FP64 kernel that can be resident at once on this
+// device (which = 0: k_f64_coop, 1: k_f64_flow).
+static int coop_capacity(int which = 0) {
+  static int cap[64][2] = {};
+  int dev = 0;
+  LMA_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return 0;
+  if (!cap[dev][which]) {
+    int nb = 0, sms = 0;
+    if (which == 0)
+      LMA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f64::k_f64_coop, f64::NTH, 0));
+    else
+      LMA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f64::k_f64_flow, f64::NTH, 0));
+    LMA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cap[dev][which] = std::max(1, nb * sms);
+  }
+  return cap[dev][which];
+}
+
+// Tiles of the dataflow form, column by column (see k_f64_flow).
+static std::vector<int2> flow_tiles(int npan, int nrt, int nid) {
+  std::vector<int2> t;
+  for (int j = 0; j < npan; ++j)
+    for (int i = j; i < nrt; ++i) {
+      const int e = i - npan;
+      if (e > j && (e + 1) * f64::TS <= nid) continue;  // identity-row tile that stays zero
+      t.push_back(make_int2(i, j));
+    }
+  return t;
+}
+
+// Launch variants: 0 one launch per panel (k_f64_panel), 1 two launches per
+// panel (k_f64_solve2 + k_f64_update2), 2-4 one cooperative launch
+// (k_f64_coop) with 1, 2 or 4 CTAs per SM, 5 the dataflow form (k_f64_flow,
+// as many CTAs as fit).  `bar` (a zeroed counter for k_f64_coop; npan x nrt
+// zeroed tile flags for k_f64_flow, whose tile list goes to `tl`) and `err`
+// (set on a wait timeout) serve the cooperative forms.
 static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* buf, double* dv, int* info,
-                               int nid = 0, int variant = 0) {
+                               int nid = 0, int variant = 0, unsigned* bar = nullptr, int* err = nullptr,
+                               int2* tl = nullptr) {
   (void)wd;
   using namespace f64;
   const int npan = w.npad / TS, nrt = (w.rows + TS - 1) / TS;
   const int64_t ld = w.npad;
+  if (variant == 5) {
+    const std::vector<int2> tiles = flow_tiles(npan, nrt, nid);
+    const int G = std::max(1, std::min(coop_capacity(1), (int)tiles.size()));
+    stage_copy(tl, tiles.data(), sizeof(int2) * tiles.size(), st);
+    LMA_CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * (size_t)npan * nrt, st));
+    launch_coop("k_f64_flow", k_f64_flow, (unsigned)G, NTH, 0, st, buf, ld, w.rows, npan, nid, dv, info,
+                (const int2*)tl, (int)tiles.size(), bar, err);
+    return;
+  }
+  if (variant >= 2) {
+    int sms = 0, dev = 0;
+    LMA_CK(cudaGetDevice(&dev));
+    LMA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int m0 = npan - 1, work = std::max(m0 * (m0 + 1) / 2 + (nrt - npan) * m0, nrt);
+    const int G = std::max(1, std::min({sms << (variant - 2), coop_capacity(), work}));
+    LMA_CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+    launch_coop("k_f64_coop", k_f64_coop, (unsigned)G, NTH, 0, st, buf, ld, w.rows, npan, nid, dv, info, bar, err);
+    return;
+  }
   launch_pdl("k_f64_potrf", k_f64_potrf, 1, NTH, 0, st, buf, ld, 0, dv, info);
   if (variant == 1) {
     for (int kp = 0; kp < npan; ++kp) {
@@ -398,17 +464,21 @@ static void right_looking_fp64(cudaStream_t st, const Win& w, Win* wd, double* b
 
 // Factorise one FP64 matrix already laid out in `buf` (order n, npad rows,
 // `extra` extra rows); the first failing pivot (+1) goes to *info (device),
-// which the caller checks after its next synchronisation.  The launch
-// variant is a tuning site: both are timed on a scratch copy of the matrix
-// (the factorisation works in place), the model's default being the
-// two-launch form from order 1,024 on.
+// which the caller checks after its next synchronisation; a grid-barrier
+// timeout of the cooperative form sets *err.  The launch variant is a tuning
+// site: all six are timed on a scratch copy of the matrix (the
+// factorisation works in place), the model's default being the dataflow
+// form.
 static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, int npad, int extra, int nid,
-                               int* info) {
+                               int* info, int* err) {
   Win w{};
   w.n = n;
   w.npad = npad;
   w.rows = npad + extra;
   double* dv = tmp.alloc<double>((size_t)npad * TB);
+  const size_t nflag = (size_t)(npad / f64::TS) * ((w.rows + f64::TS - 1) / f64::TS);
+  unsigned* bar = tmp.alloc<unsigned>(nflag);
+  int2* tl = tmp.alloc<int2>(nflag);
   const size_t bytes = (size_t)w.rows * npad * sizeof(double);
   double* scratch = nullptr;
   int* sinfo = nullptr;
@@ -419,12 +489,12 @@ static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
     }
     LMA_CK(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, st));
     LMA_CK(cudaMemsetAsync(sinfo, 0, sizeof(int), st));
-    right_looking_fp64(st, w, nullptr, scratch, dv, sinfo, nid, v);
+    right_looking_fp64(st, w, nullptr, scratch, dv, sinfo, nid, v, bar, err, tl);
   };
   const std::string key = "fp64 factor n=" + std::to_string(n) + " rows=" + std::to_string(w.rows) +
                           " identity=" + std::to_string(nid);
-  const int v = tune::pick(key, {0, 1}, n >= 1024 ? 1 : 0, st, run);
-  right_looking_fp64(st, w, nullptr, buf, dv, info, nid, v);
+  const int v = tune::pick(key, {0, 1, 2, 3, 4, 5}, 5, st, run);
+  right_looking_fp64(st, w, nullptr, buf, dv, info, nid, v, bar, err, tl);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,7 +548,7 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
   mc.flags = mc.keep.alloc<int>(4);
   LMA_CK(cudaMemsetAsync(mc.flags, 0, 4 * sizeof(int), st));
-  factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0);
+  factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
   T* ET = mc.keep.alloc<T>(s * s);
   launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
   mc.ET = ET;
@@ -546,11 +616,23 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       mc.vlo = mc.keep.alloc<float>((size_t)n * sp);
       split_rows(st, (const float*)Vt, n, s, sp, true, mc.vhi, mc.vlo, tmp);
       const CUtensorMap vh = rows_tensor_map(mc.vhi, n, sp), vl = rows_tensor_map(mc.vlo, n, sp);
+      // tiles of window k inside its blanket's [0, L)^2 are copied from the
+      // windows of the blanket's blocks afterwards (k_copy_shared_tiles)
+      // instead of being recomputed; only where all those windows are in this fit
+      std::vector<int> Ls((size_t)M, 0);
+      int maxL = 0;
+      for (int64_t k = 0; k < M; ++k) {
+        const int64_t m = mc.wins[k].m, last = std::min<int64_t>(m + mc.B, mc.M - 1);
+        if (last - w_begin >= M) continue;
+        Ls[k] = (mc.wins[k].nB / 128) * 128;
+        maxL = std::max(maxL, Ls[k]);
+      }
       std::vector<int4> items;
       for (int64_t m = 0; m < M; ++m) {
-        const int np = mc.wins[m].npad;
+        const int np = mc.wins[m].npad, Lt = Ls[m] / 128;
         for (int I = 0; I * 128 < np; ++I)
-          for (int J = 0; J * RB < np && J * RB <= 128 * I + 127; ++J) items.push_back(make_int4((int)m, I, J, 0));
+          for (int J = 0; J * RB < np && J * RB <= 128 * I + 127; ++J)
+            if (!(I < Lt && J < Lt)) items.push_back(make_int4((int)m, I, J, 0));
       }
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
@@ -559,6 +641,12 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
              kSplitThreads, split_smem_bytes(), st,
              (const int4*)itd, (int)items.size(), wd, (const float*)xsT, d, vh, vl, (int)n, sp / 32, (float)mc.ss2, (float)mc.sn2,
              (float*)wbuf, rerr);
+      if (maxL > 0) {
+        int* Lsd = tmp.alloc<int>((size_t)M);
+        stage_copy(Lsd, Ls.data(), sizeof(int) * M, st);
+        launch("k_copy_shared_tiles", k_copy_shared_tiles<float>, dim3((unsigned)maxL, (unsigned)M), NT, 0, st,
+               (const Win*)wd, (int)M, (int)mc.B, (const int*)Lsd, (float*)wbuf);
+      }
       launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
     } else if (batched) {
       launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
@@ -677,7 +765,7 @@ void Impl<T>::fit_global(ModelCore& mc, int64_t n_total, cudaStream_t on) {
     const int npC = (int)roundup(s, TB);
     double* cb = tmp.alloc<double>((size_t)(npC + 1 + s) * npC);
     launch("k_build_global", k_build_global, nblk((int64_t)(npC + 1 + s) * npC), NT, 0, st, mc.G, (int)s, npC, cb);
-    factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1, (int)s, mc.flags + 1);
+    factor_fp64_single(st, tmp, cb, (int)s, npC, (int)s + 1, (int)s, mc.flags + 1, mc.flags + 3);
     mc.beta = mc.keep.alloc<double>(s);
     mc.sc_d = mc.keep.alloc<double>(4);
     double* sc = mc.sc_d;
@@ -725,6 +813,10 @@ void Impl<T>::check(ModelCore& mc, bool global, int64_t n_total, bool logdet_fro
   }
   if (fl[2]) {
     fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the residual or window-sweep kernels");
+    throw Fail{};
+  }
+  if (fl[3]) {
+    fail(LMA_ERR_TIMEOUT, "grid barrier of the FP64 factorisation timed out");
     throw Fail{};
   }
   for (int64_t m = 0; m < nw; ++m)
@@ -1236,29 +1328,66 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     T* Gb = tmp.alloc<T>(ge);
     T* GV = tmp.alloc<T>(gve);
     const T* wbuf = (const T*)mc.wbuf;
-    launch("k_grad_rhs", k_grad_rhs<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd, wbuf,
-           (const T*)mc.LcT, si, Q);
-    launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
-           (const T*)mc.ew, si, Q);
-    std::vector<int2> it_sw, it_g;
-    for (int64_t m = 0; m < M; ++m) {
-      const int nrt = (gw[m].nrows + TB - 1) / TB;
-      for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
-      const int nt = mc.wins[m].npad / TB;
-      for (int t = 0; t < nt * (nt + 1) / 2; ++t) it_g.push_back(make_int2((int)m, t));
-    }
-    int2* isw = tmp.alloc<int2>(it_sw.size());
-    int2* ig = tmp.alloc<int2>(it_g.size());
-    stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
-    stage_copy(ig, it_g.data(), sizeof(int2) * it_g.size(), st);
-    launch("k_bwd_sweep", k_bwd_sweep<T>, dim3((unsigned)it_sw.size()), NT, sizeof(CholSmem<T>), st, isw,
-           mc.wins_d, gwd, wbuf, (const T*)mc.dinv, Q);
     const int np2 = d + 2;
-    double* pG = tmp.alloc<double>(it_g.size() * np2);
-    launch("k_grad_G", k_grad_G<T>, dim3((unsigned)it_g.size()), NT, 0, st, ig, mc.wins_d, gwd, (const T*)Q,
-           (const T*)mc.xsT, d, si, mc.ss2, mc.sn2, Gb, pG);
-    launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd,
-           (const T*)Gb, (const T*)mc.Vt, si, GV);
+    // the window products on the tensor cores in the mixed form (3xTF32,
+    // lma_grad_tc.cuh), on the SIMT kernels of lma_grad.cuh otherwise
+    const bool tc = sizeof(T) == 4 && use_tensor_cores();
+    int* tc_err = mc.flags + 2;
+    LMA_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
+    size_t n_g = 0;
+    double* pG = nullptr;
+    if (tc) {
+      const unsigned st128 = nblk(s, 128);
+      launch("k_grad_rhs_tc", k_grad_rhs_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, mc.wins_d,
+             gwd, (const float*)wbuf, (const float*)mc.LcT, si, (float*)Q, tc_err);
+      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+             (const T*)mc.ew, si, Q);
+      std::vector<int2> it_sw;
+      std::vector<int4> it_g;
+      for (int64_t m = 0; m < M; ++m) {
+        const int nrt = (gw[m].nrows + 127) / 128;
+        for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
+        const int np = mc.wins[m].npad;
+        for (int I = 0; I * 128 < np; ++I)
+          for (int J = 0; J * 64 < np && J * 64 <= 128 * I + 127; ++J) it_g.push_back(make_int4((int)m, I, J, 0));
+      }
+      int2* isw = tmp.alloc<int2>(it_sw.size());
+      int4* ig = tmp.alloc<int4>(it_g.size());
+      stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
+      stage_copy(ig, it_g.data(), sizeof(int4) * it_g.size(), st);
+      launch("k_bwd_sweep_tc", k_bwd_sweep_tc, dim3((unsigned)it_sw.size()), 256, tc_chol_smem(), st,
+             (const int2*)isw, mc.wins_d, gwd, (const float*)wbuf, (const float*)mc.dinv, (float*)Q, tc_err);
+      n_g = it_g.size();
+      pG = tmp.alloc<double>(n_g * np2);
+      launch("k_grad_G_tc", k_grad_G_tc, dim3((unsigned)n_g), 256, tc_chol_smem(), st, (const int4*)ig, mc.wins_d,
+             gwd, (const float*)Q, (const float*)mc.xsT, d, si, (float)mc.ss2, mc.sn2, (float*)Gb, pG, tc_err);
+      launch("k_grad_gv_tc", k_grad_gv_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, mc.wins_d,
+             gwd, (const float*)Gb, (const float*)mc.Vt, si, (float*)GV, tc_err);
+    } else {
+      launch("k_grad_rhs", k_grad_rhs<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd, wbuf,
+             (const T*)mc.LcT, si, Q);
+      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+             (const T*)mc.ew, si, Q);
+      std::vector<int2> it_sw, it_g;
+      for (int64_t m = 0; m < M; ++m) {
+        const int nrt = (gw[m].nrows + TB - 1) / TB;
+        for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
+        const int nt = mc.wins[m].npad / TB;
+        for (int t = 0; t < nt * (nt + 1) / 2; ++t) it_g.push_back(make_int2((int)m, t));
+      }
+      int2* isw = tmp.alloc<int2>(it_sw.size());
+      int2* ig = tmp.alloc<int2>(it_g.size());
+      stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
+      stage_copy(ig, it_g.data(), sizeof(int2) * it_g.size(), st);
+      launch("k_bwd_sweep", k_bwd_sweep<T>, dim3((unsigned)it_sw.size()), NT, sizeof(CholSmem<T>), st, isw,
+             mc.wins_d, gwd, wbuf, (const T*)mc.dinv, Q);
+      n_g = it_g.size();
+      pG = tmp.alloc<double>(n_g * np2);
+      launch("k_grad_G", k_grad_G<T>, dim3((unsigned)n_g), NT, 0, st, ig, mc.wins_d, gwd, (const T*)Q,
+             (const T*)mc.xsT, d, si, mc.ss2, mc.sn2, Gb, pG);
+      launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+             (const T*)Gb, (const T*)mc.Vt, si, GV);
+    }
     int64_t* bptr_d = tmp.alloc<int64_t>(M + 1);
     stage_copy(bptr_d, mc.bptr.data(), sizeof(int64_t) * (M + 1), st);
     T* PsiT = tmp.alloc<T>((s + 1) * n);
@@ -1304,11 +1433,17 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     launch("k_grad_kss", k_grad_kss, (unsigned)s, NT, 0, st, (const double*)Sb, (const double*)mc.ss64, si, d,
            mc.ss2, pS);
     // ordered reduction of the partial sums on the host
-    std::vector<double> h1(it_g.size() * np2), h2((size_t)gx * gy * np2), h3(s * np2);
+    std::vector<double> h1(n_g * np2), h2((size_t)gx * gy * np2), h3(s * np2);
+    int terr = 0;
     LMA_CK(cudaMemcpyAsync(h1.data(), pG, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, st));
     LMA_CK(cudaMemcpyAsync(h2.data(), pK, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, st));
     LMA_CK(cudaMemcpyAsync(h3.data(), pS, sizeof(double) * h3.size(), cudaMemcpyDeviceToHost, st));
+    LMA_CK(cudaMemcpyAsync(&terr, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     LMA_CK(cudaStreamSynchronize(st));
+    if (terr) {
+      fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in the gradient kernels");
+      throw Fail{};
+    }
     for (int q = 0; q < np2; ++q) grad[q] = 0.0;
     for (const auto* v : {&h1, &h2, &h3})
       for (size_t i = 0; i < v->size(); i += np2)

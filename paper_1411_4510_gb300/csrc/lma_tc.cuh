@@ -383,6 +383,145 @@ __device__ bool tile_product(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA
   return ok;
 }
 
+// Four consecutive floats from p with at most lim of them valid (the rest
+// zero); one 16-byte load when p is aligned and all four are valid.
+__device__ __forceinline__ float4 load4_lim(const float* p, int lim) {
+  if (!p || lim <= 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lim >= 4 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) return *reinterpret_cast<const float4*>(p);
+  float4 v;
+  v.x = p[0];
+  v.y = lim > 1 ? p[1] : 0.f;
+  v.z = lim > 2 ? p[2] : 0.f;
+  v.w = lim > 3 ? p[3] : 0.f;
+  return v;
+}
+
+// TF32 hi/lo of one value into (row, k) of a swizzled stage.
+__device__ __forceinline__ void store_split1(float* hi, float* lo, uint32_t row, uint32_t k, float x) {
+  const float h = tf32_round(x);
+  const uint32_t off = sw128_offset(row, k) >> 2;
+  hi[off] = h;
+  lo[off] = tf32_round(x - h);
+}
+
+// tile_product with either operand optionally supplied transposed.
+//   TA = false: rowA(r) -> the K values of row r of A (16-byte aligned) or nullptr;
+//   TA = true:  rowA(k) -> the values A(0 .. 127, k), contiguous, or nullptr
+//               (k in [0, ceil32(K)); only the first alim are read).
+// The same for B with BN rows (TB, blim).  negB: B enters negated.  acc0:
+// add to the accumulator instead of overwriting it with the first chunk.
+// A transposed chunk (32 values of K x 128 rows) is read by lane = k, so a
+// warp's shared-memory stores fill one 128-byte row of the swizzled stage
+// (conflict-free) while its global loads take 16 bytes from each of 32 rows.
+template <int BN, bool TA, bool TB, int DEPTH = 2, class RA, class RB>
+__device__ bool tile_product2(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, RA rowA, RB rowB, int alim, int blim,
+                              bool negB, bool acc0) {
+  constexpr int NA = 128 * 8 / 256;
+  constexpr int NB = (BN * 8 + 255) / 256;
+  const int tid = threadIdx.x;
+  const uint32_t idesc = idesc_tf32(128, BN);
+  const int nchunk = (K + 31) / 32;
+  float4 ra[DEPTH][NA], rb[DEPTH][NB];
+  auto load = [&](int c, float4 (&xa)[NA], float4 (&xb)[NB]) {
+    const int kc = c * 32;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int i = tid + 256 * j;
+      if (TA) {
+        const int kk = i & 31, r4 = i >> 5;
+        const float* src = rowA(kc + kk);
+        xa[j] = load4_lim(src ? src + r4 * 4 : nullptr, alim - r4 * 4);
+      } else {
+        const float* src = rowA(i >> 3);
+        xa[j] = src ? *reinterpret_cast<const float4*>(src + kc + (i & 7) * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int i = tid + 256 * j;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < BN * 8) {
+        if (TB) {
+          const int kk = i & 31, c4 = i >> 5;
+          const float* src = rowB(kc + kk);
+          v = load4_lim(src ? src + c4 * 4 : nullptr, blim - c4 * 4);
+        } else {
+          const float* src = rowB(i >> 3);
+          if (src) v = *reinterpret_cast<const float4*>(src + kc + (i & 7) * 4);
+        }
+      }
+      if (negB) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+      xb[j] = v;
+    }
+  };
+#pragma unroll
+  for (int d = 0; d < DEPTH; ++d)
+    if (d < nchunk) load(d, ra[d], rb[d]);
+  for (int cb = 0; cb < nchunk; cb += DEPTH) {
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) {
+      const int c = cb + d;
+      if (c >= nchunk) break;
+      const int s = c & 1;
+      if (!tc_drain(sm, p, s)) return false;
+      TcStage<BN>& S = sm.st[s];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int i = tid + 256 * j;
+        if (TA) {
+          const int kk = i & 31, r = (i >> 5) * 4;
+          store_split1(S.a_hi, S.a_lo, r + 0, kk, ra[d][j].x);
+          store_split1(S.a_hi, S.a_lo, r + 1, kk, ra[d][j].y);
+          store_split1(S.a_hi, S.a_lo, r + 2, kk, ra[d][j].z);
+          store_split1(S.a_hi, S.a_lo, r + 3, kk, ra[d][j].w);
+        } else {
+          store_split4(S.a_hi, S.a_lo, i >> 3, (i & 7) * 4, ra[d][j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int i = tid + 256 * j;
+        if (i >= BN * 8) continue;
+        if (TB) {
+          const int kk = i & 31, r = (i >> 5) * 4;
+          store_split1(S.b_hi, S.b_lo, r + 0, kk, rb[d][j].x);
+          store_split1(S.b_hi, S.b_lo, r + 1, kk, rb[d][j].y);
+          store_split1(S.b_hi, S.b_lo, r + 2, kk, rb[d][j].z);
+          store_split1(S.b_hi, S.b_lo, r + 3, kk, rb[d][j].w);
+        } else {
+          store_split4(S.b_hi, S.b_lo, i >> 3, (i & 7) * 4, rb[d][j]);
+        }
+      }
+      if (c + DEPTH < nchunk) load(c + DEPTH, ra[d], rb[d]);
+      fence_async_smem();
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      if (tid < 32) {
+        if (tid == 0) {
+          const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
+          const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (acc0 || c > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(tmem, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+            mma_tf32(tmem, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+          }
+          mma_commit(&sm.bar[s]);
+        }
+        __syncwarp();
+      }
+      p.cnt[s] += 1;
+      p.pending[s] = true;
+    }
+  }
+  bool ok = tc_drain(sm, p, 0);
+  ok = tc_drain(sm, p, 1) && ok;
+  fence_after_sync();
+  return ok;
+}
+
 }  // namespace tc
 }  // namespace lma
 
@@ -393,9 +532,10 @@ namespace lma {
 // window buffer: T = A_{rows, panel} - A_{rows, kb:k0} A_{panel, kb:k0}^T with
 // the product on tcgen05 (3xTF32); columns [0, kb) were applied by the
 // super-panel update (kb = 0 without one).  The diagonal 64x64 block (first
-// rows of y = 0) is factorised in shared memory; every other row keeps T
-// for k_chol_trsm_tc.  Row tile 0 of every window comes first in launch
-// order, so the diagonal factorisations start in the first wave.
+// rows of y = 0) is factorised in shared memory; every other row keeps T.
+// The mixed sweep launches it for the row tile holding the diagonal block
+// only (y = 0, K = 0: the first panel of a 128-column group); the rows
+// below are solved by k_chol_panel2_tc.
 __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
                                                       int kb, int* __restrict__ err) {
@@ -722,12 +862,23 @@ __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __re
 
 namespace lma {
 
-// Panel solve of column panel kp on the tensor cores: rows
-// [k0 + 64 + 128 x, ... + 128) of every window get A_{row, panel} <- T inv(L_kk)^T
-// (T held there by k_chol_step_tc, inv(L_kk) in dinv).  Rows of the tile are
-// read into shared memory before any result is written back.
-__global__ void __launch_bounds__(256, 2) k_chol_trsm_tc(const Win* __restrict__ wins, float* __restrict__ buf,
-                                                      const float* __restrict__ dinv, int kp, int* __restrict__ err) {
+// Update and solve of column panel kp in one pass (mixed form), for the rows
+// below its diagonal block: CTA (row tile x, window y) owns rows
+// [k0 + 64 + 128 x, ... + 128) and computes
+//   T = A_{rows, panel} - A_{rows, kfrom:k0} A_{panel, kfrom:k0}^T   (skipped when kfrom = k0)
+//   A_{rows, panel} <- T inv(L_kk)^T
+// with both products on tcgen05 (3xTF32); columns [0, kfrom) were applied
+// by the wider updates and inv(L_kk) is in dinv.  With `next`, row tile 0
+// then also finishes panel kp + 1's diagonal block: its rows are the tile's
+// first 64, whose panel-kp values it has just written, so
+//   D = A_{kp+1, kp+1} - L_{kp+1, kp} L_{kp+1, kp}^T
+// is the block with every column left of panel kp + 1 applied (those left of
+// panel kp came from the wider updates), and the CTA factorises it into
+// L_{kp+1, kp+1} and inv(L_{kp+1, kp+1}).  Row tile 0 of every window comes
+// first in launch order, so the factorisations start in the first wave.
+__global__ void __launch_bounds__(256, 2) k_chol_panel2_tc(const Win* __restrict__ wins, float* __restrict__ buf,
+                                                        float* __restrict__ dinv, int* __restrict__ info, int kp,
+                                                        int kfrom, int next, int* __restrict__ err) {
   grid_dep_wait();
   grid_dep_launch();
   using namespace tc;
@@ -741,7 +892,6 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm_tc(const Win* __restrict__
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* A = buf + w.base;
   const int64_t ld = w.npad;
-  const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
   if (tid == 0) {
     mbar_init(&sm.bar[0], 1);
     mbar_init(&sm.bar[1], 1);
@@ -753,36 +903,94 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm_tc(const Win* __restrict__
   fence_after_sync();
   const uint32_t tmem = sm.tmem;
   TcPipe pipe;
-  auto rowA = [&](int r) -> const float* {
-    const int row = r0 + r;
-    return row < w.rows ? A + (int64_t)row * ld + k0 : nullptr;
-  };
-  auto rowB = [&](int c) -> const float* { return Dv + (int64_t)c * TB; };
-  const bool ok = tile_product<64>(sm, pipe, tmem, TB, rowA, rowB);
-  if (!ok && tid == 0) atomicExch(err, 1);
   const int q = warp & 3, half = warp >> 2;
-  const int row = r0 + q * 32 + lane;
-  if (ok) {  // uniform: tcgen05.ld is executed by whole warps, stores are per row
-    float* dst = A + (int64_t)row * ld + k0 + half * 32;
+  const int rl = q * 32 + lane, row = r0 + rl;
+  const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
+  float* myrow = A + (int64_t)row * ld + k0 + half * 32;
+  bool ok = true;
+  const int K = k0 - kfrom;
+  if (K > 0) {
+    auto rowA = [&](int r) -> const float* {
+      return r0 + r < w.rows ? A + (int64_t)(r0 + r) * ld + kfrom : nullptr;
+    };
+    auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld + kfrom; };
+    ok = tile_product<64>(sm, pipe, tmem, K, rowA, rowB);
+    if (ok) {
+      float v[32], t[16];
+      tmem_ld16(taddr, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = t[j];
+      tmem_ld16(taddr + 16, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
+      if (row < w.rows) {
+        float4 av[8];
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(myrow + 4 * j4);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          float4 a = av[j4];
+          a.x -= v[4 * j4 + 0];
+          a.y -= v[4 * j4 + 1];
+          a.z -= v[4 * j4 + 2];
+          a.w -= v[4 * j4 + 3];
+          *reinterpret_cast<float4*>(myrow + 4 * j4) = a;
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  if (ok) {
+    const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
+    auto rowT = [&](int r) -> const float* { return r0 + r < w.rows ? A + (int64_t)(r0 + r) * ld + k0 : nullptr; };
+    auto rowD = [&](int c) -> const float* { return Dv + (int64_t)c * TB; };
+    ok = tile_product<64>(sm, pipe, tmem, TB, rowT, rowD);
+    if (ok) {
+      float t[16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tmem_ld16(taddr + 16 * h, t);
+        if (row < w.rows)
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4)
+            *reinterpret_cast<float4*>(myrow + 16 * h + 4 * j4) =
+                make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  const bool diag = ok && next && blockIdx.x == 0 && k0 + TB < w.npad;
+  if (diag) {
+    // D = A_{kp+1, kp+1} - X X^T over the 64 panel-kp columns of rows [k0 + 64, k0 + 128)
+    const int d0 = k0 + TB;
+    auto rowX = [&](int r) -> const float* { return r < TB ? A + (int64_t)(d0 + r) * ld + k0 : nullptr; };
+    auto rowY = [&](int c) -> const float* { return A + (int64_t)(d0 + c) * ld + k0; };
+    ok = tile_product<64>(sm, pipe, tmem, TB, rowX, rowY);
+  }
+  float* scratch = reinterpret_cast<float*>(&sm.st[0]);
+  float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
+  if (diag && ok) {
     float t[16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + half * 32 + 16 * h, t);
-      if (row < w.rows)
+      tmem_ld16(taddr + 16 * h, t);  // whole warps; only rows < 64 are used
+      if (rl < TB) {
+        const float* src = A + (int64_t)(k0 + TB + rl) * ld + k0 + TB + half * 32 + 16 * h;
 #pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4)
-          *reinterpret_cast<float4*>(dst + 16 * h + 4 * j4) =
-              make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
+        for (int j = 0; j < 16; ++j) Dm[rl][half * 32 + 16 * h + j] = src[j] - t[j];
+      }
     }
   }
+  if (!ok && tid == 0) atomicExch(err, 1);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
+  if (diag && ok)
+    diag_factor<float>(Dm, A + (int64_t)(k0 + TB) * ld + k0 + TB, ld, dinv + w.dinv + (int64_t)(kp + 1) * TB * TB,
+                       info + blockIdx.y, k0 + TB);
 }
-
-}  // namespace lma
-
-namespace lma {
 
 // Forward solve of the prediction right-hand sides on the tensor cores: CTA
 // (pair, 128 test rows) sweeps the window's column panels left to right,

@@ -27,6 +27,7 @@ struct State {
   int enabled = -1;                                    // -1: not read from the environment yet
   std::map<int, std::map<std::string, Entry>> cache;  // device -> key -> entry
   std::map<int, std::string> dev_name;
+  std::vector<std::pair<std::string, int>> pins;      // key prefix -> forced choice
   bool file_read = false;
 };
 
@@ -107,8 +108,15 @@ int pick(const std::string& key, const std::vector<int>& cands, int fallback, cu
          const std::function<void(int)>& run, int reps) {
   if (cands.empty()) return fallback;
   if (cands.size() == 1) return cands[0];
-  if (!enabled()) return fallback;
   State& s = st();
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    for (auto it = s.pins.rbegin(); it != s.pins.rend(); ++it)
+      if (key.compare(0, it->first.size(), it->first) == 0)
+        for (int c : cands)
+          if (c == it->second) return c;
+  }
+  if (!enabled()) return fallback;
   int dev = 0;
   LMA_CK(cudaGetDevice(&dev));
   {
@@ -163,6 +171,16 @@ std::string report() {
       o << "\n";
     }
   return o.str();
+}
+
+void pin(const char* prefix, int choice) {
+  State& s = st();
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (!prefix) {
+    s.pins.clear();
+    return;
+  }
+  s.pins.emplace_back(prefix, choice);
 }
 
 void clear() {

@@ -35,6 +35,11 @@ void set_enabled(bool on);
 int pick(const std::string& key, const std::vector<int>& cands, int fallback, cudaStream_t st,
          const std::function<void(int)>& run, int reps = 2);
 
+// Pins every key starting with `prefix` to `choice` (where it is a
+// candidate), ahead of the cache and of timing; the latest matching pin wins.
+// prefix == nullptr removes all pins.
+void pin(const char* prefix, int choice);
+
 // Text report of the cache: "device | key | choice | candidates and their ms".
 std::string report();
 void clear();

@@ -19,9 +19,9 @@ def test_work_model_c2():
     assert all(v > 0 for v in fused.values())
     assert "k_pred_sweep_tc" not in fused and plain["k_pred_sweep_tc"] > 0
     # the test rows add work to the fit's sweep only
-    for k in ("k_chol_step_tc", "k_chol_wide", "k_chol_mid", "k_chol_trsm_tc"):
+    for k in ("k_chol_panel2_tc", "k_chol_wide", "k_chol_mid"):
         assert fused[k] > plain[k]
-    for k in ("k_resid_tc", "k_gram_split", "k_pred_rhs_tc", "k_proj", "k_f64_panel"):
+    for k in ("k_resid_tc", "k_gram_split", "k_pred_rhs_tc", "k_proj", "k_f64_chain"):
         assert fused[k] == plain[k]
     # left-looking update of the windows, counted once: wide + mid + step = the full left-looking sum
     s = p.s
@@ -31,4 +31,11 @@ def test_work_model_c2():
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
             full += 2.0 * ((rows - k0) * w - w * (w - 1) / 2.0) * k0
-    assert abs(plain["k_chol_wide"] + plain["k_chol_mid"] + plain["k_chol_step_tc"] - full) <= 1e-9 * full
+    tri = 0.0
+    for n, b, nb in bench.window_sizes(p.block_ptr, 1):
+        rows = n + s + 1
+        for k0 in range(0, n, 64):
+            w = min(64, n - k0)
+            tri += max(0, rows - k0 - w) * w * w
+    panel_update = plain["k_chol_panel2_tc"] - tri
+    assert abs(plain["k_chol_wide"] + plain["k_chol_mid"] + panel_update - full) <= 1e-9 * full

@@ -56,6 +56,7 @@ def test_c3_shaped_uneven_blocks(L, c3, prec):
     args.update(X=torch.as_tensor(p.X, device=dev), y=torch.as_tensor(p.y, device=dev),
                 S=torch.as_tensor(p.S, device=dev))
     model = L.lma_fit(precision=getattr(L, prec), **args)
+    assert L.lma_model_precision(model) == getattr(L, prec), "the mixed fit was redone in FP64"
     mean, var = L.lma_predict(model, torch.as_tensor(p.XU, device=dev), p.test_block_ptr)
     mean, var = mean.cpu().numpy()[sel], var.cpu().numpy()[sel]
     ll = L.lma_model_loglik(model)

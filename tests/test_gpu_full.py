@@ -22,7 +22,11 @@ spec figure).  Mixed form: predictive mean 1e-4 norm-wise and RMSE
 within 0.1 % of the oracle's (spec figures); the element-wise,
 variance, log-likelihood, summary and gradient bounds are about three
 times the largest error measured on the GB300 at these workloads, so that a
-regression costing one digit fails.  The summary entries of the mixed form
+regression costing one digit fails.  The variance's norm-wise error is
+largest at C4 (3.8e-4; 4.5e-5 at C2): C4's noise variance is 0.01 and its
+test points sit among 2M training points, so their variances are about
+1.5 sigma_n^2 while the terms that make them are O(sigma_s^2) = O(1); the
+FP32 window solves' absolute error of ~6e-6 is 4e-4 of such a variance.  The summary entries of the mixed form
 (quad, A, y-ddot) carry errors of ~1e-2 that the outputs do not: the FP32
 window solves err along the directions that the support set explains, and
 the same error enters quad, y-ddot and A, so that it cancels in
@@ -51,7 +55,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TOL_FP64 = 1e-9
 MEAN_NORM_MIXED = 1e-4          # north star
 MEAN_ELEM_MIXED = 2e-4          # max |dmean| / max |mean|
-VAR_NORM_MIXED = 3e-4
+VAR_NORM_MIXED = 1.2e-3         # measured 3.8e-4 at full C4 (below)
 VAR_ELEM_MIXED = 1.5e-2         # max |dvar| / var (measured 3.7e-3 at full C2; see test_gpu_parity.py)
 LL_MIXED = 5e-5
 SUMMARY_MIXED = 5e-2            # quad, tr A, y-ddot and diag A entries (measured 1.6e-2 at full C2; see below)
@@ -102,6 +106,7 @@ def _fit_predict(L, p, prec):
     mean, var, model = L.lma_fit_predict(XU=XU, test_block_ptr=p.test_block_ptr, precision=prec,
                                          keep_model=True, **a)
     torch.cuda.synchronize()
+    assert L.lma_model_precision(model) == prec, "the mixed fit was redone in FP64"
     summ = L.lma_model_summary(model)
     del model
     return mean.cpu().numpy(), var.cpu().numpy(), summ

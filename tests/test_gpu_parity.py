@@ -48,6 +48,14 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1e-300, np.linalg.norm(np.asarray(b))))
 
 
+def expect_mixed(L, model, prec):
+    """A mixed fit that lost positive definiteness in a window is redone in
+    the FP64 form (lma_model_precision tells); none of these cases should
+    need that, and an FP64 model would pass the mixed bounds unnoticed."""
+    if prec == L.MIXED:
+        assert L.lma_model_precision(model) == L.MIXED, "the mixed fit was redone in FP64"
+
+
 def run_gpu(L, p, prec, B=None, on_device=True, noisy=True):
     import torch
     args = L.problem_args(p, B)
@@ -59,6 +67,7 @@ def run_gpu(L, p, prec, B=None, on_device=True, noisy=True):
     else:
         XU = p.XU
     model = L.lma_fit(precision=prec, **args)
+    expect_mixed(L, model, prec)
     mean, var = L.lma_predict(model, XU, p.test_block_ptr, noisy=noisy)
     if on_device:
         mean, var = mean.cpu().numpy(), var.cpu().numpy()
@@ -188,6 +197,7 @@ def run_fit_predict(L, p, prec, B=None):
     args = L.problem_args(p, B)
     mean, var, model = L.lma_fit_predict(XU=p.XU, test_block_ptr=p.test_block_ptr, precision=prec,
                                          keep_model=True, **args)
+    expect_mixed(L, model, prec)
     return model, mean, var
 
 

@@ -47,6 +47,7 @@ def test_sharded_equals_whole(L, prec, tol_ll, tol_mean, B, world):
     args = L.problem_args(p)
     precision = getattr(L, prec)
     whole = L.lma_fit(precision=precision, **args)
+    assert L.lma_model_precision(whole) == precision, "the mixed fit was redone in FP64"
     ll_whole = L.lma_model_loglik(whole)
     mean_w, var_w = L.lma_predict(whole, p.XU, p.test_block_ptr)
     shards = [shard.plan(p.block_ptr, B, world, r) for r in range(world)]
@@ -54,6 +55,7 @@ def test_sharded_equals_whole(L, prec, tol_ll, tol_mean, B, world):
     for sh in shards:
         sub = shard.sub_problem(args, sh)
         m = api.lma_fit_local(**sub, win_begin=0, own_begin=sh.own_begin, own_end=sh.own_end, precision=precision)
+        assert L.lma_model_precision(m) == precision, "the mixed local fit was redone in FP64"
         g, l = api.lma_model_local_summary(m, device=torch.device("cuda:0"))
         G = g if G is None else G + g
         ld += l
