@@ -1102,12 +1102,14 @@ namespace lma {
 // 4 BN worker threads (warps 0 .. BN/8 - 1) load each 32-wide K chunk one
 // chunk ahead into registers, split it into TF32 hi/lo into stage c mod 2 and
 // arrive on full[s]; the last warp issues the chunk's 12 MMAs into tensor-
-// memory slot c mod 2 (columns [BN s, BN s + BN)) and commits to done[s].
-// Before refilling stage s the workers wait for done[s] of chunk c - 2 and
-// drain that slot into registers, adding the chunk sums with TwoSum; their
-// arrival on full[s] therefore also frees slot s for the next MMAs.  The
-// tensor core's FP32 accumulation is only 12 MMA steps deep, the cross-chunk
-// sum is compensated, and no CTA-wide barrier waits for the MMA issue.
+// memory slot (c / 2) mod 2 (columns [BN slot, BN slot + BN)) and commits to
+// done[s].  Before refilling stage s the workers wait for done[s] of chunk
+// c - 2; when that chunk ends a pair (chunks 2p, 2p + 1) they drain the
+// pair's slot into registers, adding its sums with TwoSum, so the slot is
+// free before the MMAs of pair p + 2 start.  The tensor core's FP32
+// accumulation is 24 MMA steps (64 values of K) deep, the cross-pair sum is
+// compensated, and no CTA-wide barrier waits for the MMA issue.  (Draining
+// after every chunk made the workers' TwoSum work, not the MMAs, the limit.)
 template <int BN>
 struct CompSmem {
   tc::TcStage<BN> st[2];
@@ -1190,12 +1192,12 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
       if (!okw) *abort_flag = 1;
       return okw != 0;
     };
-    auto drain = [&](int g) {
+    auto drain = [&](int pair) {
       fence_after_sync();
       float t[16];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        tmem_ld16(tlane + BN * (g & 1) + 16 * h, t);
+        tmem_ld16(tlane + BN * (pair & 1) + 16 * h, t);
 #pragma unroll
         for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], t[j]);
       }
@@ -1227,12 +1229,15 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
         rb[j] = ld4(rowB(row), k0 + c4 * 4);
       }
     };
+    // chunk c of this call accumulates into tensor-memory slot (c / 2) mod 2;
+    // a slot is drained once the last chunk of its pair has completed
+    auto ends_pair = [&](int c) { return (c & 1) == 1 || c == nchunk - 1; };
     if (nchunk > 0) load(0);
     for (int c = 0; c < nchunk; ++c) {
       const int g = g0 + c, s = g & 1;
-      if (c >= 2) {  // chunk g - 2 used stage s and slot s
+      if (c >= 2) {  // chunk c - 2 used stage s
         if (!wait_done(g - 2)) break;
-        drain(g - 2);
+        if (ends_pair(c - 2)) drain((c - 2) >> 1);
       }
       if (*abort_flag) break;
       TcStage<BN>& S = sm.st[s];
@@ -1254,7 +1259,7 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
     }
     for (int c = max(0, nchunk - 2); c < nchunk && !*abort_flag; ++c) {  // the last one or two chunks, in order
       if (!wait_done(g0 + c)) break;
-      drain(g0 + c);
+      if (ends_pair(c)) drain(c >> 1);
     }
   } else {
     // MMA warp: the whole warp runs the loop, lane 0 issues
@@ -1274,11 +1279,12 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
         TcStage<BN>& S = sm.st[s];
         const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
         const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-        const uint32_t dcol = sm.tmem + BN * s;
+        const uint32_t dcol = sm.tmem + BN * ((c >> 1) & 1);
+        const bool first = (c & 1) == 0;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           const uint32_t o = ks * 32;
-          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, ks > 0 ? 1u : 0u);
+          mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (first && ks == 0) ? 0u : 1u);
           mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
           mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
         }

@@ -33,6 +33,15 @@ the same error enters quad, y-ddot and A, so that it cancels in
 quad - y-ddot^T (I + A)^-1 y-ddot and in Theorem 2's mean and variance (the
 log-likelihood agrees to 6e-7 at full C2 while quad is off by 5e-3).
 
+The mixed gradient at full C5 is 1.5e-3 from the oracle's (norm-wise and
+against the central differences); the same adjoint on the CUDA cores (the
+SIMT kernels, FP32 FMA) measured 1.1e-3 on the same FP32 window factors, so
+most of it is the mixed form's FP32 factorisation (its R_W^-1 terms enter
+the trace part of the gradient, where the data and trace parts cancel to
+about 1 % of either), and the tensor-core products add a little (TF32
+splitting, FP32 accumulation over K = 2(s + 1) + b = 2,562 values).  The
+bound is about three times the measurement.
+
 The inputs are rebuilt from their seeds and compared with the fingerprints
 the oracle's run recorded (exact hashes of X, S, XU and both partitions; the
 outputs y to 1e-10 relative, since the random-Fourier-feature cosines may
@@ -62,7 +71,7 @@ SUMMARY_MIXED = 5e-2            # quad, tr A, y-ddot and diag A entries (measure
 LOGDET_MIXED = 5e-4             # log|R-bar| and log|I + A| (measured 1.5e-4)
 RMSE_MIXED = 1e-3               # spec: RMSE within 0.1 % of the oracle's
 GRAD_FP64 = 1e-9                # the benchmark spec's figure (measured 2.4e-13 on the reduced cases, test_gpu_grad.py)
-GRAD_MIXED = 3e-4
+GRAD_MIXED = 5e-3               # measured 1.5e-3 at full C5 (1.1e-3 with the SIMT adjoint; below)
 FD_TOL = 1e-6                   # central differences with h = 1e-4: truncation ~h^2 relative
 
 
