@@ -424,6 +424,32 @@ def build_problem(args, world, rank):
     return make_replicated(args.config, hi - lo + 1, B=args.B, first_draw=lo, **kw), rank - lo
 
 
+def grad_only(args, p, full, dev, L):
+    """--mode grad: lma_loglik_grad on the configured workload (inputs resident),
+    args.warmup untimed and args.steps timed calls (host clock: the call
+    synchronises and returns host values), one JSON line."""
+    import torch
+    prec = L.FP64 if args.precision == "fp64" else L.MIXED
+    d = {k: torch.as_tensor(full[k], device=dev) for k in ("X", "y", "S")}
+    kw = {k: v for k, v in full.items() if k not in ("X", "y", "S")}
+    for _ in range(args.warmup):
+        L.lma_loglik_grad(d["X"], d["y"], S=d["S"], precision=prec, **kw)
+    torch.cuda.synchronize()
+    n0 = L.lma_kernel_launch_count()
+    tms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        L.lma_loglik_grad(d["X"], d["y"], S=d["S"], precision=prec, **kw)
+        tms.append(1e3 * (time.perf_counter() - t0))
+    ms = statistics.mean(tms)
+    gfl = fit_flops(p, args.B if args.B is not None else p.B) + grad_flops(p, args.B if args.B is not None else p.B)
+    print(json.dumps({"metric": "lma_loglik_grad train-points/s", "value": p.N / (ms / 1e3), "unit": "train-points/s",
+                      "ms_per_call": ms, "steps": args.steps, "warmup": args.warmup, "tflops": gfl / (ms / 1e3) / 1e12,
+                      "gpu_launches": int(L.lma_kernel_launch_count() - n0),
+                      "config": workload_config(p, args.B if args.B is not None else p.B, 1,
+                                                any(getattr(args, k) is not None for k in ("N", "M", "s", "U")))}))
+
+
 # ----------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -437,8 +463,9 @@ def main():
     ap.add_argument("--M", type=int, default=None, help="reduced case: blocks")
     ap.add_argument("--s", type=int, default=None, help="reduced case: support points")
     ap.add_argument("--U", type=int, default=None, help="reduced case: test points")
-    ap.add_argument("--mode", default="full", choices=["full", "step"],
-                    help="step: warm-up and timed steps only (for profilers)")
+    ap.add_argument("--mode", default="full", choices=["full", "step", "grad"],
+                    help="step: warm-up and timed steps only (for profilers); grad: lma_loglik_grad on the "
+                         "configured workload, warm-up and timed calls only (1 GPU)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="form of the timed steps")
     ap.add_argument("--ref-blocks", type=int, default=2,
                     help="blocks of the oracle's sample (cpu_baseline and the reference arm)")
@@ -483,6 +510,9 @@ def main():
     p, my = build_problem(args, world, rank)
     dev = torch.device("cuda", local)
     full = L.problem_args(p, B=args.B)
+    if args.mode == "grad":
+        grad_only(args, p, full, dev, L)
+        return
     if world == 1:
         sh, sub, u0, u1, tptr = None, full, 0, p.U, p.test_block_ptr
     else:

@@ -207,6 +207,19 @@ lma_status lma_model_local_summary(const lma_model* model, double* G_out, double
 lma_status lma_model_set_global(lma_model* model, const double* G, double logdet_R,
                                 int64_t n_total, int on_device);
 
+/* Gradient of the log-likelihood of a fitted model with respect to
+ * (log l_1..log l_d, log sigma_s, log sigma_n) (d+2 doubles, host), by the
+ * hand adjoint of lma_loglik_grad applied to the windows of the blocks whose
+ * summaries the model holds: all of them for a model of lma_fit, blocks
+ * [own_begin, own_end) for one of lma_fit_local whose global step is done
+ * (lma_model_set_global).  Every step of the adjoint after the window terms
+ * is linear in them, so the shards' results add up to the whole gradient:
+ * a sharded gradient is one all-reduce of d+2 values (the paper does not
+ * differentiate its likelihood; jitter and the partition are held fixed).
+ * The model's stored window factors are reused.  LMA_ERR_INVALID_ARG before
+ * the global step.                                                          */
+lma_status lma_model_loglik_grad(lma_model* model, double* grad_out);
+
 /* The residual R = Sigma - Q over the window D_m u D^B_m of block m, as an
  * n_w x n_w matrix in natural row order (host memory, n_w = number of rows
  * of D_m u D^B_m), evaluated by the selected precision's kernels before any

@@ -357,7 +357,7 @@ def _tri_adj_chol(L, Lbar):
     return 0.5 * (Y + Y.T)
 
 
-def loglik_grad(prob, B: int | None = None) -> tuple[float, np.ndarray]:
+def loglik_grad(prob, B: int | None = None, windows=None) -> tuple[float, np.ndarray]:
     """Hand adjoint of the summary-form log-likelihood.
 
     In the whitened support coordinates V = L_SS^-1 Sigma_SD (Vt = V^T,
@@ -376,7 +376,12 @@ def loglik_grad(prob, B: int | None = None) -> tuple[float, np.ndarray]:
         theta-bar += <G_m, dK_W/dtheta> + 2 sigma_n^2 tr(G_m) (log sigma_n)
     then Vt = K_DS L_SS^-T: K_DS-bar = Vt-bar L_SS^-1, L_SS-bar = -L_SS^-T Vt-bar^T Vt
     and the Cholesky adjoint back to Sigma_SS.
-    Returns (loglik, grad) with grad ordered (log l_1..d, log sigma_s, log sigma_n)."""
+    Returns (loglik, grad) with grad ordered (log l_1..d, log sigma_s, log sigma_n).
+
+    windows: the blocks m whose window terms enter (default: all).  Beta and
+    Lc are the whole fit's; every step after the window loop is linear in
+    Vbar and g, so the results for a partition of the blocks add up to the
+    whole gradient (a sharded gradient is one sum of d+2 values)."""
     B = prob.B if B is None else int(B)
     f = fit(prob, B)
     cv = _Cov(prob)
@@ -409,7 +414,7 @@ def loglik_grad(prob, B: int | None = None) -> tuple[float, np.ndarray]:
         Vdir = Rinv @ (np.outer(e[idx], beta) - Vt[idx] @ Cinv)
         return G, Vdir
 
-    for m in range(M):
+    for m in (range(M) if windows is None else windows):
         last = min(m + B, M - 1)
         W = np.arange(ptr[m], ptr[last + 1])
         G, Vdir = win_terms(W)

@@ -80,6 +80,7 @@ class Model:
     handle: int
     n_blocks: int
     s: int
+    d: int = 0
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -98,7 +99,7 @@ def lma_fit(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, jitter=1e-
                               precision, stream, keep)
     h = C.c_void_p()
     _abi.check(lib.lma_fit(C.byref(prob), C.byref(hyp), C.byref(opt), C.byref(h)))
-    return Model(h.value, prob.m_blocks, prob.s)
+    return Model(h.value, prob.m_blocks, prob.s, prob.d)
 
 
 def lma_predict(model: Model, XU, test_block_ptr, noisy: bool = True, out=None):
@@ -173,7 +174,7 @@ def lma_fit_predict(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, XU
     _abi.check(lib.lma_fit_predict(C.byref(prob), C.byref(hyp), C.byref(opt), u, xp, tp, int(bool(noisy)), int(dev),
                                    mp, vp, C.byref(h) if keep_model else None))
     if keep_model:
-        return m, v, Model(h.value, prob.m_blocks, prob.s)
+        return m, v, Model(h.value, prob.m_blocks, prob.s, prob.d)
     return m, v
 
 
@@ -181,6 +182,16 @@ def lma_model_loglik(model: Model) -> float:
     out = C.c_double()
     _abi.check(_abi.load().lma_model_loglik(model.handle, C.byref(out)))
     return out.value
+
+
+def lma_model_loglik_grad(model: Model) -> np.ndarray:
+    """Gradient of the model's log-likelihood over (log l_1..d, log sigma_s,
+    log sigma_n) from the windows of its own blocks (all of them for lma_fit;
+    a shard's part, which sums over the shards, for lma_fit_local after
+    lma_model_set_global).  See lma_model_loglik_grad in lma.h."""
+    g = np.empty(model.d + 2)
+    _abi.check(_abi.load().lma_model_loglik_grad(model.handle, g.ctypes.data))
+    return g
 
 
 def lma_model_summary(model: Model):
@@ -203,7 +214,7 @@ def lma_fit_local(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, win_
     h = C.c_void_p()
     _abi.check(lib.lma_fit_local(C.byref(prob), C.byref(hyp), C.byref(opt), int(win_begin), int(own_begin),
                                  int(own_end), C.byref(h)))
-    return Model(h.value, prob.m_blocks, prob.s)
+    return Model(h.value, prob.m_blocks, prob.s, prob.d)
 
 
 def lma_model_local_summary(model: Model, device=None):

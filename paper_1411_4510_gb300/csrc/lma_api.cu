@@ -389,6 +389,19 @@ lma_status lma_loglik_grad(const lma_problem* P, const lma_hyper* H, const lma_o
   return st;
 }
 
+lma_status lma_model_loglik_grad(lma_model* md, double* grad) {
+  if (!md || !grad) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  ModelCore& mc = md->core;
+  if (!mc.have_global) return fail(LMA_ERR_INVALID_ARG, "the model's global step is not done (lma_model_set_global)");
+  return guarded([&] {
+    const int64_t k_lo = mc.own_b - mc.w0, k_hi = mc.own_e - mc.w0;
+    if (mc.prec == LMA_MIXED)
+      Impl<float>::grad_windows(mc, k_lo, k_hi, grad);
+    else
+      Impl<double>::grad_windows(mc, k_lo, k_hi, grad);
+  });
+}
+
 lma_precision lma_model_precision(const lma_model* md) { return md ? md->core.prec : LMA_FP64; }
 
 lma_status lma_model_summary(const lma_model* md, double* A_out, double* y_out, double* sc) {

@@ -265,12 +265,14 @@ __global__ void __launch_bounds__(NT) k_grad_gv(const Win* __restrict__ wins, co
 // Gather the per-window contributions onto training rows (fixed window order):
 //   PsiT[k][p] = sum_{m: p in W_m} (Phi_W - pad Phi_B)[k][i_m(p)]     k in [0, s]
 //   GVT[k][p]  = sum_{m: p in W_m} GVt_m[k][i_m(p)]                   k in [0, s)
+// over the windows of the gradient only: window of block m is wins[m - w0],
+// taken when m - w0 is in [k_lo, k_hi), its backward layout gw[m - w0 - k_lo].
 // (grid: x over rows p, y over k in [0, 2s+1))
 template <typename T>
 __global__ void k_grad_gather(const Win* __restrict__ wins, const GWin* __restrict__ gw,
                               const int64_t* __restrict__ bptr, int M, int B, int64_t n, int s,
                               const T* __restrict__ Q, const T* __restrict__ GV, T* __restrict__ PsiT,
-                              T* __restrict__ GVT) {
+                              T* __restrict__ GVT, int w0, int k_lo, int k_hi) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (p >= n) return;
@@ -283,8 +285,10 @@ __global__ void k_grad_gather(const Win* __restrict__ wins, const GWin* __restri
   const int j = lo;
   double acc = 0.0;
   for (int m = max(0, j - B); m <= j; ++m) {
-    const Win w = wins[m];
-    const GWin g = gw[m];
+    const int wi = m - w0;  // window index in the model
+    if (wi < k_lo || wi >= k_hi) continue;
+    const Win w = wins[wi];
+    const GWin g = gw[wi - k_lo];
     const int i = (int)(w.g_end - 1 - p);
     if (k <= s) {
       const T* Qw = Q + g.q;

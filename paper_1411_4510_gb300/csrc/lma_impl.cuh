@@ -212,6 +212,7 @@ struct ModelCore {
   double* ss64 = nullptr;     // s*d scaled support inputs (FP64)
   int npS = 0;
   int64_t w0 = 0;             // block index of the first window (partitioned fits)
+  int64_t own_b = 0, own_e = 0;  // blocks whose local summaries this model holds
   bool have_global = false;   // global step done (prediction possible)
   // device status words, checked once at the end of a call:
   // [0] Sigma_SS pivot failure (+1 column), [1] I + A pivot failure,
@@ -268,6 +269,8 @@ struct Impl {
                           const int64_t* tptr, int noisy, int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);
   static void loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad);
+  // gradient terms of windows [k_lo, k_hi) of a model with its global step done (d+2 doubles, host)
+  static void grad_windows(ModelCore& mc, int64_t k_lo, int64_t k_hi, double* grad);
   static void setup_attributes();
 };
 

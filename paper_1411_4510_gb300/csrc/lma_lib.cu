@@ -589,6 +589,8 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     if (ft) trows = fused_test_rows(mc.M, mc.B, ft->tptr);
     make_windows(mc.bptr, mc.B, s, sizeof(T), mc.wins, bufe, dinve, ewe, w_begin, own_end, ft ? &trows : nullptr);
     mc.w0 = w_begin;
+    mc.own_b = own_begin;
+    mc.own_e = own_end;
     const int64_t M = (int64_t)mc.wins.size();  // windows of this fit
     T* wbuf = mc.keep.alloc<T>(bufe);
     T* dinv = mc.keep.alloc<T>(dinve);
@@ -685,8 +687,8 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       }
       float* shi = tmp.alloc<float>((size_t)nown * se * kmax);
       float* slo = tmp.alloc<float>((size_t)nown * se * kmax);
-      launch("k_split_summary", k_split_summary, dim3(nblk(kmax), (unsigned)se, (unsigned)nown), NT, 0, st, wown,
-             (const float*)wbuf, se, kmax, shi, slo);
+      launch("k_split_summary", k_split_summary, dim3((unsigned)((se + 3) / 4), (unsigned)nown), dim3(64, 4), 0, st,
+             wown, (const float*)wbuf, se, kmax, shi, slo);
       const CUtensorMap sh = rows_tensor_map(shi, nown * se, kmax), sl = rows_tensor_map(slo, nown * se, kmax);
       int2* tld = tmp.alloc<int2>(tl.size());
       stage_copy(tld, tl.data(), sizeof(int2) * tl.size(), st);
@@ -1297,19 +1299,30 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
 template <typename T>
 void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* H, double* ll, double* grad) {
   fit(mc, P, H);
+  grad_windows(mc, 0, (int64_t)mc.wins.size(), grad);
+  *ll = mc.loglik;
+}
+
+// The adjoint restricted to windows [k_lo, k_hi) of the model: their
+// G_m terms and the chain of their Vt-bar contributions through K_DS and
+// L_SS.  Every step after the window terms is linear in them, so the parts
+// of a partition of the windows add up to the whole gradient.
+template <typename T>
+void Impl<T>::grad_windows(ModelCore& mc, int64_t k_lo, int64_t k_hi, double* grad) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
   try {
-    const int64_t n = mc.n, s = mc.s, M = mc.M;
+    const int64_t n = mc.n, s = mc.s, M = k_hi - k_lo;
     const int d = (int)mc.d;
     const int si = (int)s;
+    const Win* wk = mc.wins_d + k_lo;  // the windows of this gradient, indexed from 0
     // per-window backward layout
     std::vector<GWin> gw(M);
     int64_t qe = 0, ge = 0, gve = 0;
     int maxnt = 0, maxrows = 0;
     for (int64_t m = 0; m < M; ++m) {
-      const Win& w = mc.wins[m];
+      const Win& w = mc.wins[k_lo + m];
       GWin g{};
       g.nrows = 2 * (si + 1) + (w.n - w.nB);
       g.q = qe;
@@ -1338,16 +1351,16 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     double* pG = nullptr;
     if (tc) {
       const unsigned st128 = nblk(s, 128);
-      launch("k_grad_rhs_tc", k_grad_rhs_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, mc.wins_d,
+      launch("k_grad_rhs_tc", k_grad_rhs_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, wk,
              gwd, (const float*)wbuf, (const float*)mc.LcT, si, (float*)Q, tc_err);
-      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, wk, gwd,
              (const T*)mc.ew, si, Q);
       std::vector<int2> it_sw;
       std::vector<int4> it_g;
       for (int64_t m = 0; m < M; ++m) {
         const int nrt = (gw[m].nrows + 127) / 128;
         for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
-        const int np = mc.wins[m].npad;
+        const int np = mc.wins[k_lo + m].npad;
         for (int I = 0; I * 128 < np; ++I)
           for (int J = 0; J * 64 < np && J * 64 <= 128 * I + 127; ++J) it_g.push_back(make_int4((int)m, I, J, 0));
       }
@@ -1356,23 +1369,23 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
       stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
       stage_copy(ig, it_g.data(), sizeof(int4) * it_g.size(), st);
       launch("k_bwd_sweep_tc", k_bwd_sweep_tc, dim3((unsigned)it_sw.size()), 256, tc_chol_smem(), st,
-             (const int2*)isw, mc.wins_d, gwd, (const float*)wbuf, (const float*)mc.dinv, (float*)Q, tc_err);
+             (const int2*)isw, wk, gwd, (const float*)wbuf, (const float*)mc.dinv, (float*)Q, tc_err);
       n_g = it_g.size();
       pG = tmp.alloc<double>(n_g * np2);
-      launch("k_grad_G_tc", k_grad_G_tc, dim3((unsigned)n_g), 256, tc_chol_smem(), st, (const int4*)ig, mc.wins_d,
+      launch("k_grad_G_tc", k_grad_G_tc, dim3((unsigned)n_g), 256, tc_chol_smem(), st, (const int4*)ig, wk,
              gwd, (const float*)Q, (const float*)mc.xsT, d, si, (float)mc.ss2, mc.sn2, (float*)Gb, pG, tc_err);
-      launch("k_grad_gv_tc", k_grad_gv_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, mc.wins_d,
+      launch("k_grad_gv_tc", k_grad_gv_tc, dim3(maxnt, st128, (unsigned)M), 256, tc_chol_smem(), st, wk,
              gwd, (const float*)Gb, (const float*)mc.Vt, si, (float*)GV, tc_err);
     } else {
-      launch("k_grad_rhs", k_grad_rhs<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd, wbuf,
+      launch("k_grad_rhs", k_grad_rhs<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, wk, gwd, wbuf,
              (const T*)mc.LcT, si, Q);
-      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+      launch("k_grad_rhs_fill", k_grad_rhs_fill<T>, dim3(64, (unsigned)M), NT, 0, st, wk, gwd,
              (const T*)mc.ew, si, Q);
       std::vector<int2> it_sw, it_g;
       for (int64_t m = 0; m < M; ++m) {
         const int nrt = (gw[m].nrows + TB - 1) / TB;
         for (int ut = 0; ut < nrt; ++ut) it_sw.push_back(make_int2((int)m, ut));
-        const int nt = mc.wins[m].npad / TB;
+        const int nt = mc.wins[k_lo + m].npad / TB;
         for (int t = 0; t < nt * (nt + 1) / 2; ++t) it_g.push_back(make_int2((int)m, t));
       }
       int2* isw = tmp.alloc<int2>(it_sw.size());
@@ -1380,20 +1393,21 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
       stage_copy(isw, it_sw.data(), sizeof(int2) * it_sw.size(), st);
       stage_copy(ig, it_g.data(), sizeof(int2) * it_g.size(), st);
       launch("k_bwd_sweep", k_bwd_sweep<T>, dim3((unsigned)it_sw.size()), NT, sizeof(CholSmem<T>), st, isw,
-             mc.wins_d, gwd, wbuf, (const T*)mc.dinv, Q);
+             wk, gwd, wbuf, (const T*)mc.dinv, Q);
       n_g = it_g.size();
       pG = tmp.alloc<double>(n_g * np2);
-      launch("k_grad_G", k_grad_G<T>, dim3((unsigned)n_g), NT, 0, st, ig, mc.wins_d, gwd, (const T*)Q,
+      launch("k_grad_G", k_grad_G<T>, dim3((unsigned)n_g), NT, 0, st, ig, wk, gwd, (const T*)Q,
              (const T*)mc.xsT, d, si, mc.ss2, mc.sn2, Gb, pG);
-      launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, mc.wins_d, gwd,
+      launch("k_grad_gv", k_grad_gv<T>, dim3(maxnt, nblk(s, TB), (unsigned)M), NT, 0, st, wk, gwd,
              (const T*)Gb, (const T*)mc.Vt, si, GV);
     }
-    int64_t* bptr_d = tmp.alloc<int64_t>(M + 1);
-    stage_copy(bptr_d, mc.bptr.data(), sizeof(int64_t) * (M + 1), st);
+    int64_t* bptr_d = tmp.alloc<int64_t>(mc.M + 1);
+    stage_copy(bptr_d, mc.bptr.data(), sizeof(int64_t) * (mc.M + 1), st);
     T* PsiT = tmp.alloc<T>((s + 1) * n);
     T* GVT = tmp.alloc<T>(s * n);
     launch("k_grad_gather", k_grad_gather<T>, dim3(nblk(n), (unsigned)(2 * s + 1)), NT, 0, st, mc.wins_d, gwd,
-           bptr_d, (int)M, (int)mc.B, n, si, (const T*)Q, (const T*)GV, PsiT, GVT);
+           bptr_d, (int)mc.M, (int)mc.B, n, si, (const T*)Q, (const T*)GV, PsiT, GVT, (int)mc.w0, (int)k_lo,
+           (int)k_hi);
     T* VbT = tmp.alloc<T>(s * n);
     launch("k_grad_vbar", k_grad_vbar<T>, dim3(nblk(n, TB), nblk(s, TB)), NT, 0, st, (const T*)PsiT,
            (const T*)GVT, (const T*)mc.LcT, mc.beta, n, si, VbT);
@@ -1448,7 +1462,6 @@ void Impl<T>::loglik_grad(ModelCore& mc, const lma_problem* P, const lma_hyper* 
     for (const auto* v : {&h1, &h2, &h3})
       for (size_t i = 0; i < v->size(); i += np2)
         for (int q = 0; q < np2; ++q) grad[q] += (*v)[i + q];
-    *ll = mc.loglik;
     tmp.release();
   } catch (...) {
     tmp.release();

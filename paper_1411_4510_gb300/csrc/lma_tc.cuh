@@ -1637,15 +1637,33 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __res
 // [0, n - nB) of (hi, lo), row length kmax (a multiple of 32, zero pad).
 __global__ void k_split_summary(const Win* __restrict__ wins, const float* __restrict__ buf, int se, int kmax,
                                 float* __restrict__ hi, float* __restrict__ lo) {
-  const Win w = wins[blockIdx.z];
-  const int e = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= kmax) return;
-  const float x = (j < w.n - w.nB) ? buf[w.base + (int64_t)(w.npad + e) * w.npad + w.nB + j] : 0.f;
-  const float h = tc::tf32_round(x);
-  const int64_t o = ((int64_t)blockIdx.z * se + e) * kmax + j;
-  hi[o] = h;
-  lo[o] = tc::tf32_round(x - h);
+  // block (x, window y): rows e = 4 x + threadIdx.y, four values per thread
+  // and step (16-byte loads when the row's first value is aligned)
+  const Win w = wins[blockIdx.y];
+  const int e = blockIdx.x * blockDim.y + threadIdx.y;
+  if (e >= se) return;
+  const int nb = w.n - w.nB;
+  const float* src = buf + w.base + (int64_t)(w.npad + e) * w.npad + w.nB;
+  const bool al = (w.nB & 3) == 0;
+  const int64_t o = ((int64_t)blockIdx.y * se + e) * kmax;
+  for (int j = 4 * threadIdx.x; j < kmax; j += 4 * blockDim.x) {
+    float4 x;
+    if (al && j + 3 < nb) {
+      x = *reinterpret_cast<const float4*>(src + j);
+    } else {
+      x.x = j < nb ? src[j] : 0.f;
+      x.y = j + 1 < nb ? src[j + 1] : 0.f;
+      x.z = j + 2 < nb ? src[j + 2] : 0.f;
+      x.w = j + 3 < nb ? src[j + 3] : 0.f;
+    }
+    float4 h, l;
+    h.x = tc::tf32_round(x.x); l.x = tc::tf32_round(x.x - h.x);
+    h.y = tc::tf32_round(x.y); l.y = tc::tf32_round(x.y - h.y);
+    h.z = tc::tf32_round(x.z); l.z = tc::tf32_round(x.z - h.z);
+    h.w = tc::tf32_round(x.w); l.w = tc::tf32_round(x.w - h.w);
+    *reinterpret_cast<float4*>(hi + o + j) = h;
+    *reinterpret_cast<float4*>(lo + o + j) = l;
+  }
 }
 
 // Gram of the local summaries on the tensor cores (mixed form), one

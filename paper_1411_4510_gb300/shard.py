@@ -131,3 +131,26 @@ def sharded_fit(args: dict, sh: Shard, group=None, device=None, precision=api.MI
     G, logdet = reduce(G, logdet, group)
     set_global(model, G, logdet, int(np.asarray(args["block_ptr"])[-1]))
     return model
+
+
+def allreduce_vec(v, group=None):
+    """Sum a host vector over the ranks of `group` (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if group is None and not (dist.is_available() and dist.is_initialized()):
+        return np.asarray(v)
+    t = torch.as_tensor(np.asarray(v, dtype=np.float64))
+    if dist.get_backend(group) == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t.cpu().numpy()
+
+
+def sharded_loglik_grad(model, group=None, model_grad=None, reduce=allreduce_vec):
+    """Gradient of the whole problem's log-likelihood from a shard's model
+    (sharded_fit): the adjoint of the shard's own windows, then one
+    all-reduce of the d+2 values (the adjoint is linear in the window terms
+    after them).  Returns the whole gradient on every rank."""
+    model_grad = model_grad or api.lma_model_loglik_grad
+    return reduce(model_grad(model), group)
+

@@ -105,3 +105,58 @@ def test_predict_needs_global_and_windows(L):
     tp[3:] = 1
     with pytest.raises(L.LMAError):
         L.lma_predict(m, p.XU[:1], tp)
+
+
+@pytest.mark.parametrize("prec,tol_whole,tol_oracle", [("FP64", 1e-11, 1e-9), ("MIXED", 5e-5, 1.5e-3)])
+@pytest.mark.parametrize("B,world", [(1, 2), (2, 3)])
+def test_sharded_gradient_adds_up(L, prec, tol_whole, tol_oracle, B, world):
+    """lma_model_loglik_grad of each shard's model (its own windows' part of
+    the adjoint) summed over the shards: the whole problem's gradient.
+
+    Mixed bounds about three times the measurement: the shards' sum differs
+    from the whole mixed gradient by 1.1e-5 element-wise (their global
+    summaries are summed in another order and their edge windows compute the
+    residual tiles the whole fit copies, so beta and L_C move in the last FP32
+    bits, which the gradient's cancellation amplifies), and both are 4.6e-4
+    from the oracle on this C2-recipe case (|S| = 100, sigma_s^2 / sigma_n^2
+    = 400)."""
+    import torch
+    from oracle import lma_oracle as O2
+    from paper_1411_4510_gb300 import api, shard
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=B)
+    args = L.problem_args(p)
+    precision = getattr(L, prec)
+    ll_whole, g_whole = L.lma_loglik_grad(precision=precision, **args)
+    shards = [shard.plan(p.block_ptr, B, world, r) for r in range(world)]
+    models, G, ld = [], None, 0.0
+    for sh in shards:
+        sub = shard.sub_problem(args, sh)
+        m = api.lma_fit_local(**sub, win_begin=0, own_begin=sh.own_begin, own_end=sh.own_end, precision=precision)
+        assert L.lma_model_precision(m) == precision
+        g, l = api.lma_model_local_summary(m, device=torch.device("cuda:0"))
+        G = g if G is None else G + g
+        ld += l
+        models.append(m)
+    total = 0.0
+    for m in models:
+        api.lma_model_set_global(m, G, ld, p.block_ptr[-1])
+        total = total + L.lma_model_loglik_grad(m)
+    t = f"shard_grad_b{B}_w{world}_{prec.lower()}"
+    check(t, "grad vs whole", total, g_whole, tol_whole, tol_whole)
+    _, g_o = O2.loglik_grad(p)
+    check(t, "grad vs oracle", total, g_o, tol_oracle, tol_oracle)
+
+
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-12), ("MIXED", 1e-6)])
+def test_model_gradient_equals_loglik_grad(L, prec, tol):
+    """lma_model_loglik_grad on a model of lma_fit repeats lma_loglik_grad
+    without refitting."""
+    from workloads import make_problem
+    p = make_problem("C2", N=3200, M=16, s=100, U=400, B=1)
+    args = L.problem_args(p)
+    precision = getattr(L, prec)
+    ll, g = L.lma_loglik_grad(precision=precision, **args)
+    m = L.lma_fit(precision=precision, **args)
+    check(f"model_grad_{prec.lower()}", "grad", L.lma_model_loglik_grad(m), g, tol, tol)
+

@@ -139,6 +139,21 @@ def test_grad_central_fd(case):
     assert np.allclose(g, fd, rtol=1e-6, atol=1e-6 * max(1.0, np.max(np.abs(fd))))
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[4]])
+def test_grad_partition_of_windows_adds_up(case):
+    """The adjoint is linear in the window terms after the window loop, so
+    the gradients restricted to the windows of a partition of the blocks add
+    up to the whole gradient (the sharded gradient's single reduction)."""
+    p = _p(*case)
+    _, g = O2.loglik_grad(p)
+    M = len(p.block_ptr) - 1
+    cuts = sorted({0, M // 3, (2 * M) // 3, M})
+    parts = [O2.loglik_grad(p, windows=range(a, b))[1] for a, b in zip(cuts, cuts[1:])]
+    assert np.allclose(sum(parts), g, rtol=1e-10, atol=1e-10 * np.max(np.abs(g)))
+    _, g_all = O2.loglik_grad(p, windows=range(M))
+    assert np.array_equal(g_all, g)
+
+
 def test_grad_full_gp_closed_form():
     """At B = M-1 the LMA likelihood is the exact GP one, whose gradient is
     1/2 tr((a a^T - K^-1) dK/dtheta), a = K^-1 (y - mu)."""

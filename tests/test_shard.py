@@ -131,6 +131,10 @@ def _rank_main(rank, world, port, B, out_path):
         model = shard.sharded_fit(_args(p), sh, fit_local=_oracle_fit_local, local_summary=_oracle_local_summary,
                                   set_global=_oracle_set_global)
         np.save(f"{out_path}.{rank}.npy", np.concatenate([[model["loglik"]], np.asarray(model["G"]).ravel()]))
+        # the shard's part of the gradient (the oracle's adjoint restricted to
+        # the windows of its blocks) and the all-reduce of the d+2 values
+        grad = shard.sharded_loglik_grad(model, model_grad=lambda m: O2.loglik_grad(p, windows=range(sh.m0, sh.m1))[1])
+        np.save(f"{out_path}.grad.{rank}.npy", grad)
     finally:
         dist.destroy_process_group()
 
@@ -155,3 +159,7 @@ def test_sharded_fit_two_gloo_ranks(tmp_path, B):
         G = v[1:].reshape(p.S.shape[0] + 1, -1)
         assert np.allclose(0.5 * (G[1:, 1:] + G[1:, 1:].T), f.A_white, rtol=1e-10, atol=1e-12)
         assert G[0, 0] == pytest.approx(f.quad, rel=1e-11)
+    _, g = O2.loglik_grad(p)
+    for r in range(world):
+        gr = np.load(f"{out}.grad.{r}.npy")
+        assert np.allclose(gr, g, rtol=1e-10, atol=1e-10 * np.max(np.abs(g)))
