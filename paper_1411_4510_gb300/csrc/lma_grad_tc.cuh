@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(256, 2) k_grad_G_tc(const int4* __restrict__ i
     for (int q = 0; q < MAXD; ++q) xr[q] = (q < d && gi < w.n) ? xs[(w.g_end - 1 - gi) * d + q] : 0.f;
     float* G = Gbuf + g.g;
     if (gi < w.npad) {
+      // the thread's 32 terms are summed in FP32 (a short sum of products
+      // that are themselves FP32), then added to the FP64 sums once
+      float glf[MAXD];
+#pragma unroll
+      for (int q = 0; q < MAXD; ++q) glf[q] = 0.f;
+      float gsf = 0.f;
       for (int j = 0; j < 32; ++j) {
         const int gj = c0 + cb + j;
         if (gj > gi) break;
@@ -253,12 +259,12 @@ __global__ void __launch_bounds__(256, 2) k_grad_G_tc(const int4* __restrict__ i
             const float t = xr[q] - xc[cb + j][q];
             d2 = fmaf(t, t, d2);
           }
-          const double kg = (double)val * (double)(ss2 * expf(-0.5f * d2)) * (gi == gj ? 1.0 : 2.0);
+          const float kg = val * ss2 * expf(-0.5f * d2) * (gi == gj ? 1.f : 2.f);
           for (int q = 0; q < d; ++q) {
             const float t = xr[q] - xc[cb + j][q];
-            gl[q] += kg * (double)(t * t);
+            glf[q] = fmaf(kg, t * t, glf[q]);
           }
-          gsig += 2.0 * kg;
+          gsf += kg;
           if (gi == gj) gnoise += 2.0 * sn2 * (double)val;
         } else {
           val = 0.f;
@@ -266,6 +272,8 @@ __global__ void __launch_bounds__(256, 2) k_grad_G_tc(const int4* __restrict__ i
         G[(int64_t)gi * ld + gj] = val;
         G[(int64_t)gj * ld + gi] = val;
       }
+      for (int q = 0; q < d; ++q) gl[q] += (double)glf[q];
+      gsig += 2.0 * (double)gsf;
     }
   }
   // block reduction of the d + 2 sums: warp shuffles, then one value per warp

@@ -417,6 +417,61 @@ __global__ void __launch_bounds__(NT) k_fill_ext(const Win* __restrict__ wins, c
   }
 }
 
+// k_fill_ext for FP32 windows with 16-byte accesses: block (x, y, window z)
+// transposes points [64 x, 64 x + 64) (reversed order) x support coordinates
+// k in [64 y, 64 y + 64) of V into extra rows 1 + k; y = ceil(s / 64) writes
+// row 0 (r).  Loads take four consecutive k of one point (scalar when the
+// row length s is not a multiple of 4), stores four consecutive columns.
+__global__ void __launch_bounds__(256) k_fill_ext4(const Win* __restrict__ wins, const float* __restrict__ Vt,
+                                                   const float* __restrict__ r, int s, float* __restrict__ buf) {
+  const Win w = wins[blockIdx.z];
+  const int c0 = blockIdx.x * 64;
+  if (c0 >= w.npad) return;
+  const int ky = (s + 63) / 64;
+  float* ext = buf + w.base + (int64_t)w.npad * w.npad;  // extra row e at ext + e * npad
+  const int t = threadIdx.x;
+  if ((int)blockIdx.y == ky) {  // row 0: r over the window's points
+    for (int c = t; c < 64; c += blockDim.x) {
+      const int i = c0 + c;
+      ext[c0 + c] = i < w.n ? r[w.g_end - 1 - i] : 0.f;
+    }
+    return;
+  }
+  const int k0 = blockIdx.y * 64;
+  __shared__ float tile[64][65];  // [point][k]
+  const bool vec = (s & 3) == 0;
+#pragma unroll
+  for (int rep = 0; rep < 4; ++rep) {
+    const int ci = (t >> 4) + 16 * rep, kq = (t & 15) * 4;
+    const int i = c0 + ci, k = k0 + kq;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < w.n) {
+      const float* src = Vt + (w.g_end - 1 - i) * (int64_t)s + k;
+      if (vec && k + 3 < s) {
+        v = *reinterpret_cast<const float4*>(src);
+      } else {
+        v.x = k < s ? src[0] : 0.f;
+        v.y = k + 1 < s ? src[1] : 0.f;
+        v.z = k + 2 < s ? src[2] : 0.f;
+        v.w = k + 3 < s ? src[3] : 0.f;
+      }
+    }
+    tile[ci][kq] = v.x;
+    tile[ci][kq + 1] = v.y;
+    tile[ci][kq + 2] = v.z;
+    tile[ci][kq + 3] = v.w;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int rep = 0; rep < 4; ++rep) {
+    const int kk = (t >> 4) + 16 * rep, cq = (t & 15) * 4;
+    const int k = k0 + kk;
+    if (k < s)
+      *reinterpret_cast<float4*>(ext + (int64_t)(1 + k) * w.npad + c0 + cq) =
+          make_float4(tile[cq][kk], tile[cq + 1][kk], tile[cq + 2][kk], tile[cq + 3][kk]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Left-looking blocked Cholesky sweep, one 64-wide column panel kp per
 // launch pair.  k_chol_step: for every row tile i >= kp of every window,

@@ -649,7 +649,8 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
         launch("k_copy_shared_tiles", k_copy_shared_tiles<float>, dim3((unsigned)maxL, (unsigned)M), NT, 0, st,
                (const Win*)wd, (int)M, (int)mc.B, (const int*)Lsd, (float*)wbuf);
       }
-      launch("k_fill_ext", k_fill_ext<T>, dim3(maxnt, et, (unsigned)M), NT, 0, st, wd, Vt, rT, (int)s, wbuf);
+      launch("k_fill_ext", k_fill_ext4, dim3(maxnt, (unsigned)((s + 63) / 64 + 1), (unsigned)M), 256, 0, st,
+             (const Win*)wd, (const float*)Vt, (const float*)rT, (int)s, (float*)wbuf);
     } else if (batched) {
       launch("k_resid", k_resid<T>, dim3(maxnt * (maxnt + 1) / 2, (unsigned)M), NT, 0, st, wd, xsT, d, Vt, (int)s, (T)mc.ss2,
                                                                           (T)mc.sn2, wbuf);
