@@ -150,8 +150,8 @@ def kernel_work(p, B, fused=True):
     # the panel steps' update (columns [kh, k0), at most 64) and the panel
     # solves run in one kernel, k_chol_panel2_tc; k_chol_step_tc only
     # factorises the first diagonal block of each 128-column group
-    return {"k_chol_panel2_tc": step + tri, "k_chol_wide": wide, "k_chol_mid": mid, "k_resid_tc": resid,
-            "k_gram_split": gram, "k_pred_rhs_tc": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
+    return {"k_chol_panel2_tc": step + tri, "k_chol_wide": wide, "k_chol_mid": mid, "k_resid_bf6": resid,
+            "k_gram_bf6": gram, "k_pred_rhs_bf6": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
             "k_proj_tc": proj, "k_var_gemm": var,
             "k_f64_chain": f64, **({} if fused else {"k_pred_sweep_tc": psweep})}
 
@@ -184,10 +184,10 @@ def sources_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-TENSOR_KERNELS = {"k_chol_panel2_tc", "k_chol_wide", "k_chol_mid", "k_pred_sweep_tc", "k_resid_tc",
-                  "k_gram_split", "k_pred_rhs_tc", "k_pred_accum_tc", "k_bwd_sweep_tc", "k_grad_G_tc",
+TENSOR_KERNELS = {"k_chol_panel2_tc", "k_chol_wide", "k_chol_mid", "k_pred_sweep_tc",
+                  "k_pred_accum_tc", "k_bwd_sweep_tc", "k_grad_G_tc",
                   "k_grad_gv_tc", "k_grad_rhs_tc"}
-BF16X6_KERNELS = {"k_proj_tc"}   # bfloat16 x 6 split products (the variance term shares the name k_var_gemm)
+BF16X6_KERNELS = {"k_proj_tc", "k_gram_bf6", "k_resid_bf6", "k_pred_rhs_bf6"}   # bfloat16 x 6 split products (the variance term shares the name k_var_gemm)
 FP64_KERNELS = {"k_f64_chain"}
 # launches of the FP64 factorisations (whichever form the tuner chose), reported as one entry
 F64_CHAIN = ("k_f64_potrf", "k_f64_panel", "k_f64_solve2", "k_f64_coop", "k_f64_flow")

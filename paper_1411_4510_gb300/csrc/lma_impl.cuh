@@ -194,9 +194,8 @@ struct ModelCore {
   void* ssT = nullptr;        // s*d scaled support inputs (T)
   void* ET = nullptr;         // s*s, ET[k][i] = (L_SS^-1)[i][k]   (T)
   void* Vt = nullptr;         // n*s whitened support coordinates  (T)
-  float* vhi = nullptr;       // TF32 halves of Vt in reversed point order, row length ldvs
-  float* vlo = nullptr;       //   (mixed form on the tensor cores only)
-  int ldvs = 0;
+  uint16_t* vb3 = nullptr;    // three bfloat16 planes of Vt in reversed point order, row length
+  int ldvs = 0;               //   ldvs (a multiple of 64; mixed form on the tensor cores only)
   void* wbuf = nullptr;       // window buffers (T)
   void* dinv = nullptr;       // inverted diagonal tiles (T)
   void* ew = nullptr;         // per-window L^-1 e (T)

@@ -115,7 +115,6 @@ static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack
 template <int BN>
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, BN>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
-static size_t split_smem_bytes() { return sizeof(SplitSmem) + tc::kTcAlignSlack; }
 
 // Grid of a persistent kernel with one CTA per SM: min(items, SM count).
 static unsigned persistent_grid(size_t items) {
@@ -141,30 +140,6 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   });
   return fn;
-}
-
-// Tensor map of a row-major FP32 matrix (rows x cols, cols a multiple of 32,
-// 16-byte-aligned base): 32 x 128 boxes with the 128-byte swizzle the MMA
-// descriptors expect; rows outside [0, rows) read zero.
-static CUtensorMap rows_tensor_map(const float* base, int64_t rows, int cols) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) {
-    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    throw Fail{};
-  }
-  CUtensorMap m;
-  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)cols * sizeof(float)};
-  cuuint32_t box[2] = {32, 128};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    fail(LMA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    throw Fail{};
-  }
-  return m;
 }
 
 // Tensor map of row-major bfloat16 planes (rows x cols, cols a multiple of
@@ -235,19 +210,13 @@ static void project(const ModelCore& mc, const T* xsP, int64_t npts, T* out, Are
   tmp.free_one(Kds);
 }
 
-// TF32 hi/lo halves (k_split_tf32) of the point-major rows of V (n x s) with
-// the row length padded to ld = s rounded up to 32 (zero pad), reversed or not.
-static void split_rows(cudaStream_t st, const float* V, int64_t n, int64_t s, int ld, bool reverse, float* hi,
-                       float* lo, Arena& tmp) {
-  const float* src = V;
-  if (ld != s) {
-    float* pad = tmp.alloc<float>((size_t)n * ld);
-    LMA_CK(cudaMemsetAsync(pad, 0, sizeof(float) * n * ld, st));
-    LMA_CK(cudaMemcpy2DAsync(pad, sizeof(float) * ld, V, sizeof(float) * s, sizeof(float) * s, n,
-                             cudaMemcpyDeviceToDevice, st));
-    src = pad;
-  }
-  launch("k_split_tf32", k_split_tf32, nblk(n * (ld / 4)), NT, 0, st, src, n, ld, reverse ? 1 : 0, hi, lo);
+// Three bfloat16 planes (k_split_bf3) of the point-major rows of V (n x s),
+// row length ld (s rounded up to 64, zero pad), reversed or not.
+static uint16_t* split_rows_bf3(cudaStream_t st, const float* V, int64_t n, int64_t s, int ld, bool reverse,
+                                uint16_t* out) {
+  launch("k_split_bf3", k_split_bf3, nblk(n * (ld / 8)), NT, 0, st, V, n, (int)s, (int64_t)s, ld, out,
+         reverse ? 1 : 0);
+  return out;
 }
 
 // Tensor cores for the mixed form's sweep; LMA_NO_TENSOR_CORES=1 selects the
@@ -278,11 +247,11 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_panel2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
-    cudaFuncSetAttribute(k_resid_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_resid_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_pred_rhs_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_pred_rhs_tc<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
-    cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes());
+    cudaFuncSetAttribute(k_gram_bf6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
+    cudaFuncSetAttribute(k_resid_bf6<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
+    cudaFuncSetAttribute(k_resid_bf6<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
+    cudaFuncSetAttribute(k_pred_rhs_bf6<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
+    cudaFuncSetAttribute(k_pred_rhs_bf6<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
     cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_accum_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<256>());
@@ -610,14 +579,13 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
     const T* xsT = (const T*)mc.xsT;
     const unsigned et = nblk(s + 1, TB);
     if (batched && sizeof(T) == 4 && use_tensor_cores()) {
-      // residual tiles on the tensor cores, fed by TMA from the TF32 halves
-      // of V (row length padded to 32) in reversed point order
-      const int sp = (int)roundup(s, 32);
+      // residual tiles on the tensor cores (bf16x6 products), fed by TMA from
+      // the three bfloat16 planes of V (row length padded to 64) in reversed
+      // point order
+      const int sp = (int)roundup(s, 64);
       mc.ldvs = sp;
-      mc.vhi = mc.keep.alloc<float>((size_t)n * sp);
-      mc.vlo = mc.keep.alloc<float>((size_t)n * sp);
-      split_rows(st, (const float*)Vt, n, s, sp, true, mc.vhi, mc.vlo, tmp);
-      const CUtensorMap vh = rows_tensor_map(mc.vhi, n, sp), vl = rows_tensor_map(mc.vlo, n, sp);
+      mc.vb3 = split_rows_bf3(st, (const float*)Vt, n, s, sp, true, mc.keep.alloc<uint16_t>((size_t)3 * n * sp));
+      const CUtensorMap vb = bf16_tensor_map(mc.vb3, 3 * n, sp);
       // tiles of window k inside its blanket's [0, L)^2 are copied from the
       // windows of the blanket's blocks afterwards (k_copy_shared_tiles)
       // instead of being recomputed; only where all those windows are in this fit
@@ -639,10 +607,9 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", pad_dim(d) == 8 ? k_resid_tc<8> : k_resid_tc<MAXD>, persistent_grid(items.size()),
-             kSplitThreads, split_smem_bytes(), st,
-             (const int4*)itd, (int)items.size(), wd, (const float*)xsT, d, vh, vl, (int)n, sp / 32, (float)mc.ss2, (float)mc.sn2,
-             (float*)wbuf, rerr);
+      launch("k_resid_bf6", pad_dim(d) == 8 ? k_resid_bf6<8> : k_resid_bf6<MAXD>, persistent_grid(items.size()),
+             bf6::NTHR, bf6::smem_bytes(), st, (const int4*)itd, (int)items.size(), (const Win*)wd, (const float*)xsT,
+             d, vb, (int)n, sp / bf6::KC, (float)mc.ss2, (float)mc.sn2, (float*)wbuf, rerr);
       if (maxL > 0) {
         int* Lsd = tmp.alloc<int>((size_t)M);
         stage_copy(Lsd, Ls.data(), sizeof(int) * M, st);
@@ -681,16 +648,16 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       const int nt = (se + 127) / 128;
       for (int I = 0; I < nt; ++I)
         for (int J = 0; J <= I; ++J) tl.push_back(make_int2(I, J));
-      int kmax = 32;
+      int kmax = bf6::KC;
       for (int64_t m = own_begin; m < own_end; ++m) {
         const Win& w = mc.wins[m - w_begin];
-        kmax = std::max(kmax, (int)roundup(w.n - w.nB, 32));
+        kmax = std::max(kmax, (int)roundup(w.n - w.nB, bf6::KC));
       }
-      float* shi = tmp.alloc<float>((size_t)nown * se * kmax);
-      float* slo = tmp.alloc<float>((size_t)nown * se * kmax);
-      launch("k_split_summary", k_split_summary, dim3((unsigned)((se + 3) / 4), (unsigned)nown), dim3(64, 4), 0, st,
-             wown, (const float*)wbuf, se, kmax, shi, slo);
-      const CUtensorMap sh = rows_tensor_map(shi, nown * se, kmax), sl = rows_tensor_map(slo, nown * se, kmax);
+      // the summary rows in three bfloat16 planes (bf16x6 products, lma_bf6.cuh)
+      uint16_t* sb3 = tmp.alloc<uint16_t>((size_t)3 * nown * se * kmax);
+      launch("k_split_summary", k_split_summary_bf3, dim3((unsigned)((se + 7) / 8), (unsigned)nown), dim3(32, 8), 0,
+             st, wown, (const float*)wbuf, se, (int)nown, kmax, sb3);
+      const CUtensorMap sb = bf16_tensor_map(sb3, 3 * nown * se, kmax);
       int2* tld = tmp.alloc<int2>(tl.size());
       stage_copy(tld, tl.data(), sizeof(int2) * tl.size(), st);
       // Window groups: item (tile, group) sums the group's windows; the
@@ -717,10 +684,10 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
       partial = tmp.alloc<double>((size_t)gmaxc * se * se);
       auto run = [&](int g) {
         const int c = (int)((nown + g - 1) / g);
-        launch("k_gram_split", k_gram_split, persistent_grid(tl.size() * g), kSplitThreads, split_smem_bytes(), st,
-               (const int2*)tld, (int)tl.size(), (int)nown, c, se, kmax, sh, sl, partial, tc_err);
+        launch("k_gram_bf6", k_gram_bf6, persistent_grid(tl.size() * g), bf6::NTHR, bf6::smem_bytes(), st,
+               (const int2*)tld, (int)tl.size(), (int)nown, c, se, kmax, sb, (int)(nown * se), partial, tc_err);
       };
-      const std::string key = "k_gram_split se=" + std::to_string(se) + " windows=" + std::to_string(nown) +
+      const std::string key = "k_gram_bf6 se=" + std::to_string(se) + " windows=" + std::to_string(nown) +
                               " k=" + std::to_string(kmax) + " sm=" + std::to_string(nsm);
       const int g = tune::pick(key, cands, (int)groups_of(gbest), st, run);
       chunk = (int)((nown + g - 1) / g);
@@ -913,7 +880,7 @@ void Impl<T>::fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* 
 
 template <typename T>
 void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
-  if (sizeof(T) != 4 || !mc.vhi) {
+  if (sizeof(T) != 4 || !mc.vb3) {
     fail(LMA_ERR_INTERNAL, "appended test rows need the mixed form on the tensor cores");
     throw Fail{};
   }
@@ -958,23 +925,20 @@ void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
   Pair* pd = tmp.alloc<Pair>(pairs.size());
   stage_copy(pd, pairs.data(), sizeof(Pair) * pairs.size(), st);
   const int sp = mc.ldvs;
-  float* uhi = tmp.alloc<float>((size_t)U * sp);
-  float* ulo = tmp.alloc<float>((size_t)U * sp);
-  split_rows(st, Vu, U, s, sp, false, uhi, ulo, tmp);
-  const CUtensorMap vh = rows_tensor_map(mc.vhi, mc.n, sp), vl = rows_tensor_map(mc.vlo, mc.n, sp);
-  const CUtensorMap uh = rows_tensor_map(uhi, U, sp), ul = rows_tensor_map(ulo, U, sp);
+  uint16_t* ub3 = split_rows_bf3(st, Vu, U, s, sp, false, tmp.alloc<uint16_t>((size_t)3 * U * sp));
+  const CUtensorMap vb = bf16_tensor_map(mc.vb3, 3 * mc.n, sp), ub = bf16_tensor_map(ub3, 3 * U, sp);
   std::vector<int4> it_r;
   for (size_t pi = 0; pi < pairs.size(); ++pi) {
-    const int nct = (mc.wins[pairs[pi].win].npad + RB - 1) / RB;
+    const int nct = (mc.wins[pairs[pi].win].npad + 127) / 128;
     for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut)
       for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
   }
   int4* irr = tmp.alloc<int4>(it_r.size());
   stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-  launch("k_pred_rhs_tc", pad_dim(d) == 8 ? k_pred_rhs_tc<8> : k_pred_rhs_tc<MAXD>, persistent_grid(it_r.size()),
-         kSplitThreads, split_smem_bytes(), st, pd, (const int4*)irr, (int)it_r.size(), mc.wins_d,
-         (const float*)mc.xsT, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n, sp / 32, (float)mc.ss2,
-         (float*)mc.wbuf, mc.flags + 2);
+  launch("k_pred_rhs_bf6", pad_dim(d) == 8 ? k_pred_rhs_bf6<8> : k_pred_rhs_bf6<MAXD>, persistent_grid(it_r.size()),
+         bf6::NTHR, bf6::smem_bytes(), st, (const Pair*)pd, (const int4*)irr, (int)it_r.size(),
+         (const Win*)mc.wins_d, (const float*)mc.xsT, (const float*)xu, d, ub, (int)U, vb, (int)mc.n, sp / bf6::KC,
+         (float)mc.ss2, (float*)mc.wbuf, mc.flags + 2);
 }
 
 template <typename T>
@@ -1050,33 +1014,27 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     } else if (mc.prec == LMA_MIXED) {
       const bool tc = (sizeof(T) == 4 && use_tensor_cores());
       if (tc) {
-        // right-hand sides on the tensor cores, fed by TMA from the TF32
-        // halves of Vu (test order) and of Vt (reversed point order)
-        const int sp = (int)roundup(s, 32);
-        float* vhi = mc.vhi;
-        float* vlo = mc.vlo;
-        if (!vhi || mc.ldvs != sp) {
-          vhi = tmp.alloc<float>((size_t)mc.n * sp);
-          vlo = tmp.alloc<float>((size_t)mc.n * sp);
-          split_rows(st, (const float*)Vt, mc.n, s, sp, true, vhi, vlo, tmp);
-        }
-        float* uhi = tmp.alloc<float>((size_t)U * sp);
-        float* ulo = tmp.alloc<float>((size_t)U * sp);
-        split_rows(st, (const float*)Vu, U, s, sp, false, uhi, ulo, tmp);
-        const CUtensorMap vh = rows_tensor_map(vhi, mc.n, sp), vl = rows_tensor_map(vlo, mc.n, sp);
-        const CUtensorMap uh = rows_tensor_map(uhi, U, sp), ul = rows_tensor_map(ulo, U, sp);
+        // right-hand sides on the tensor cores (bf16x6 products), fed by TMA
+        // from the bfloat16 planes of Vu (test order) and of Vt (reversed
+        // point order)
+        const int sp = (int)roundup(s, 64);
+        const uint16_t* vb3 = mc.vb3;
+        if (!vb3 || mc.ldvs != sp)
+          vb3 = split_rows_bf3(st, (const float*)Vt, mc.n, s, sp, true, tmp.alloc<uint16_t>((size_t)3 * mc.n * sp));
+        uint16_t* ub3 = split_rows_bf3(st, (const float*)Vu, U, s, sp, false, tmp.alloc<uint16_t>((size_t)3 * U * sp));
+        const CUtensorMap vb = bf16_tensor_map(vb3, 3 * mc.n, sp), ub = bf16_tensor_map(ub3, 3 * U, sp);
         std::vector<int4> it_r;
         for (size_t pi = 0; pi < pairs.size(); ++pi) {
-          const int nct = (mc.wins[pairs[pi].win].npad + RB - 1) / RB;
+          const int nct = (mc.wins[pairs[pi].win].npad + 127) / 128;
           for (int ut = 0; ut < (pairs[pi].nu + 127) / 128; ++ut)
             for (int ct = 0; ct < nct; ++ct) it_r.push_back(make_int4((int)pi, ut, ct, 0));
         }
         int4* irr = tmp.alloc<int4>(it_r.size());
         stage_copy(irr, it_r.data(), sizeof(int4) * it_r.size(), st);
-        launch("k_pred_rhs_tc", pad_dim(d) == 8 ? k_pred_rhs_tc<8> : k_pred_rhs_tc<MAXD>, persistent_grid(it_r.size()),
-               kSplitThreads, split_smem_bytes(), st,
-               pd, (const int4*)irr, (int)it_r.size(), mc.wins_d, (const float*)xs, (const float*)xu, d, uh, ul, vh, vl, (int)mc.n,
-               sp / 32, (float)mc.ss2, (float*)Pbuf, perr);
+        launch("k_pred_rhs_bf6", pad_dim(d) == 8 ? k_pred_rhs_bf6<8> : k_pred_rhs_bf6<MAXD>,
+               persistent_grid(it_r.size()), bf6::NTHR, bf6::smem_bytes(), st, (const Pair*)pd, (const int4*)irr,
+               (int)it_r.size(), (const Win*)mc.wins_d, (const float*)xs, (const float*)xu, d, ub, (int)U, vb,
+               (int)mc.n, sp / bf6::KC, (float)mc.ss2, (float*)Pbuf, perr);
       } else {
         launch("k_pred_rhs", k_pred_rhs<T>, (unsigned)it_rhs.size(), NT, 0, st, pd, ird, mc.wins_d, xs, xu, d, Vt, Vu,
                (int)s, (T)mc.ss2, Pbuf);
@@ -1169,7 +1127,7 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     if (sizeof(T) == 4 && mc.lcinv3) {  // L_C^-1 h on the tensor cores (bf16x6), then row norms
       uint16_t* hp = tmp.alloc<uint16_t>((size_t)3 * U * mc.ldk);
       launch("k_split_bf3", k_split_bf3, nblk(U * (mc.ldk / 8)), NT, 0, st, (const float*)h, U, (int)s, (int64_t)s,
-             mc.ldk, hp);
+             mc.ldk, hp, 0);
       float* g = tmp.alloc<float>((size_t)U * s);
       proj_tc(st, "k_var_gemm", hp, U, mc.lcinv3, mc.brows, (int)s, mc.ldk, g, s, perr);
       launch("k_row_sqnorm", k_row_sqnorm, nblk(U * 32), NT, 0, st, (const float*)g, U, (int)s, part);
@@ -1257,25 +1215,21 @@ void Impl<T>::window_residual(ModelCore& mc, const lma_problem* P, const lma_hyp
     const int nt = w.npad / TB;
     if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
       const int64_t s = mc.s, n = mc.n;
-      const int sp = (int)roundup(s, 32);
-      float* vhi = mc.vhi;
-      float* vlo = mc.vlo;
-      if (!vhi || mc.ldvs != sp) {
-        vhi = tmp.alloc<float>((size_t)n * sp);
-        vlo = tmp.alloc<float>((size_t)n * sp);
-        split_rows(st, (const float*)mc.Vt, n, s, sp, true, vhi, vlo, tmp);
-      }
-      const CUtensorMap vh = rows_tensor_map(vhi, n, sp), vl = rows_tensor_map(vlo, n, sp);
+      const int sp = (int)roundup(s, 64);
+      const uint16_t* vb3 = mc.vb3;
+      if (!vb3 || mc.ldvs != sp)
+        vb3 = split_rows_bf3(st, (const float*)mc.Vt, n, s, sp, true, tmp.alloc<uint16_t>((size_t)3 * n * sp));
+      const CUtensorMap vb = bf16_tensor_map(vb3, 3 * n, sp);
       std::vector<int4> items;
       for (int I = 0; I * 128 < w.npad; ++I)
         for (int J = 0; J * RB < w.npad && J * RB <= 128 * I + 127; ++J) items.push_back(make_int4(0, I, J, 0));
       int4* itd = tmp.alloc<int4>(items.size());
       int* rerr = mc.flags + 2;
       stage_copy(itd, items.data(), sizeof(int4) * items.size(), st);
-      launch("k_resid_tc", pad_dim((int)mc.d) == 8 ? k_resid_tc<8> : k_resid_tc<MAXD>, persistent_grid(items.size()),
-             kSplitThreads, split_smem_bytes(), st,
-             (const int4*)itd, (int)items.size(), wd, (const float*)mc.xsT, (int)mc.d, vh, vl, (int)n, sp / 32, (float)mc.ss2,
-             (float)mc.sn2, (float*)buf, rerr);
+      launch("k_resid_bf6", pad_dim((int)mc.d) == 8 ? k_resid_bf6<8> : k_resid_bf6<MAXD>,
+             persistent_grid(items.size()), bf6::NTHR, bf6::smem_bytes(), st, (const int4*)itd, (int)items.size(),
+             (const Win*)wd, (const float*)mc.xsT, (int)mc.d, vb, (int)n, sp / bf6::KC, (float)mc.ss2, (float)mc.sn2,
+             (float*)buf, rerr);
     } else {
       launch("k_resid", k_resid<T>, dim3(nt * (nt + 1) / 2, 1), NT, 0, st, wd, (const T*)mc.xsT, (int)mc.d,
              (const T*)mc.Vt, (int)mc.s, (T)mc.ss2, (T)mc.sn2, buf);

@@ -91,6 +91,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ---- descriptors -----------------------------------------------------------
 // K-major operand tile in shared memory with the 128-byte swizzle: rows of
 // 128 bytes (32 FP32/TF32 values of K), 8-row atoms 1024 bytes apart; the
@@ -1303,81 +1313,9 @@ __device__ bool comp_product(CompSmem<BN>& sm, CompState& cs, int kbeg, int kend
 }
 
 // ---------------------------------------------------------------------------
-// Compensated product with pre-split operands fed by TMA.  The TF32 hi/lo
-// halves of both operands are in global memory (k_split_tf32), so a
-// 128 x 128 output tile costs no conversion work on the SM: one producer
-// thread loads each 32-wide K chunk (four 128 x 32 boxes, 64 KB) into a ring
-// of kSplitStages stages, one thread issues the chunk's 12 MMAs
-// (hi.hi + hi.lo + lo.hi per 8-wide K step) into one of two tensor-memory
-// accumulators, and 16 worker warps drain an accumulator into (hi, lo) with
-// TwoSum every kSplitDrain chunks while the other one is being filled.
-// Draining every 64 values of K instead of every 32 (comp_product) halves
-// the SM's TwoSum work; the FP32 partial sums are twice as long, which moves
-// the predictive mean by a few per cent of its error against the FP64 form
-// (that error is dominated by the FP32 window factorisations).
-constexpr int kSplitStages = 3;
-constexpr int kSplitDrain = 2;
-constexpr int kSplitWorkers = 16;                        // 4 lane quarters x 4 groups of 32 columns
-constexpr int kSplitThreads = 32 * (kSplitWorkers + 2);  // + MMA warp + TMA warp
-struct SplitSmem {
-  tc::TcStage<128> st[kSplitStages];
-  uint64_t full[kSplitStages], empty[kSplitStages], done[2], drained[2], fin;
-  uint32_t tmem;
-  int abort;
-};
-__device__ __forceinline__ SplitSmem& split_smem(unsigned char* raw) {
-  uintptr_t p = reinterpret_cast<uintptr_t>(raw);
-  p = (p + 1023) & ~uintptr_t(1023);
-  return *reinterpret_cast<SplitSmem*>(p);
-}
-
-// TF32 hi/lo halves of a point-major FP32 matrix (n rows of ld values, ld a
-// multiple of 4), rounded as store_split4 rounds them: hi = tf32(x),
-// lo = tf32(x - hi).  reverse != 0 stores row p at row n - 1 - p: the rows
-// of a window (training points in reverse) are then consecutive.
-__global__ void k_split_tf32(const float* __restrict__ V, int64_t n, int ld, int reverse, float* __restrict__ hi,
-                             float* __restrict__ lo) {
-  const int l4 = ld >> 2;
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n * l4) return;
-  const int64_t p = q / l4, c = q - p * l4;
-  const float4 v = reinterpret_cast<const float4*>(V)[q];
-  float4 h, l;
-  h.x = tc::tf32_round(v.x); l.x = tc::tf32_round(v.x - h.x);
-  h.y = tc::tf32_round(v.y); l.y = tc::tf32_round(v.y - h.y);
-  h.z = tc::tf32_round(v.z); l.z = tc::tf32_round(v.z - h.z);
-  h.w = tc::tf32_round(v.w); l.w = tc::tf32_round(v.w - h.w);
-  const int64_t o = (reverse ? n - 1 - p : p) * l4 + c;
-  reinterpret_cast<float4*>(hi)[o] = h;
-  reinterpret_cast<float4*>(lo)[o] = l;
-}
-
-__device__ __forceinline__ void split_setup(SplitSmem& sm) {
-  using namespace tc;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kSplitStages; ++s) {
-      mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.empty[s], 1);
-    }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&sm.done[a], 1);
-      mbar_init(&sm.drained[a], kSplitWorkers);
-    }
-    mbar_init(&sm.fin, 1);
-    sm.abort = 0;
-    mbar_fence_init();
-  }
-  if ((threadIdx.x >> 5) == kSplitWorkers) tmem_alloc(&sm.tmem, 256);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-}
-__device__ __forceinline__ void split_teardown(SplitSmem& sm) {
-  using namespace tc;
-  fence_before_sync();
-  __syncthreads();
-  if ((threadIdx.x >> 5) == kSplitWorkers) tmem_dealloc(sm.tmem, 256);
-}
+// Worker warps of the persistent tensor-core products (4 lane quarters x 4
+// groups of 32 columns of a 128 x 128 tile).
+constexpr int kSplitWorkers = 16;
 
 // Barrier of the kSplitWorkers worker warps only (id 1) that also ANDs a
 // flag over them, so that all of them take the same branch after it.
@@ -1391,157 +1329,7 @@ __device__ __forceinline__ bool worker_sync_and(bool v) {
   return r != 0;
 }
 
-// Persistent loop over output tiles t = blockIdx.x, blockIdx.x + gridDim.x,
-// ... < ntiles, each hi + lo = sum over its chunks c < chunks(t) of
-// sum_{k < 32} A(ya + r, x + k) B(yb + c', x + k) with (x, ya, yb) =
-// at(base, c) and base = coords(t) (computed once per tile by the producer):
-// A from (ahi, alo), B from (bhi, blo); rows outside the maps read zero.  The
-// producer and MMA warps run ahead into the next tile while the workers
-// finish the current one: before(t) (shared-memory set-up of the epilogue,
-// worker warps only, between two worker barriers), the drains, then
-// after(t, hi, lo), where worker warp w holds row 32 (w mod 4) + lane,
-// columns 32 (w / 4) + j in hi[j] + lo[j].  Barrier phases run on across
-// tiles.  Every wait has an iteration limit: on a timeout all roles stop,
-// no copy is left landing, and false is returned in every thread.
-template <class Chunks, class Coords, class At, class Before, class After>
-__device__ bool split_persistent(SplitSmem& sm, const CUtensorMap* ahi, const CUtensorMap* alo,
-                                 const CUtensorMap* bhi, const CUtensorMap* blo, int ntiles, Chunks chunks,
-                                 Coords coords, At at, Before before, After after) {
-  using namespace tc;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  volatile int* abort_flag = &sm.abort;
-  if (warp < kSplitWorkers) {
-    const int q = warp & 3, half = warp >> 2;
-    const uint32_t tlane = sm.tmem + ((uint32_t)(q * 32) << 16) + half * 32;
-    int G = 0;  // groups drained so far by this CTA
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      ok = worker_sync_and(ok && !*abort_flag);  // also: the previous epilogue is done with shared memory
-      if (!ok) break;
-      before(t);
-      worker_sync_and(true);
-      float hi[32], lo[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
-      const int ngroup = (chunks(t) + kSplitDrain - 1) / kSplitDrain;
-      for (int g = 0; g < ngroup && ok; ++g, ++G) {
-        const int a = G & 1;
-        int okw = 1;
-        if (lane == 0) okw = mbar_wait(&sm.done[a], (G >> 1) & 1) ? 1 : 0;
-        okw = __shfl_sync(0xffffffffu, okw, 0);
-        if (!okw) {
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        fence_after_sync();
-        float tv[16];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tmem_ld16(tlane + 128 * a + 16 * h, tv);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) two_sum(hi[16 * h + j], lo[16 * h + j], tv[j]);
-        }
-        fence_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.drained[a]);
-      }
-      ok = worker_sync_and(ok && !*abort_flag);
-      if (!ok) break;
-      after(t, hi, lo);
-    }
-  } else if (warp == kSplitWorkers) {
-    // MMA warp: the whole warp runs the loops, lane 0 waits and issues
-    const uint32_t idesc = idesc_tf32(128, 128);
-    int C = 0, G = 0;  // chunks and groups issued so far by this CTA
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int nchunk = chunks(t);
-      for (int c = 0; c < nchunk; ++c, ++C) {
-        const int s = C % kSplitStages, a = G & 1;
-        const bool first = (c % kSplitDrain) == 0, last = (c % kSplitDrain) == kSplitDrain - 1 || c == nchunk - 1;
-        int okw = 1;
-        if (lane == 0) {
-          okw = mbar_wait(&sm.full[s], (C / kSplitStages) & 1) ? 1 : 0;
-          if (okw && first && G >= 2) okw = mbar_wait(&sm.drained[a], ((G - 2) >> 1) & 1) ? 1 : 0;
-        }
-        okw = __shfl_sync(0xffffffffu, okw, 0);
-        if (!okw || *abort_flag) {
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        fence_after_sync();
-        if (lane == 0) {
-          TcStage<128>& S = sm.st[s];
-          const uint32_t ah = smem_addr(S.a_hi), al = smem_addr(S.a_lo);
-          const uint32_t bh = smem_addr(S.b_hi), bl = smem_addr(S.b_lo);
-          const uint32_t dcol = sm.tmem + 128 * a;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (first && ks == 0) ? 0u : 1u);
-            mma_tf32(dcol, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
-            mma_tf32(dcol, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
-          }
-          mma_commit(&sm.empty[s]);           // the stage may be refilled
-          if (last) mma_commit(&sm.done[a]);  // the accumulator may be drained
-        }
-        __syncwarp();
-        if (last) ++G;
-      }
-    }
-    if (lane == 0) mma_commit(&sm.fin);  // arrives once every MMA issued above has completed
-    __syncwarp();
-  } else {
-    // TMA producer: the whole warp runs the loops, lane 0 waits and issues
-    int C = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int4 base = coords(t);
-      const int nchunk = chunks(t);
-      for (int c = 0; c < nchunk; ++c, ++C) {
-        const int s = C % kSplitStages;
-        int okw = 1;
-        if (lane == 0 && C >= kSplitStages) okw = mbar_wait(&sm.empty[s], (C / kSplitStages - 1) & 1) ? 1 : 0;
-        okw = __shfl_sync(0xffffffffu, okw, 0);
-        if (!okw || *abort_flag) {
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        if (lane == 0) {
-          TcStage<128>& S = sm.st[s];
-          const int3 y = at(base, c);
-          mbar_arrive_expect_tx(&sm.full[s], 4u * 128u * 32u * 4u);
-          tma_load_2d(S.a_hi, ahi, y.x, y.y, &sm.full[s]);
-          tma_load_2d(S.a_lo, alo, y.x, y.y, &sm.full[s]);
-          tma_load_2d(S.b_hi, bhi, y.x, y.z, &sm.full[s]);
-          tma_load_2d(S.b_lo, blo, y.x, y.z, &sm.full[s]);
-        }
-        __syncwarp();
-      }
-    }
-    // no copy may still be landing in shared memory when the CTA leaves
-    if (lane == 0)
-      for (int c = C > kSplitStages ? C - kSplitStages : 0; c < C; ++c)
-        mbar_wait(&sm.full[c % kSplitStages], (c / kSplitStages) & 1);
-    __syncwarp();
-  }
-  // every issued MMA has completed before anyone frees tensor memory
-  const bool w = mbar_wait(&sm.fin, 0);
-  return __syncthreads_and(w && !*abort_flag) != 0;
-}
-
-// Residual tiles on the tensor cores (mixed form), one persistent CTA per SM
-// walking the item list.  Item (window, I, J): rows [128 I, 128 I + 128) x
-// columns [RB J, RB J + RB) of the window's residual
-// R = K + sigma_n^2 I - Vt Vt^T, blanket-first, with the Vt Vt^T sum of
-// split_persistent (RB = 128 columns).  (vhi, vlo): tensor maps of the TF32
-// halves of V in reversed point order (row nrev - 1 - p holds point p), 32 x
-// 128 boxes, 128-byte swizzle; nchunk = (row length of V) / 32.  Rows and
-// columns past the window's order read other points' rows (or zeros): the
-// epilogue writes the identity there and never reads those sums.
+// Width of the 128 x RB output tiles of the compensated products.
 constexpr int RB = 128;
 
 // Squared scaled distance |a - b|^2 over D (zero-padded) dimensions; b is a
@@ -1566,154 +1354,8 @@ __device__ __forceinline__ float dist2(const float (&a)[D], const float* b) {
 // Input dimension padded for the unrolled epilogues (a multiple of 4).
 __host__ __device__ constexpr int pad_dim(int d) { return d <= 8 ? 8 : MAXD; }
 
-template <int D>
-__global__ void __launch_bounds__(kSplitThreads, 1) k_resid_tc(const int4* __restrict__ items, int nitems,
-                                                  const Win* __restrict__ wins, const float* __restrict__ xs, int d,
-                                                  const __grid_constant__ CUtensorMap vhi,
-                                                  const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
-                                                  float ss2, float sn2, float* __restrict__ buf,
-                                                  int* __restrict__ err) {
-  using namespace tc;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  SplitSmem& sm = split_smem(smraw);
-  __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  split_setup(sm);
-  auto chunks = [&](int) { return nchunk; };
-  auto coords = [&](int t) -> int4 {
-    const int4 it = items[t];
-    const int base = nrev - (int)wins[it.x].g_end;  // reversed row of the window's local row 0
-    return make_int4(base + it.y * 128, base + it.z * RB, 0, 0);
-  };
-  auto at = [](int4 b, int c) { return make_int3(32 * c, b.x, b.y); };
-  auto before = [&](int t) {
-    const int4 it = items[t];
-    const Win w = wins[it.x];
-    const int c0 = it.z * RB;
-    for (int e = tid; e < RB * D; e += kSplitWorkers * 32) {
-      const int r = e / D, q = e % D;
-      xc[r][q] = (c0 + r < w.n && q < d) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
-    }
-  };
-  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
-    const int4 it = items[t];
-    const Win w = wins[it.x];
-    const int r0 = it.y * 128, c0 = it.z * RB;
-    const int q = warp & 3, half = warp >> 2;
-    const int i = r0 + q * 32 + lane;
-    const int cg = c0 + half * 32;  // this thread's 32 columns (npad is a multiple of 64)
-    if (i >= w.npad || cg >= w.npad) return;
-    float xr[D];
-#pragma unroll
-    for (int t2 = 0; t2 < D; ++t2) xr[t2] = (i < w.n && t2 < d) ? xs[(w.g_end - 1 - i) * d + t2] : 0.f;
-    float* dst = buf + w.base + (int64_t)i * w.npad + cg;
-#pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
-      float out[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int j = 4 * j4 + k, cl = half * 32 + j, jj = c0 + cl;
-        float v;
-        if (i < w.n && jj < w.n) {
-          const float d2 = dist2<D>(xr, xc[cl]);
-          v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
-          if (i == jj) v += sn2;
-        } else {
-          v = (i == jj) ? 1.f : 0.f;
-        }
-        out[k] = v;
-      }
-      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
-    }
-  };
-  const bool ok = split_persistent(sm, &vhi, &vlo, &vhi, &vlo, nitems, chunks, coords, at, before, after);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  split_teardown(sm);
-}
 
-// Block-part summary rows of the owned windows, compacted and split for
-// k_gram_split: window wi's extra rows e < se = s + 1, columns [nB, n) (its
-// [z_m | Z_m]^T, Definition 1 whitened) go to rows wi se + e, columns
-// [0, n - nB) of (hi, lo), row length kmax (a multiple of 32, zero pad).
-__global__ void k_split_summary(const Win* __restrict__ wins, const float* __restrict__ buf, int se, int kmax,
-                                float* __restrict__ hi, float* __restrict__ lo) {
-  // block (x, window y): rows e = 4 x + threadIdx.y, four values per thread
-  // and step (16-byte loads when the row's first value is aligned)
-  const Win w = wins[blockIdx.y];
-  const int e = blockIdx.x * blockDim.y + threadIdx.y;
-  if (e >= se) return;
-  const int nb = w.n - w.nB;
-  const float* src = buf + w.base + (int64_t)(w.npad + e) * w.npad + w.nB;
-  const bool al = (w.nB & 3) == 0;
-  const int64_t o = ((int64_t)blockIdx.y * se + e) * kmax;
-  for (int j = 4 * threadIdx.x; j < kmax; j += 4 * blockDim.x) {
-    float4 x;
-    if (al && j + 3 < nb) {
-      x = *reinterpret_cast<const float4*>(src + j);
-    } else {
-      x.x = j < nb ? src[j] : 0.f;
-      x.y = j + 1 < nb ? src[j + 1] : 0.f;
-      x.z = j + 2 < nb ? src[j + 2] : 0.f;
-      x.w = j + 3 < nb ? src[j + 3] : 0.f;
-    }
-    float4 h, l;
-    h.x = tc::tf32_round(x.x); l.x = tc::tf32_round(x.x - h.x);
-    h.y = tc::tf32_round(x.y); l.y = tc::tf32_round(x.y - h.y);
-    h.z = tc::tf32_round(x.z); l.z = tc::tf32_round(x.z - h.z);
-    h.w = tc::tf32_round(x.w); l.w = tc::tf32_round(x.w - h.w);
-    *reinterpret_cast<float4*>(hi + o + j) = h;
-    *reinterpret_cast<float4*>(lo + o + j) = l;
-  }
-}
 
-// Gram of the local summaries on the tensor cores (mixed form), one
-// persistent CTA per SM: item t = (tile (I, J) of the lower 128-tiles of G,
-// window group g) adds sum over the windows of group g of
-// [z_m | Z_m]^T [z_m | Z_m] with split_persistent, whose K runs window by
-// window over the compacted rows of k_split_summary (kmax / 32 chunks each),
-// and writes hi + lo as FP64 partial g, summed over groups by k_gram_reduce.
-// Rows and columns past se read the next window's rows (or zeros) and are
-// never written.
-__global__ void __launch_bounds__(kSplitThreads, 1) k_gram_split(const int2* __restrict__ tiles, int ntile, int nwin,
-                                                    int group, int se, int kmax,
-                                                    const __grid_constant__ CUtensorMap shi,
-                                                    const __grid_constant__ CUtensorMap slo,
-                                                    double* __restrict__ partial, int* __restrict__ err) {
-  using namespace tc;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  SplitSmem& sm = split_smem(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int cpw = kmax / 32;
-  const int ngroup = (nwin + group - 1) / group;
-  split_setup(sm);
-  auto chunks = [&](int t) {
-    const int g = t / ntile;
-    return (min(nwin, (g + 1) * group) - g * group) * cpw;
-  };
-  auto coords = [&](int t) -> int4 {
-    const int2 tl = tiles[t % ntile];
-    return make_int4(tl.x * 128, tl.y * 128, (t / ntile) * group, 0);
-  };
-  auto at = [&](int4 b, int c) {
-    const int wi = b.z + c / cpw;
-    return make_int3(32 * (c % cpw), wi * se + b.x, wi * se + b.y);
-  };
-  auto before = [](int) {};
-  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
-    const int2 tl = tiles[t % ntile];
-    const int q = warp & 3, half = warp >> 2;
-    const int e1 = tl.x * 128 + q * 32 + lane;
-    const int cg = tl.y * 128 + half * 32;
-    if (e1 >= se) return;
-    double* P = partial + (int64_t)(t / ntile) * se * se + (int64_t)e1 * se;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (cg + j < se) P[cg + j] = (double)hi[j] + (double)lo[j];
-  };
-  const bool ok = split_persistent(sm, &shi, &slo, &shi, &slo, ntile * ngroup, chunks, coords, at, before, after);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  split_teardown(sm);
-}
 
 // h[u][k] = sum over the pairs (n, m) of test block n of
 // sum_{c in kept columns} P[u][c] X_{1+k}[c]  -  Vu[u][k]  on the tensor
@@ -1864,77 +1506,5 @@ __global__ void k_pred_hsum(const int4* __restrict__ tb, const int64_t* __restri
   h[o] = (float)(acc - (double)Vu[o]);
 }
 
-// Prediction right-hand sides on the tensor cores, one persistent CTA per SM
-// walking the item list: item (pair, u tile of 128, column tile of RB):
-// P[u][i] = K(xu_u, x_g(i)) - Vu[u] . Vt[g(i)] for the window of the pair,
-// with split_persistent (the same cancellation as the residual).
-// (uhi, ulo): tensor maps of the TF32 halves of Vu in test-point order;
-// (vhi, vlo) those of Vt in reversed point order (row nrev - 1 - p holds
-// point p); nchunk = (row length) / 32.  Test rows past the block and window
-// columns past its order are never written from their sums.
-template <int D>
-__global__ void __launch_bounds__(kSplitThreads, 1) k_pred_rhs_tc(const Pair* __restrict__ pairs, const int4* __restrict__ items,
-                                                     int nitems, const Win* __restrict__ wins,
-                                                     const float* __restrict__ xs, const float* __restrict__ xu, int d,
-                                                     const __grid_constant__ CUtensorMap uhi,
-                                                     const __grid_constant__ CUtensorMap ulo,
-                                                     const __grid_constant__ CUtensorMap vhi,
-                                                     const __grid_constant__ CUtensorMap vlo, int nrev, int nchunk,
-                                                     float ss2, float* __restrict__ P, int* __restrict__ err) {
-  using namespace tc;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  SplitSmem& sm = split_smem(smraw);
-  __shared__ __align__(16) float xc[RB][D];  // scaled inputs of the tile's columns, zero-padded
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  split_setup(sm);
-  auto chunks = [&](int) { return nchunk; };
-  auto coords = [&](int t) -> int4 {
-    const int4 it = items[t];
-    const Pair pr = pairs[it.x];
-    return make_int4(pr.u0 + it.y * 128, nrev - (int)wins[pr.win].g_end + it.z * RB, 0, 0);
-  };
-  auto at = [](int4 b, int c) { return make_int3(32 * c, b.x, b.y); };
-  auto before = [&](int t) {
-    const int4 it = items[t];
-    const Win w = wins[pairs[it.x].win];
-    const int c0 = it.z * RB;
-    for (int e = tid; e < RB * D; e += kSplitWorkers * 32) {
-      const int r = e / D, q = e % D;
-      xc[r][q] = (c0 + r < w.n && q < d) ? xs[(w.g_end - 1 - (c0 + r)) * d + q] : 0.f;
-    }
-  };
-  auto after = [&](int t, float(&hi)[32], float(&lo)[32]) {
-    const int4 it = items[t];
-    const Pair pr = pairs[it.x];
-    const Win w = wins[pr.win];
-    const int u0 = it.y * 128, c0 = it.z * RB;
-    const int q = warp & 3, half = warp >> 2;
-    const int uu = u0 + q * 32 + lane;
-    const int cg = c0 + half * 32;
-    if (uu >= pr.nu || cg >= w.npad) return;
-    float xr[D];
-#pragma unroll
-    for (int t2 = 0; t2 < D; ++t2) xr[t2] = t2 < d ? xu[(int64_t)(pr.u0 + uu) * d + t2] : 0.f;
-    float* dst = P + pr.pbase + (int64_t)uu * w.npad + cg;
-#pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
-      float out[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int j = 4 * j4 + k, cl = half * 32 + j;
-        float v = 0.f;
-        if (c0 + cl < w.n) {
-          const float d2 = dist2<D>(xr, xc[cl]);
-          v = (ss2 * expf(-0.5f * d2) - hi[j]) - lo[j];
-        }
-        out[k] = v;
-      }
-      *reinterpret_cast<float4*>(dst + 4 * j4) = make_float4(out[0], out[1], out[2], out[3]);
-    }
-  };
-  const bool ok = split_persistent(sm, &uhi, &ulo, &vhi, &vlo, nitems, chunks, coords, at, before, after);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  split_teardown(sm);
-}
 
 }  // namespace lma

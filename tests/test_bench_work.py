@@ -21,7 +21,7 @@ def test_work_model_c2():
     # the test rows add work to the fit's sweep only
     for k in ("k_chol_panel2_tc", "k_chol_wide", "k_chol_mid"):
         assert fused[k] > plain[k]
-    for k in ("k_resid_tc", "k_gram_split", "k_pred_rhs_tc", "k_proj", "k_f64_chain"):
+    for k in ("k_resid_bf6", "k_gram_bf6", "k_pred_rhs_bf6", "k_proj", "k_f64_chain"):
         assert fused[k] == plain[k]
     # left-looking update of the windows, counted once: wide + mid + step = the full left-looking sum
     s = p.s
