@@ -467,6 +467,37 @@ static void factor_fp64_single(cudaStream_t st, Arena& tmp, double* buf, int n, 
 }
 
 // ---------------------------------------------------------------------------
+// One side stream and two events per host thread and device (created on
+// first use): work that does not depend on the call stream's latest results
+// runs there and is joined by an event.
+struct Side {
+  int dev = -1;
+  cudaStream_t st = nullptr;
+  cudaEvent_t local = nullptr, global = nullptr;
+  void drop() {
+    if (local) cudaEventDestroy(local);
+    if (global) cudaEventDestroy(global);
+    if (st) cudaStreamDestroy(st);
+    st = nullptr;
+    local = global = nullptr;
+  }
+  ~Side() { drop(); }
+};
+
+static Side& side_streams() {
+  static thread_local Side side;
+  int dev = 0;
+  LMA_CK(cudaGetDevice(&dev));
+  if (side.dev != dev) {
+    side.drop();
+    LMA_CK(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+    LMA_CK(cudaEventCreateWithFlags(&side.local, cudaEventDisableTiming));
+    LMA_CK(cudaEventCreateWithFlags(&side.global, cudaEventDisableTiming));
+    side.dev = dev;
+  }
+  return side;
+}
+
 template <typename T>
 void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, Arena& tmp, const double** X_d,
                       const double** y_d) {
@@ -517,21 +548,42 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   launch("k_build_kss", k_build_kss, nblk((int64_t)(npS + s) * npS), NT, 0, st, ss64, (int)s, (int)d, mc.ss2, H->jitter, npS, kb);
   mc.flags = mc.keep.alloc<int>(4);
   LMA_CK(cudaMemsetAsync(mc.flags, 0, 4 * sizeof(int), st));
-  factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
   T* ET = mc.keep.alloc<T>(s * s);
-  launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
+  T* Vt = mc.keep.alloc<T>(n * s);
   mc.ET = ET;
+  mc.Vt = Vt;
   // V = L_SS^-1 Sigma_SD, point-major
   if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
+    // the K_SD planes do not depend on L_SS: they are evaluated on the side
+    // stream while Sigma_SS is factorised (FP64, latency-bound) on this one
     mc.ldk = (int)roundup(s, 64);
     mc.brows = (int)roundup(s, 128);
     mc.linv3 = mc.keep.alloc<uint16_t>((size_t)3 * mc.brows * mc.ldk);
-    launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb, (int64_t)npS,
-           (int)s, mc.brows, mc.ldk, mc.linv3);
+    uint16_t* Ap = tmp.alloc<uint16_t>((size_t)3 * n * mc.ldk);
+    Side& sd = side_streams();
+    LMA_CK(cudaEventRecord(sd.local, st));
+    LMA_CK(cudaStreamWaitEvent(sd.st, sd.local, 0));
+    try {
+      launch("k_kds_bf3", pad_dim((int)d) == 8 ? k_kds_bf3<8> : k_kds_bf3<MAXD>,
+             dim3((unsigned)(mc.ldk / 64), nblk(n, 32)), 256, 0, sd.st, (const float*)xsT, n, (int)d,
+             (const float*)ssT, (int)s, (float)mc.ss2, mc.ldk, Ap);
+      LMA_CK(cudaEventRecord(sd.global, sd.st));
+      factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
+      launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
+      launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb,
+             (int64_t)npS, (int)s, mc.brows, mc.ldk, mc.linv3);
+    } catch (...) {
+      cudaStreamSynchronize(sd.st);  // nothing of this call may still run on the side stream
+      throw;
+    }
+    LMA_CK(cudaStreamWaitEvent(st, sd.global, 0));
+    proj_tc(st, "k_proj_tc", Ap, n, mc.linv3, mc.brows, (int)s, mc.ldk, (float*)Vt, s, mc.flags + 2);
+    tmp.free_one(Ap);
+  } else {
+    factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
+    launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
+    project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
   }
-  T* Vt = mc.keep.alloc<T>(n * s);
-  project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
-  mc.Vt = Vt;
 }
 
 // Local part of a fit: windows of blocks [w_begin, own_end) are formed and
@@ -823,29 +875,7 @@ void Impl<T>::fit(ModelCore& mc, const lma_problem* P, const lma_hyper* H) {
 template <typename T>
 void Impl<T>::fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
                           const int64_t* tptr, int noisy, int on_device, double* mean, double* var) {
-  struct Side {  // one side stream and two events per host thread and device
-    int dev = -1;
-    cudaStream_t st = nullptr;
-    cudaEvent_t local = nullptr, global = nullptr;
-    void drop() {
-      if (local) cudaEventDestroy(local);
-      if (global) cudaEventDestroy(global);
-      if (st) cudaStreamDestroy(st);
-      st = nullptr;
-      local = global = nullptr;
-    }
-    ~Side() { drop(); }
-  };
-  static thread_local Side side;
-  int dev = 0;
-  LMA_CK(cudaGetDevice(&dev));
-  if (side.dev != dev) {
-    side.drop();
-    LMA_CK(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
-    LMA_CK(cudaEventCreateWithFlags(&side.local, cudaEventDisableTiming));
-    LMA_CK(cudaEventCreateWithFlags(&side.global, cudaEventDisableTiming));
-    side.dev = dev;
-  }
+  Side& side = side_streams();
   // mixed form on the tensor cores: the test right-hand sides ride the fit's sweep
   FusedTest ft;
   FusedTest* ftp = nullptr;
