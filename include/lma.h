@@ -116,6 +116,23 @@ lma_status lma_predict(const lma_model* model, int64_t u, const double* XU,
                        const int64_t* test_block_ptr, int noisy, int io_on_device,
                        double* mean_out, double* var_out);
 
+/* lma_predict, enqueued: the call returns once the prediction is queued on
+ * the model's stream (the cuda_stream of its fit), without waiting for it.
+ * XU, mean_out and var_out must be device memory and stay valid until the
+ * stream has passed the work (a stream synchronisation or lma_model_wait).
+ * Argument errors are returned at once (LMA_ERR_INVALID_ARG, also for host
+ * buffers); an error found on the device (a bounded pipeline wait that gave
+ * up) is recorded in a status word of the model and returned by the next
+ * lma_model_wait.  Calls on one model are ordered by its stream.  The
+ * paper has no counterpart.                                                 */
+lma_status lma_predict_async(lma_model* model, int64_t u, const double* XU, const int64_t* test_block_ptr,
+                             int noisy, double* mean_out, double* var_out);
+
+/* Waits until the model's stream has finished everything queued on it and
+ * returns the device status of the lma_predict_async calls since the last
+ * wait (LMA_ERR_TIMEOUT if a bounded device wait gave up), clearing it.     */
+lma_status lma_model_wait(lma_model* model);
+
 /* lma_predict plus the predictive covariance of every test block: for the
  * test points of block n, Eq. (vapvar) restricted to U_n x U_n (these pairs
  * are in-band, so Sigma-bar_UU = Sigma_UU there), evaluated by the same local

@@ -11,7 +11,7 @@ LMA_OK, LMA_ERR_INVALID_ARG, LMA_ERR_NOT_PD, LMA_ERR_CUDA, LMA_ERR_OOM, LMA_ERR_
 LMA_FP64, LMA_MIXED = 0, 1
 
 EXPORTED = (
-    "lma_fit", "lma_predict", "lma_model_loglik", "lma_model_loglik_grad", "lma_loglik", "lma_loglik_grad", "lma_model_summary",
+    "lma_fit", "lma_predict", "lma_predict_async", "lma_model_wait", "lma_model_loglik", "lma_model_loglik_grad", "lma_loglik", "lma_loglik_grad", "lma_model_summary",
     "lma_window_residual", "lma_window_rows", "lma_model_free", "lma_status_string", "lma_last_error_info",
     "lma_kernel_launch_count", "lma_profile_start", "lma_profile_stop", "lma_profile_trace", "lma_tc_gemm_check",
     "lma_global_step_noalloc", "lma_fit_local", "lma_model_local_summary", "lma_model_set_global",
@@ -65,6 +65,10 @@ def load(path: str | None = None):
     lib.lma_model_loglik.restype = C.c_int
     lib.lma_model_loglik_grad.argtypes = [vp, vp]
     lib.lma_model_loglik_grad.restype = C.c_int
+    lib.lma_predict_async.argtypes = [vp, C.c_int64, vp, vp, C.c_int, vp, vp]
+    lib.lma_predict_async.restype = C.c_int
+    lib.lma_model_wait.argtypes = [vp]
+    lib.lma_model_wait.restype = C.c_int
     lib.lma_loglik.argtypes = [P, H, O, C.POINTER(C.c_double)]
     lib.lma_loglik.restype = C.c_int
     lib.lma_loglik_grad.argtypes = [P, H, O, C.POINTER(C.c_double), vp]

@@ -121,6 +121,29 @@ def lma_predict(model: Model, XU, test_block_ptr, noisy: bool = True, out=None):
     return mean, var
 
 
+def lma_predict_async(model: Model, XU, test_block_ptr, noisy: bool = True):
+    """lma_predict queued on the model's stream, without waiting (see
+    lma_predict_async in lma.h).  XU must be a contiguous float64 CUDA tensor
+    and stay alive until lma_model_wait(model) (or a synchronisation of the
+    model's stream); returns the (mean, var) CUDA tensors that the queued work
+    fills."""
+    if not (isinstance(XU, torch.Tensor) and XU.is_cuda and XU.dtype == torch.float64 and XU.is_contiguous()):
+        raise ValueError("lma_predict_async needs XU as a contiguous float64 CUDA tensor")
+    keep = []
+    u = int(XU.shape[0])
+    mean = torch.empty(u, dtype=torch.float64, device=XU.device)
+    var = torch.empty(u, dtype=torch.float64, device=XU.device)
+    tp = _i64(test_block_ptr, keep)
+    _abi.check(_abi.load().lma_predict_async(model.handle, u, XU.data_ptr(), tp, int(bool(noisy)), mean.data_ptr(),
+                                             var.data_ptr()))
+    return mean, var
+
+
+def lma_model_wait(model: Model) -> None:
+    """Wait for the model's stream; raises the status of the queued predictions."""
+    _abi.check(_abi.load().lma_model_wait(model.handle))
+
+
 def lma_predict_cov(model: Model, XU, test_block_ptr, noisy: bool = True):
     """(mean, var, covs): covs[n] is the |U_n| x |U_n| predictive covariance of
     test block n (None for empty blocks); numpy for host input, torch CUDA

@@ -254,8 +254,9 @@ lma_status lma_model_set_global(lma_model* md, const double* G, double logdet_R,
   });
 }
 
-lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
-                       int io_on_device, double* mean_out, double* var_out) {
+// Argument checks shared by lma_predict and lma_predict_async.
+static lma_status lma_predict_checks(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr,
+                                     const double* mean_out, const double* var_out) {
   if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
   if (u < 0) return fail(LMA_ERR_INVALID_ARG, "negative test count");
   if (u > 0 && (!XU || !tptr || !mean_out || !var_out)) return fail(LMA_ERR_INVALID_ARG, "null pointer");
@@ -270,12 +271,65 @@ lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const i
         return fail(LMA_ERR_INVALID_ARG, "test block outside the windows of this model", m);
     }
   }
+  return LMA_OK;
+}
+
+lma_status lma_predict(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
+                       int io_on_device, double* mean_out, double* var_out) {
+  lma_status cst = lma_predict_checks(md, u, XU, tptr, mean_out, var_out);
+  if (cst != LMA_OK) return cst;
+  const ModelCore& mc = md->core;
   return guarded([&] {
     if (mc.prec == LMA_MIXED)
       Impl<float>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
     else
       Impl<double>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out);
   });
+}
+
+static bool on_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lma_status lma_predict_async(lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
+                             double* mean_out, double* var_out) {
+  if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
+  if (u > 0 && (!on_device_ptr(XU) || !on_device_ptr(mean_out) || !on_device_ptr(var_out)))
+    return fail(LMA_ERR_INVALID_ARG, "lma_predict_async needs XU, mean_out and var_out in device memory");
+  ModelCore& mc = md->core;
+  lma_status st = lma_predict_checks(md, u, XU, tptr, mean_out, var_out);
+  if (st != LMA_OK || u == 0) return st;
+  return guarded([&] {
+    if (!mc.async_err) {
+      mc.async_err = mc.keep.alloc<int>(1);
+      LMA_CK(cudaMemsetAsync(mc.async_err, 0, sizeof(int), mc.st));
+    }
+    if (mc.prec == LMA_MIXED)
+      Impl<float>::predict(mc, u, XU, tptr, noisy, 1, mean_out, var_out, nullptr, nullptr, nullptr, mc.async_err);
+    else
+      Impl<double>::predict(mc, u, XU, tptr, noisy, 1, mean_out, var_out, nullptr, nullptr, nullptr, mc.async_err);
+  });
+}
+
+lma_status lma_model_wait(lma_model* md) {
+  if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
+  ModelCore& mc = md->core;
+  int herr = 0;
+  lma_status st = guarded([&] {
+    if (mc.async_err) {
+      LMA_CK(cudaMemcpyAsync(&herr, mc.async_err, sizeof(int), cudaMemcpyDeviceToHost, mc.st));
+      LMA_CK(cudaMemsetAsync(mc.async_err, 0, sizeof(int), mc.st));
+    }
+    LMA_CK(cudaStreamSynchronize(mc.st));
+  });
+  if (st != LMA_OK) return st;
+  if (herr) return fail(LMA_ERR_TIMEOUT, "tensor-core pipeline wait timed out in an enqueued prediction");
+  return LMA_OK;
 }
 
 lma_status lma_fit_predict(const lma_problem* P, const lma_hyper* H, const lma_options* O, int64_t u,

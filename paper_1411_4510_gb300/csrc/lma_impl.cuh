@@ -165,8 +165,11 @@ inline int64_t roundup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 struct Staging {
   char* base = nullptr;
   size_t cap = 0, used = 0;
+  bool hold = false;  // an enqueued call's uploads may still be in flight: no reuse before a device sync
   void* take(size_t bytes, cudaStream_t st);
-  void reset() { used = 0; }
+  void reset() {
+    if (!hold) used = 0;
+  }
 };
 Staging& staging();
 
@@ -212,6 +215,7 @@ struct ModelCore {
   int npS = 0;
   int64_t w0 = 0;             // block index of the first window (partitioned fits)
   int64_t own_b = 0, own_e = 0;  // blocks whose local summaries this model holds
+  int* async_err = nullptr;   // device status word of the enqueued predictions (lma_predict_async)
   bool have_global = false;   // global step done (prediction possible)
   // device status words, checked once at the end of a call:
   // [0] Sigma_SS pivot failure (+1 column), [1] I + A pivot failure,
@@ -263,7 +267,7 @@ struct Impl {
   static void check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
                       int on_device, double* mean, double* var, cudaEvent_t global_done = nullptr,
-                      double* cov = nullptr, FusedTest* ft = nullptr);
+                      double* cov = nullptr, FusedTest* ft = nullptr, int* async_err = nullptr);
   static void fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
                           const int64_t* tptr, int noisy, int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);

@@ -352,6 +352,11 @@ __global__ void __launch_bounds__(NT) k_resid(const Win* __restrict__ wins, cons
     }
 }
 
+// dst |= src (one device status word into another).
+__global__ void k_or_flag(const int* __restrict__ src, int* __restrict__ dst) {
+  if (threadIdx.x == 0 && *src) atomicOr(dst, *src);
+}
+
 // Residual entries shared between windows.  A pair of training points (p, q),
 // p <= q (global order), lies in every window that holds both; in the window
 // of p's block, p is a point of the window's own block, and the residual

@@ -93,6 +93,7 @@ void* Staging::take(size_t bytes, cudaStream_t st) {
     // every earlier upload (of any stream of this thread) must have landed
     (void)st;
     LMA_CK(cudaDeviceSynchronize());
+    hold = false;
     if (bytes > cap) {
       if (base) cudaFreeHost(base);
       base = nullptr;
@@ -552,38 +553,17 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
   T* Vt = mc.keep.alloc<T>(n * s);
   mc.ET = ET;
   mc.Vt = Vt;
-  // V = L_SS^-1 Sigma_SD, point-major
+  factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
+  launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
   if (sizeof(T) == 4 && mc.prec == LMA_MIXED && use_tensor_cores()) {
-    // the K_SD planes do not depend on L_SS: they are evaluated on the side
-    // stream while Sigma_SS is factorised (FP64, latency-bound) on this one
     mc.ldk = (int)roundup(s, 64);
     mc.brows = (int)roundup(s, 128);
     mc.linv3 = mc.keep.alloc<uint16_t>((size_t)3 * mc.brows * mc.ldk);
-    uint16_t* Ap = tmp.alloc<uint16_t>((size_t)3 * n * mc.ldk);
-    Side& sd = side_streams();
-    LMA_CK(cudaEventRecord(sd.local, st));
-    LMA_CK(cudaStreamWaitEvent(sd.st, sd.local, 0));
-    try {
-      launch("k_kds_bf3", pad_dim((int)d) == 8 ? k_kds_bf3<8> : k_kds_bf3<MAXD>,
-             dim3((unsigned)(mc.ldk / 64), nblk(n, 32)), 256, 0, sd.st, (const float*)xsT, n, (int)d,
-             (const float*)ssT, (int)s, (float)mc.ss2, mc.ldk, Ap);
-      LMA_CK(cudaEventRecord(sd.global, sd.st));
-      factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
-      launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
-      launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb,
-             (int64_t)npS, (int)s, mc.brows, mc.ldk, mc.linv3);
-    } catch (...) {
-      cudaStreamSynchronize(sd.st);  // nothing of this call may still run on the side stream
-      throw;
-    }
-    LMA_CK(cudaStreamWaitEvent(st, sd.global, 0));
-    proj_tc(st, "k_proj_tc", Ap, n, mc.linv3, mc.brows, (int)s, mc.ldk, (float*)Vt, s, mc.flags + 2);
-    tmp.free_one(Ap);
-  } else {
-    factor_fp64_single(st, tmp, kb, (int)s, npS, (int)s, (int)s, mc.flags + 0, mc.flags + 3);
-    launch("k_copy_block", k_copy_block<T>, nblk(s * s), NT, 0, st, kb + (int64_t)npS * npS, npS, (int)s, ET);
-    project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
+    launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb, (int64_t)npS,
+           (int)s, mc.brows, mc.ldk, mc.linv3);
   }
+  // V = L_SS^-1 Sigma_SD, point-major
+  project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
 }
 
 // Local part of a fit: windows of blocks [w_begin, own_end) are formed and
@@ -973,7 +953,8 @@ void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
 
 template <typename T>
 void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
-                      double* mean, double* var, cudaEvent_t global_done, double* cov, FusedTest* ft) {
+                      double* mean, double* var, cudaEvent_t global_done, double* cov, FusedTest* ft,
+                      int* async_err) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -1209,6 +1190,12 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     if (!on_device) {
       LMA_CK(cudaMemcpyAsync(mean, md, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
       LMA_CK(cudaMemcpyAsync(var, vd, sizeof(double) * U, cudaMemcpyDeviceToHost, st));
+    }
+    if (async_err) {  // enqueued: the status word is read by lma_model_wait, the staging kept
+      launch("k_or_flag", k_or_flag, 1, 32, 0, st, (const int*)perr, async_err);
+      tmp.release();
+      staging().hold = true;
+      return;
     }
     int herr = 0;
     LMA_CK(cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, st));
