@@ -15,6 +15,9 @@ loglik           log N(y_D; mu, Sigma-bar_DD) in summary form:
                  U_mm^T U_mm = R-dot_m).
 predict_cov()    The same local route for the full covariance of each test
                  block (Eq. vapvar on U_n x U_n).
+predict_cov_blocks()  Eq. (vapvar) between any two test blocks U_n x U_n':
+                 the local route on one side, R-bar_{D u'} by the recursion
+                 of Eq. (ares) on the other.
 predict_thm2()   Theorem 2 given Sigma-bar_DU (paper's route; tiny N only).
 predict()        Local route: for u in U_n the row R-bar_{uD} R-bar_DD^-1 is
                  supported on the blocks J = n-B..n+B and equals
@@ -311,6 +314,100 @@ def predict_cov(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True, blo
         hc = sla.solve_triangular(f.Lc, h, lower=True)
         Kuu = cv.K(Xu, Xu) + (cv.sn2 * np.eye(u.size) if noisy else 0.0)
         out[n] = Kuu - Wu.T @ Wu - Ru.T @ Z + hc.T @ hc
+    return out
+
+
+def _rbar_to_test(cv: _Cov, ptr, B: int, k: int, Xq, nq: int, memo: dict):
+    """R-bar_{D_k q} for the test points Xq of test block nq, by Eq. (ares):
+    R_{D_k q} when |k - nq| <= B (in the band); for k < nq - B the recursion
+    R_{D_k D^B_k} R_{D^B_k D^B_k}^-1 R-bar_{D^B_k q} over the blanket of
+    block k; 0 off the band when B = 0.  Only k <= nq + B is asked for."""
+    if k in memo:
+        return memo[k]
+    p = cv.p
+    M = len(ptr) - 1
+    I = _rows(ptr, k)
+    if abs(k - nq) <= B:
+        Wk = cv.W(p.X[I])
+        out = cv.K(p.X[I], Xq) - Wk.T @ cv.W(Xq)           # test points are not in D: no noise
+    elif B == 0:
+        out = np.zeros((I.size, Xq.shape[0]))
+    else:
+        assert k < nq - B
+        last = min(k + B, M - 1)
+        Bk = np.arange(ptr[k + 1], ptr[last + 1])
+        rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, Xq, nq, memo) for j in range(k + 1, last + 1)])
+        R_IB = cv.R_train(I, Bk)
+        R_BB = cv.R_train(Bk, Bk)
+        out = R_IB @ sla.cho_solve(sla.cho_factor(R_BB, lower=True), rho_B)
+    memo[k] = out
+    return out
+
+
+def predict_cov_blocks(f: LMAFit, pairs, XU=None, test_block_ptr=None, noisy: bool = True) -> list:
+    """Predictive covariance between test blocks U_n and U_n' (Eq. vapvar on
+    U_n x U_n') for each requested (n, n'); returns one |U_n| x |U_n'| matrix
+    per pair.  In the whitened support coordinates (W = L_SS^-1 Sigma_S.),
+    Eq. (vapvar) splits as
+        Cov(u, u') = R-bar_{uu'} - R-bar_{uD} R-bar_DD^-1 R-bar_{Du'} + hc_u^T hc_u'
+    (Woodbury on Sigma-bar_DD = Q_DD + R-bar_DD; hc = L_C^-1 h with h the
+    vector of predict()).  For n <= n' the middle term is z_u rho_J with
+    z_u = R_{u D_J} (R-bar_JJ)^-1 on the sub-chain J = n-B..n+B (the local
+    route of predict()) and rho_J = R-bar_{D_J u'} by Eq. (ares)
+    (_rbar_to_test); R-bar_{uu'} is R_{uu'} in the band (|n - n'| <= B; plus
+    sigma_n^2 where a noisy point meets itself) and otherwise
+    R_{u D^B_n} R_{D^B_n D^B_n}^-1 R-bar_{D^B_n u'} (Eq. ares; 0 when B = 0).
+    n > n' is the transpose of (n', n)."""
+    p = f.prob
+    XU = p.XU if XU is None else XU
+    tptr = p.test_block_ptr if test_block_ptr is None else test_block_ptr
+    cv = _Cov(p)
+    ptr = p.block_ptr
+    M = len(ptr) - 1
+    B = f.B
+
+    def side(n):
+        u = np.arange(tptr[n], tptr[n + 1])
+        Jb = list(range(max(0, n - B), min(M - 1, n + B) + 1))
+        rows, P = _subchain_precision(cv, ptr, Jb, B)
+        Xu = XU[u]
+        WJ = cv.W(p.X[rows])
+        Wu = cv.W(Xu)
+        Ru = cv.K(p.X[rows], Xu) - WJ.T @ Wu
+        Z = P @ Ru
+        hc = sla.solve_triangular(f.Lc, WJ @ Z - Wu, lower=True)
+        return u, Jb, Z, hc
+
+    out = []
+    for n, n2 in pairs:
+        n, n2 = int(n), int(n2)
+        if n > n2:
+            out.append(None)   # filled below from (n2, n)
+            continue
+        u, Jb, Z, hc = side(n)
+        u2, _, _, hc2 = side(n2)
+        if u.size == 0 or u2.size == 0:
+            out.append(np.zeros((u.size, u2.size)))
+            continue
+        X1, X2 = XU[u], XU[u2]
+        memo: dict = {}
+        if n2 - n <= B:
+            Rb = cv.K(X1, X2) - cv.W(X1).T @ cv.W(X2)
+            if noisy and n == n2:
+                Rb = Rb + cv.sn2 * np.eye(u.size)
+        elif B == 0:
+            Rb = np.zeros((u.size, u2.size))
+        else:
+            last = min(n + B, M - 1)
+            Bk = np.arange(ptr[n + 1], ptr[last + 1])
+            rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, X2, n2, memo) for j in range(n + 1, last + 1)])
+            R_uB = cv.K(X1, p.X[Bk]) - cv.W(X1).T @ cv.W(p.X[Bk])
+            Rb = R_uB @ sla.cho_solve(sla.cho_factor(cv.R_train(Bk, Bk), lower=True), rho_B)
+        rho_J = np.vstack([_rbar_to_test(cv, ptr, B, k, X2, n2, memo) for k in Jb])
+        out.append(Rb - Z.T @ rho_J + hc.T @ hc2)
+    for i, (n, n2) in enumerate(pairs):
+        if int(n) > int(n2):
+            out[i] = predict_cov_blocks(f, [(n2, n)], XU, tptr, noisy)[0].T
     return out
 
 
