@@ -144,6 +144,28 @@ lma_status lma_predict_cov(const lma_model* model, int64_t u, const double* XU,
                            const int64_t* test_block_ptr, int noisy, int io_on_device,
                            double* mean_out, double* var_out, double* cov_out);
 
+/* lma_predict plus chosen blocks of the predictive covariance between test
+ * blocks: for each requested pair (n, n'), Eq. (vapvar) on U_n x U_n'
+ * (Sigma-bar by Eqs. ares / acov, so off the band Sigma-bar_UU is the
+ * approximation's, not Sigma_UU).  block_pairs (host memory) holds 2*n_pairs
+ * block indices n_0, n'_0, n_1, n'_1, ..., each in [0, M); cov_out receives
+ * the blocks in request order, block i as a row-major |U_n_i| x |U_n'_i|
+ * matrix (host or device memory as io_on_device says), sum_i |U_n_i| |U_n'_i|
+ * doubles in total; a pair with an empty test block contributes nothing.
+ * Requesting every (n, n') gives the whole |U| x |U| covariance.  Evaluation:
+ * the residual part R-bar_UU - R-bar_UD R-bar_DD^-1 R-bar_DU vanishes between
+ * test blocks more than B apart (Eq. ares passes through the training
+ * blankets only) and within the band is a sum of products of the local
+ * route's window right-hand sides; the low-rank part is g_u . g_u' with
+ * g = L_C^-1 h as in the variance.  noisy adds sigma_n^2 where a point meets
+ * itself.  Errors as in lma_predict, and LMA_ERR_INVALID_ARG for a negative
+ * n_pairs, a null block_pairs with n_pairs > 0 or a block index out of
+ * range.                                                                    */
+lma_status lma_predict_cov_blocks(const lma_model* model, int64_t u, const double* XU,
+                                  const int64_t* test_block_ptr, int noisy, int io_on_device,
+                                  int64_t n_pairs, const int64_t* block_pairs,
+                                  double* mean_out, double* var_out, double* cov_out);
+
 /* lma_fit followed by lma_predict in one call: the FP64 global step
  * (Definition 2) runs on a library-owned second stream while the
  * prediction's kernels that do not need its results run on cuda_stream, and

@@ -317,7 +317,19 @@ def predict_cov(f: LMAFit, XU=None, test_block_ptr=None, noisy: bool = True, blo
     return out
 
 
-def _rbar_to_test(cv: _Cov, ptr, B: int, k: int, Xq, nq: int, memo: dict):
+def _blanket_solver(cv: _Cov, ptr, B: int, k: int, cache: dict):
+    """Rows I of D_k, rows Bk of its blanket D^B_k, R_{D_k D^B_k} and the
+    Cholesky factor of R_{D^B_k D^B_k} (computed once per block)."""
+    if k not in cache:
+        M = len(ptr) - 1
+        I = _rows(ptr, k)
+        last = min(k + B, M - 1)
+        Bk = np.arange(ptr[k + 1], ptr[last + 1])
+        cache[k] = (I, Bk, cv.R_train(I, Bk), sla.cho_factor(cv.R_train(Bk, Bk), lower=True))
+    return cache[k]
+
+
+def _rbar_to_test(cv: _Cov, ptr, B: int, k: int, Xq, nq: int, memo: dict, bl: dict):
     """R-bar_{D_k q} for the test points Xq of test block nq, by Eq. (ares):
     R_{D_k q} when |k - nq| <= B (in the band); for k < nq - B the recursion
     R_{D_k D^B_k} R_{D^B_k D^B_k}^-1 R-bar_{D^B_k q} over the blanket of
@@ -335,11 +347,9 @@ def _rbar_to_test(cv: _Cov, ptr, B: int, k: int, Xq, nq: int, memo: dict):
     else:
         assert k < nq - B
         last = min(k + B, M - 1)
-        Bk = np.arange(ptr[k + 1], ptr[last + 1])
-        rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, Xq, nq, memo) for j in range(k + 1, last + 1)])
-        R_IB = cv.R_train(I, Bk)
-        R_BB = cv.R_train(Bk, Bk)
-        out = R_IB @ sla.cho_solve(sla.cho_factor(R_BB, lower=True), rho_B)
+        _, _, R_IB, cf = _blanket_solver(cv, ptr, B, k, bl)
+        rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, Xq, nq, memo, bl) for j in range(k + 1, last + 1)])
+        out = R_IB @ sla.cho_solve(cf, rho_B)
     memo[k] = out
     return out
 
@@ -366,7 +376,13 @@ def predict_cov_blocks(f: LMAFit, pairs, XU=None, test_block_ptr=None, noisy: bo
     M = len(ptr) - 1
     B = f.B
 
+    sides: dict = {}
+    memos: dict = {}
+    bl: dict = {}
+
     def side(n):
+        if n in sides:
+            return sides[n]
         u = np.arange(tptr[n], tptr[n + 1])
         Jb = list(range(max(0, n - B), min(M - 1, n + B) + 1))
         rows, P = _subchain_precision(cv, ptr, Jb, B)
@@ -376,21 +392,16 @@ def predict_cov_blocks(f: LMAFit, pairs, XU=None, test_block_ptr=None, noisy: bo
         Ru = cv.K(p.X[rows], Xu) - WJ.T @ Wu
         Z = P @ Ru
         hc = sla.solve_triangular(f.Lc, WJ @ Z - Wu, lower=True)
-        return u, Jb, Z, hc
+        sides[n] = (u, Jb, Z, hc)
+        return sides[n]
 
-    out = []
-    for n, n2 in pairs:
-        n, n2 = int(n), int(n2)
-        if n > n2:
-            out.append(None)   # filled below from (n2, n)
-            continue
+    def block(n, n2):                                        # n <= n2
         u, Jb, Z, hc = side(n)
         u2, _, _, hc2 = side(n2)
         if u.size == 0 or u2.size == 0:
-            out.append(np.zeros((u.size, u2.size)))
-            continue
+            return np.zeros((u.size, u2.size))
         X1, X2 = XU[u], XU[u2]
-        memo: dict = {}
+        memo = memos.setdefault(n2, {})                      # R-bar_{D_k u'} for the points of block n2
         if n2 - n <= B:
             Rb = cv.K(X1, X2) - cv.W(X1).T @ cv.W(X2)
             if noisy and n == n2:
@@ -399,15 +410,17 @@ def predict_cov_blocks(f: LMAFit, pairs, XU=None, test_block_ptr=None, noisy: bo
             Rb = np.zeros((u.size, u2.size))
         else:
             last = min(n + B, M - 1)
-            Bk = np.arange(ptr[n + 1], ptr[last + 1])
-            rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, X2, n2, memo) for j in range(n + 1, last + 1)])
+            _, Bk, _, cf = _blanket_solver(cv, ptr, B, n, bl)
+            rho_B = np.vstack([_rbar_to_test(cv, ptr, B, j, X2, n2, memo, bl) for j in range(n + 1, last + 1)])
             R_uB = cv.K(X1, p.X[Bk]) - cv.W(X1).T @ cv.W(p.X[Bk])
-            Rb = R_uB @ sla.cho_solve(sla.cho_factor(cv.R_train(Bk, Bk), lower=True), rho_B)
-        rho_J = np.vstack([_rbar_to_test(cv, ptr, B, k, X2, n2, memo) for k in Jb])
-        out.append(Rb - Z.T @ rho_J + hc.T @ hc2)
-    for i, (n, n2) in enumerate(pairs):
-        if int(n) > int(n2):
-            out[i] = predict_cov_blocks(f, [(n2, n)], XU, tptr, noisy)[0].T
+            Rb = R_uB @ sla.cho_solve(cf, rho_B)
+        rho_J = np.vstack([_rbar_to_test(cv, ptr, B, k, X2, n2, memo, bl) for k in Jb])
+        return Rb - Z.T @ rho_J + hc.T @ hc2
+
+    out = []
+    for n, n2 in pairs:
+        n, n2 = int(n), int(n2)
+        out.append(block(n, n2) if n <= n2 else block(n2, n).T)
     return out
 
 

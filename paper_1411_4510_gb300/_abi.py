@@ -15,7 +15,7 @@ EXPORTED = (
     "lma_window_residual", "lma_window_rows", "lma_model_free", "lma_status_string", "lma_last_error_info",
     "lma_kernel_launch_count", "lma_profile_start", "lma_profile_stop", "lma_profile_trace", "lma_tc_gemm_check",
     "lma_global_step_noalloc", "lma_fit_local", "lma_model_local_summary", "lma_model_set_global",
-    "lma_fit_predict", "lma_predict_cov", "lma_model_precision", "lma_autotune", "lma_autotune_pin", "lma_autotune_report",
+    "lma_fit_predict", "lma_predict_cov", "lma_predict_cov_blocks", "lma_model_precision", "lma_autotune", "lma_autotune_pin", "lma_autotune_report",
 )
 
 
@@ -102,6 +102,8 @@ def load(path: str | None = None):
     lib.lma_fit_predict.restype = C.c_int
     lib.lma_predict_cov.argtypes = [vp, C.c_int64, vp, vp, C.c_int, C.c_int, vp, vp, vp]
     lib.lma_predict_cov.restype = C.c_int
+    lib.lma_predict_cov_blocks.argtypes = [vp, C.c_int64, vp, vp, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp]
+    lib.lma_predict_cov_blocks.restype = C.c_int
     lib.lma_profile_start.argtypes = [C.c_char_p]
     lib.lma_profile_start.restype = None
     lib.lma_profile_stop.argtypes = [C.c_char_p, C.c_int, vp, vp, C.c_int]

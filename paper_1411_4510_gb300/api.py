@@ -173,6 +173,57 @@ def lma_predict_cov(model: Model, XU, test_block_ptr, noisy: bool = True):
     return mean, var, covs
 
 
+def lma_predict_cov_blocks(model: Model, XU, test_block_ptr, block_pairs, noisy: bool = True):
+    """(mean, var, blocks): blocks[i] is the |U_n| x |U_n'| predictive
+    covariance between test blocks n and n' for the i-th requested pair
+    (n, n') of block_pairs (Eq. vapvar); numpy for host input, torch CUDA
+    tensors for device input."""
+    lib = _abi.load()
+    keep = []
+    u = int(XU.shape[0])
+    xp, dev = _f64(XU, keep)
+    tp = np.asarray(test_block_ptr, dtype=np.int64)
+    tpp = _i64(tp, keep)
+    bp = np.ascontiguousarray(np.asarray(block_pairs, dtype=np.int64).reshape(-1, 2))
+    sizes = np.diff(tp)
+    size = lambda n: int(sizes[n]) if 0 <= n < sizes.size else 0   # noqa: E731  (the library rejects bad indices)
+    shapes = [(size(a), size(b)) for a, b in bp]
+    total = sum(a * b for a, b in shapes)
+    if dev:
+        mean = torch.empty(u, dtype=torch.float64, device=XU.device)
+        var = torch.empty(u, dtype=torch.float64, device=XU.device)
+        cov = torch.empty(max(total, 1), dtype=torch.float64, device=XU.device)
+        ptrs = mean.data_ptr(), var.data_ptr(), cov.data_ptr()
+    else:
+        mean, var, cov = np.empty(u), np.empty(u), np.empty(max(total, 1))
+        ptrs = mean.ctypes.data, var.ctypes.data, cov.ctypes.data
+    _abi.check(lib.lma_predict_cov_blocks(model.handle, u, xp, tpp, int(bool(noisy)), int(dev), len(bp),
+                                          bp.ctypes.data, *ptrs))
+    blocks, off = [], 0
+    for a, b in shapes:
+        blocks.append(cov[off:off + a * b].reshape(a, b))
+        off += a * b
+    return mean, var, blocks
+
+
+def lma_predict_cov_full(model: Model, XU, test_block_ptr, noisy: bool = True):
+    """(mean, var, cov): the whole |U| x |U| predictive covariance (every
+    block pair through lma_predict_cov_blocks), numpy or torch like XU."""
+    tp = np.asarray(test_block_ptr, dtype=np.int64)
+    M = len(tp) - 1
+    nz = [n for n in range(M) if tp[n + 1] > tp[n]]
+    pairs = [(a, b) for a in nz for b in nz]
+    mean, var, blocks = lma_predict_cov_blocks(model, XU, tp, pairs, noisy)
+    u = int(XU.shape[0])
+    if isinstance(mean, np.ndarray):
+        cov = np.empty((u, u))
+    else:
+        cov = torch.empty((u, u), dtype=torch.float64, device=mean.device)
+    for (a, b), C in zip(pairs, blocks):
+        cov[tp[a]:tp[a + 1], tp[b]:tp[b + 1]] = C
+    return mean, var, cov
+
+
 def lma_fit_predict(X, y, block_ptr, S, B, log_ell, log_sigma_s, log_sigma_n, XU, test_block_ptr, jitter=1e-6,
                     mean=0.0, precision=MIXED, noisy: bool = True, stream=None, keep_model: bool = False):
     """lma_fit + lma_predict in one call (the global step overlaps the

@@ -375,25 +375,42 @@ lma_status lma_fit_predict(const lma_problem* P, const lma_hyper* H, const lma_o
 
 lma_status lma_predict_cov(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
                            int io_on_device, double* mean_out, double* var_out, double* cov_out) {
-  if (!md) return fail(LMA_ERR_INVALID_ARG, "null model");
-  if (u < 0) return fail(LMA_ERR_INVALID_ARG, "negative test count");
-  if (u > 0 && (!XU || !tptr || !mean_out || !var_out || !cov_out)) return fail(LMA_ERR_INVALID_ARG, "null pointer");
+  lma_status cst = lma_predict_checks(md, u, XU, tptr, mean_out, var_out);
+  if (cst != LMA_OK) return cst;
+  if (u > 0 && !cov_out) return fail(LMA_ERR_INVALID_ARG, "null pointer");
   const ModelCore& mc = md->core;
-  if (!mc.have_global) return fail(LMA_ERR_INVALID_ARG, "model has no global step yet (lma_model_set_global)");
-  if (u > 0) {
-    if (tptr[0] != 0 || tptr[mc.M] != u) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr must start at 0, end at u");
-    const int64_t w1 = mc.w0 + (int64_t)mc.wins.size();
-    for (int64_t m = 0; m < mc.M; ++m) {
-      if (tptr[m + 1] < tptr[m]) return fail(LMA_ERR_INVALID_ARG, "test_block_ptr decreases", m);
-      if (tptr[m + 1] > tptr[m] && (std::max<int64_t>(0, m - mc.B) < mc.w0 || m >= w1))
-        return fail(LMA_ERR_INVALID_ARG, "test block outside the windows of this model", m);
-    }
-  }
   return guarded([&] {
     if (mc.prec == LMA_MIXED)
       Impl<float>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out, nullptr, cov_out);
     else
       Impl<double>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out, nullptr, cov_out);
+  });
+}
+
+lma_status lma_predict_cov_blocks(const lma_model* md, int64_t u, const double* XU, const int64_t* tptr, int noisy,
+                                  int io_on_device, int64_t n_pairs, const int64_t* block_pairs, double* mean_out,
+                                  double* var_out, double* cov_out) {
+  lma_status cst = lma_predict_checks(md, u, XU, tptr, mean_out, var_out);
+  if (cst != LMA_OK) return cst;
+  if (n_pairs < 0) return fail(LMA_ERR_INVALID_ARG, "negative pair count");
+  if (n_pairs > 0 && !block_pairs) return fail(LMA_ERR_INVALID_ARG, "null block_pairs");
+  const ModelCore& mc = md->core;
+  int64_t total = 0;
+  for (int64_t i = 0; i < 2 * n_pairs; ++i)
+    if (block_pairs[i] < 0 || block_pairs[i] >= mc.M) return fail(LMA_ERR_INVALID_ARG, "block index out of range", i);
+  if (u > 0)
+    for (int64_t i = 0; i < n_pairs; ++i) {
+      const int64_t a = block_pairs[2 * i], b = block_pairs[2 * i + 1];
+      total += (tptr[a + 1] - tptr[a]) * (tptr[b + 1] - tptr[b]);
+    }
+  if (total > 0 && !cov_out) return fail(LMA_ERR_INVALID_ARG, "null cov_out");
+  return guarded([&] {
+    if (mc.prec == LMA_MIXED)
+      Impl<float>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out, nullptr, cov_out, nullptr, nullptr,
+                           block_pairs, n_pairs);
+    else
+      Impl<double>::predict(mc, u, XU, tptr, noisy, io_on_device, mean_out, var_out, nullptr, cov_out, nullptr,
+                            nullptr, block_pairs, n_pairs);
   });
 }
 

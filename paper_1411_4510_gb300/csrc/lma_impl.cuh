@@ -267,7 +267,8 @@ struct Impl {
   static void check(ModelCore& mc, bool global, int64_t n_total, bool logdet_from_device);
   static void predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy,
                       int on_device, double* mean, double* var, cudaEvent_t global_done = nullptr,
-                      double* cov = nullptr, FusedTest* ft = nullptr, int* async_err = nullptr);
+                      double* cov = nullptr, FusedTest* ft = nullptr, int* async_err = nullptr,
+                      const int64_t* cov_pairs = nullptr, int64_t n_cov_pairs = -1);
   static void fit_predict(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t U, const double* XU,
                           const int64_t* tptr, int noisy, int on_device, double* mean, double* var);
   static void window_residual(ModelCore& mc, const lma_problem* P, const lma_hyper* H, int64_t m, double* out);

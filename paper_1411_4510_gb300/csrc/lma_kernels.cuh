@@ -1151,67 +1151,83 @@ __global__ void __launch_bounds__(NT) k_lc_apply(const T* __restrict__ h, int64_
     }
 }
 
-// Predictive covariance of test block n (Eq. vapvar on U_n x U_n, local
-// route): Cov(u, u') = K(u, u') [+ sigma_n^2 delta] - Vu_u . Vu_u'
-//   - sum over the block's pairs of P_u . P_u' (kept window columns)
-//   + g_u . g_u'  (g = L_C^-1 h).  Items: x = first pair of the block,
-// y = pair count, z / w = 64-row tiles of the block; cov_off[n] is the
-// block's offset in the packed output (row-major |U_n| x |U_n|).
+// Predictive covariance between test blocks n and n2 (Eq. vapvar on
+// U_n x U_n2), one 64 x 64 tile of one requested block per CTA
+// (items: x = request, y / z = 64-row tiles of U_n / U_n2).  With
+// g = L_C^-1 h (the low-rank term of the variance) and, for u in U_n and u'
+// in U_n2,
+//   Cov(u, u') = g_u . g_u' + [|n - n2| <= B] ( K(u, u') [+ sigma_n^2 delta]
+//                - Vu_u . Vu_u' - sum_m P_(n,m)[u] . P_(n2,m)[u'] ),
+// the sum over the windows m = max(n, n2) - B .. min(n, n2) on their kept
+// columns (block columns for m < min(n, n2), all columns for m = min(n, n2)).
+// Off the band the residual part of the covariance vanishes (Eq. ares runs
+// through the training blankets only), and in the band windows before
+// max(n, n2) - B drop out of the sum (their block rows of
+// L_m^-1 R-bar_{W_m u'} are zero); within one block (n = n2) this is the
+// local route of the variance.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_pred_cov(const Pair* __restrict__ pairs, const int4* __restrict__ items,
-                                                 const Win* __restrict__ wins, const T* __restrict__ xu, int d,
-                                                 const T* __restrict__ Vu, const T* __restrict__ P,
-                                                 const T* __restrict__ g, int s, double ss2, double noise,
-                                                 const int64_t* __restrict__ cov_off, double* __restrict__ cov) {
+__global__ void __launch_bounds__(NT) k_pred_xcov(const Pair* __restrict__ pairs, const CovReq* __restrict__ reqs,
+                                                  const int4* __restrict__ items, const Win* __restrict__ wins,
+                                                  const T* __restrict__ xu, int d, const T* __restrict__ Vu,
+                                                  const T* __restrict__ P, const T* __restrict__ g, int s, double ss2,
+                                                  double noise, double* __restrict__ cov) {
   const int4 it = items[blockIdx.x];
-  const Pair first = pairs[it.x];
-  const int a0 = it.z * TB, b0 = it.w * TB, nu = first.nu;
-  const int64_t ub = first.u0;
+  const CovReq rq = reqs[it.x];
+  const int a0 = it.y * TB, b0 = it.z * TB, nua = rq.nua, nub = rq.nub;
+  const int64_t ua = rq.u0a, ub = rq.u0b;
+  const bool band = rq.nm > 0;
   __shared__ GemmSmem<T> sm;
   __shared__ T xa[TB][MAXD + 1];
   __shared__ T xb[TB][MAXD + 1];
-  for (int e = threadIdx.x; e < TB * d; e += NT) {
-    const int r = e / d, q = e % d;
-    xa[r][q] = (a0 + r < nu) ? xu[(ub + a0 + r) * d + q] : T(0);
-    xb[r][q] = (b0 + r < nu) ? xu[(ub + b0 + r) * d + q] : T(0);
-  }
   T sub[4][4] = {}, add[4][4] = {};
-  {
-    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? Vu[(ub + a0 + r) * s + k] : T(0); };
-    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? Vu[(ub + b0 + r) * s + k] : T(0); };
-    tile_mma<T, true, true>(sub, s, sm, fa, fb);
+  if (band) {
+    for (int e = threadIdx.x; e < TB * d; e += NT) {
+      const int r = e / d, q = e % d;
+      xa[r][q] = (a0 + r < nua) ? xu[(ua + a0 + r) * d + q] : T(0);
+      xb[r][q] = (b0 + r < nub) ? xu[(ub + b0 + r) * d + q] : T(0);
+    }
+    {
+      auto fa = [&](int r, int k) -> T { return (a0 + r < nua) ? Vu[(ua + a0 + r) * s + k] : T(0); };
+      auto fb = [&](int r, int k) -> T { return (b0 + r < nub) ? Vu[(ub + b0 + r) * s + k] : T(0); };
+      tile_mma<T, true, true>(sub, s, sm, fa, fb);
+    }
+    for (int j = 0; j < rq.nm; ++j) {
+      const Pair pa = pairs[rq.pa + j], pb = pairs[rq.pb + j];
+      const Win w = wins[pa.win];  // pb.win is the same window
+      const int c0 = (rq.m_lo + j < rq.lo) ? w.nB : 0;
+      const T* Pa = P + pa.pbase;
+      const T* Pb = P + pb.pbase;
+      const int64_t ld = w.npad;
+      auto fa = [&](int r, int k) -> T { return (a0 + r < nua) ? Pa[(int64_t)(a0 + r) * ld + c0 + k] : T(0); };
+      auto fb = [&](int r, int k) -> T { return (b0 + r < nub) ? Pb[(int64_t)(b0 + r) * ld + c0 + k] : T(0); };
+      tile_mma<T, true, true>(sub, w.n - c0, sm, fa, fb);
+    }
   }
-  for (int pi = 0; pi < it.y; ++pi) {
-    const Pair pr = pairs[it.x + pi];
-    const Win w = wins[pr.win];
-    const T* Pp = P + pr.pbase;
-    const int64_t ld = w.npad;
-    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? Pp[(int64_t)(a0 + r) * ld + pr.c0 + k] : T(0); };
-    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? Pp[(int64_t)(b0 + r) * ld + pr.c0 + k] : T(0); };
-    tile_mma<T, true, true>(sub, pr.c1 - pr.c0, sm, fa, fb);
-  }
   {
-    auto fa = [&](int r, int k) -> T { return (a0 + r < nu) ? g[(ub + a0 + r) * s + k] : T(0); };
-    auto fb = [&](int r, int k) -> T { return (b0 + r < nu) ? g[(ub + b0 + r) * s + k] : T(0); };
+    auto fa = [&](int r, int k) -> T { return (a0 + r < nua) ? g[(ua + a0 + r) * s + k] : T(0); };
+    auto fb = [&](int r, int k) -> T { return (b0 + r < nub) ? g[(ub + b0 + r) * s + k] : T(0); };
     tile_mma<T, true, true>(add, s, sm, fa, fb);
   }
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double* C = cov + cov_off[first.n];
+  double* C = cov + rq.off;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int r = ty + 16 * a, c = tx + 16 * b;
       const int i = a0 + r, j = b0 + c;
-      if (i < nu && j < nu) {
-        double d2 = 0.0;
-        for (int q = 0; q < d; ++q) {
-          const double t = (double)xa[r][q] - (double)xb[c][q];
-          d2 += t * t;
+      if (i < nua && j < nub) {
+        double v = (double)add[a][b];
+        if (band) {
+          double d2 = 0.0;
+          for (int q = 0; q < d; ++q) {
+            const double t = (double)xa[r][q] - (double)xb[c][q];
+            d2 += t * t;
+          }
+          v += ss2 * exp(-0.5 * d2) - (double)sub[a][b];
+          if (rq.same && i == j) v += noise;
         }
-        double v = ss2 * exp(-0.5 * d2) - (double)sub[a][b] + (double)add[a][b];
-        if (i == j) v += noise;
-        C[(int64_t)i * nu + j] = v;
+        C[(int64_t)i * nub + j] = v;
       }
     }
 }

@@ -954,7 +954,7 @@ void Impl<T>::fused_rhs(ModelCore& mc, FusedTest& ft, Arena& tmp) {
 template <typename T>
 void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const int64_t* tptr, int noisy, int on_device,
                       double* mean, double* var, cudaEvent_t global_done, double* cov, FusedTest* ft,
-                      int* async_err) {
+                      int* async_err, const int64_t* cov_pairs, int64_t n_cov_pairs) {
   cudaStream_t st = mc.st;
   Arena tmp;
   tmp.st = st;
@@ -1161,30 +1161,60 @@ void Impl<T>::predict(const ModelCore& mc, int64_t U, const double* XU, const in
     const double prior = mc.ss2 + (noisy ? mc.sn2 : 0.0);
     launch("k_pred_final", k_pred_final<T>, nblk(U * 32), NT, 0, st, Vu, U, (int)s, mc.beta, t1, t2, part, ntile_var,
            mc.mu, prior, md, vd);
-    if (cov) {  // covariance of each test block, packed row-major block after block
-      std::vector<int64_t> off(M, 0);
+    if (cov) {
+      // requested blocks of the covariance between test blocks (Eq. vapvar on
+      // U_n x U_n2), packed row-major in request order; without a request
+      // list, the block of every test block with itself, block after block
+      std::vector<int> first(M, -1);  // first pair of each test block
+      for (const int4& t : tb) first[pairs[t.x].n] = t.x;
+      std::vector<int64_t> req;
+      if (n_cov_pairs < 0) {
+        for (int64_t nb = 0; nb < M; ++nb) {
+          req.push_back(nb);
+          req.push_back(nb);
+        }
+      } else {
+        req.assign(cov_pairs, cov_pairs + 2 * n_cov_pairs);
+      }
+      std::vector<CovReq> rq;
       std::vector<int4> it_c;
       int64_t total = 0;
-      for (const int4& t : tb) {
-        const Pair& f = pairs[t.x];
-        off[f.n] = total;
-        total += (int64_t)t.w * t.w;
-        const int nt = (t.w + TB - 1) / TB;
-        for (int a = 0; a < nt; ++a)
-          for (int b = 0; b < nt; ++b) it_c.push_back(make_int4(t.x, t.y, a, b));
+      for (size_t i = 0; i + 1 < req.size(); i += 2) {
+        const int64_t n1 = req[i], n2 = req[i + 1];
+        CovReq c{};
+        c.off = total;
+        c.u0a = (int)tptr[n1];
+        c.nua = (int)(tptr[n1 + 1] - tptr[n1]);
+        c.u0b = (int)tptr[n2];
+        c.nub = (int)(tptr[n2 + 1] - tptr[n2]);
+        total += (int64_t)c.nua * c.nub;
+        if (c.nua == 0 || c.nub == 0) continue;
+        c.lo = (int)std::min(n1, n2);
+        const int64_t hi = std::max(n1, n2);
+        c.same = n1 == n2;
+        if (hi - c.lo <= B) {
+          c.m_lo = (int)std::max<int64_t>(0, hi - B);
+          c.nm = c.lo - c.m_lo + 1;
+          c.pa = first[n1] + (int)(c.m_lo - std::max<int64_t>(0, n1 - B));
+          c.pb = first[n2] + (int)(c.m_lo - std::max<int64_t>(0, n2 - B));
+        }
+        const int ri = (int)rq.size();
+        rq.push_back(c);
+        for (int a = 0; a < (c.nua + TB - 1) / TB; ++a)
+          for (int b = 0; b < (c.nub + TB - 1) / TB; ++b) it_c.push_back(make_int4(ri, a, b, 0));
       }
       T* g = tmp.alloc<T>(U * s);
       launch("k_lc_apply", k_lc_apply<T>, dim3(nblk(s, TB), nblk(U, TB)), NT, 0, st, (const T*)h, U, (int)s,
              (const T*)mc.LcT, g);
-      int64_t* offd = tmp.alloc<int64_t>(M);
+      CovReq* rqd = tmp.alloc<CovReq>(rq.size());
       int4* icd = tmp.alloc<int4>(it_c.size());
-      stage_copy(offd, off.data(), sizeof(int64_t) * M, st);
+      stage_copy(rqd, rq.data(), sizeof(CovReq) * rq.size(), st);
       stage_copy(icd, it_c.data(), sizeof(int4) * it_c.size(), st);
       double* cd = on_device ? cov : tmp.alloc<double>(total);
       if (!it_c.empty())
-        launch("k_pred_cov", k_pred_cov<T>, (unsigned)it_c.size(), NT, 0, st, pd, (const int4*)icd, mc.wins_d,
-               (const T*)xu, d, (const T*)Vu, (const T*)Pbuf, (const T*)g, (int)s, mc.ss2, noisy ? mc.sn2 : 0.0,
-               (const int64_t*)offd, cd);
+        launch("k_pred_xcov", k_pred_xcov<T>, (unsigned)it_c.size(), NT, 0, st, pd, (const CovReq*)rqd,
+               (const int4*)icd, mc.wins_d, (const T*)xu, d, (const T*)Vu, (const T*)Pbuf, (const T*)g, (int)s,
+               mc.ss2, noisy ? mc.sn2 : 0.0, cd);
       if (!on_device && total) LMA_CK(cudaMemcpyAsync(cov, cd, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
     }
     if (!on_device) {

@@ -51,4 +51,23 @@ struct Pair {
   int n;          // test block
 };
 
+// One requested block of the predictive covariance between test blocks n and
+// n2 (Eq. vapvar on U_n x U_n2), written row-major at element `off` of the
+// output.  In the band (|n - n2| <= B) the residual part sums the products of
+// the right-hand sides of the pairs (n, m) and (n2, m) over the windows
+// m = m_lo .. m_lo + nm - 1 (m_lo = max(0, max(n, n2) - B), up to min(n, n2));
+// the pairs of one test block are consecutive in m, so pair index pa + j is
+// (n, m_lo + j) and pb + j is (n2, m_lo + j).  Off the band nm = 0 and only
+// the low-rank term remains.
+struct CovReq {
+  int64_t off;  // element offset of the block in the output
+  int u0a, nua;  // test rows of block n
+  int u0b, nub;  // test rows of block n2
+  int pa, pb;    // pair indices of (n, m_lo) and (n2, m_lo)
+  int nm;        // number of windows in the sum (0: off the band)
+  int lo;        // min(n, n2): windows m < lo keep their block columns only
+  int m_lo;      // first window of the sum
+  int same;      // n == n2: noise on the diagonal
+};
+
 }  // namespace lma
