@@ -537,15 +537,13 @@ __device__ bool tile_product2(TcSmem<BN>& sm, TcPipe& p, uint32_t tmem, int K, R
 
 namespace lma {
 
-// Sweep update of column panel kp on the tensor cores (mixed form).  CTA
-// (window x, row tile y) owns rows [k0 + 128 y, k0 + 128 y + 128) of the
-// window buffer: T = A_{rows, panel} - A_{rows, kb:k0} A_{panel, kb:k0}^T with
-// the product on tcgen05 (3xTF32); columns [0, kb) were applied by the
-// super-panel update (kb = 0 without one).  The diagonal 64x64 block (first
-// rows of y = 0) is factorised in shared memory; every other row keeps T.
-// The mixed sweep launches it for the row tile holding the diagonal block
-// only (y = 0, K = 0: the first panel of a 128-column group); the rows
-// below are solved by k_chol_panel2_tc.
+// Diagonal block of column panel kp on the tensor cores (mixed form), one
+// CTA per window (grid x = window, y = 1):
+//   D = A_{kk} - A_{k, kb:k0} A_{k, kb:k0}^T   (3xTF32 on tcgen05; skipped when kb = k0)
+// over the 64 rows of the block, then D = L_kk L_kk^T factorised in shared
+// memory (L_kk and inv(L_kk) written; *info set if D is not positive
+// definite).  Columns [0, kb) were applied by the wider updates; the rows
+// below the block are left to the panel kernels.
 __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__ wins, float* __restrict__ buf,
                                                       float* __restrict__ dinv, int* __restrict__ info, int kp,
                                                       int kb, int* __restrict__ err) {
@@ -578,7 +576,7 @@ __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__
   if (K > 0) {
     auto rowA = [&](int r) -> const float* {
       const int row = r0 + r;
-      return row < w.rows ? A + (int64_t)row * ld + kb : nullptr;
+      return (r < TB && row < w.rows) ? A + (int64_t)row * ld + kb : nullptr;
     };
     auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld + kb; };
     ok = tile_product<64>(sm, pipe, tmem, K, rowA, rowB);
@@ -603,28 +601,18 @@ __global__ void __launch_bounds__(256, 2) k_chol_step_tc(const Win* __restrict__
   // all MMAs have completed (tile_product drained both stages): stage memory is free
   float* scratch = reinterpret_cast<float*>(&sm.st[0]);
   float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
-  const bool diag = (blockIdx.y == 0) && (rl < TB);
-  if (row < w.rows) {
-    float* dst = A + (int64_t)row * ld + k0 + half * 32;
-    float4 av[8];  // all loads first: they are independent of the stores below
+  if (row < w.rows && rl < TB) {  // the diagonal block's rows only; the rows below are left to the panel kernels
+    const float* src = A + (int64_t)row * ld + k0 + half * 32;
+    float4 av[8];
 #pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(dst + 4 * j4);
+    for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(src + 4 * j4);
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
-      float4 a = av[j4];
-      a.x -= v[4 * j4 + 0];
-      a.y -= v[4 * j4 + 1];
-      a.z -= v[4 * j4 + 2];
-      a.w -= v[4 * j4 + 3];
-      if (diag) {
-        float* d = &Dm[rl][half * 32 + 4 * j4];
-        d[0] = a.x;
-        d[1] = a.y;
-        d[2] = a.z;
-        d[3] = a.w;
-      } else {
-        *reinterpret_cast<float4*>(dst + 4 * j4) = a;
-      }
+      float* d = &Dm[rl][half * 32 + 4 * j4];
+      d[0] = av[j4].x - v[4 * j4 + 0];
+      d[1] = av[j4].y - v[4 * j4 + 1];
+      d[2] = av[j4].z - v[4 * j4 + 2];
+      d[3] = av[j4].w - v[4 * j4 + 3];
     }
   }
   fence_before_sync();
@@ -1000,6 +988,297 @@ __global__ void __launch_bounds__(256, 2) k_chol_panel2_tc(const Win* __restrict
   if (diag && ok)
     diag_factor<float>(Dm, A + (int64_t)(k0 + TB) * ld + k0 + TB, ld, dinv + w.dinv + (int64_t)(kp + 1) * TB * TB,
                        info + blockIdx.y, k0 + TB);
+}
+
+namespace tc {
+
+// Persistent panel kernel (below): 4 producer warps, 1 MMA warp, 4 epilogue
+// warps.  Operands are 64 values of K wide, stored as two 128-byte-swizzled
+// 32-wide halves (TF32 hi and lo of each).
+constexpr int kPtProducers = 4, kPtEpilogue = 4;
+constexpr int kPtThreads = 32 * (kPtProducers + 1 + kPtEpilogue);
+
+struct alignas(1024) PtTileA {  // 128 rows x 64
+  float hi[2][128 * 32];
+  float lo[2][128 * 32];
+};
+struct alignas(1024) PtTileB {  // 64 rows x 64
+  float hi[2][64 * 32];
+  float lo[2][64 * 32];
+};
+struct PtSmem {
+  PtTileA a[2];     // per item in flight: the update's left operand, then T
+  PtTileB b1, b2;   // per window: the update's right operand, inv(L_kk)
+  uint64_t full[2], tfull[2], empty[2], upd[2], sol[2], afree[2], bfull, bempty, done;
+  uint32_t tmem;
+  int abort;
+};
+
+// TF32 hi/lo of 4 K-consecutive values at (row, k), k < 64, of a 64-wide tile
+template <class Tile>
+__device__ __forceinline__ void pt_store(Tile& t, uint32_t row, uint32_t k, float4 v) {
+  store_split4(t.hi[k >> 5], t.lo[k >> 5], row, k & 31u, v);
+}
+
+// 3xTF32 product of a 128 x 64 tile (a) with a 64 x 64 tile (b)^T into the
+// 64 accumulator columns at d; `acc` = 0 starts from zero.
+__device__ __forceinline__ void pt_mma(uint32_t d, const PtTileA& a, const PtTileB& b, uint32_t acc) {
+  const uint32_t idesc = idesc_tf32(128, 64);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t ah = smem_addr(a.hi[h]), al = smem_addr(a.lo[h]);
+    const uint32_t bh = smem_addr(b.hi[h]), bl = smem_addr(b.lo[h]);
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint32_t o = ks * 32;
+      mma_tf32(d, sdesc_sw128(ah + o), sdesc_sw128(bh + o), idesc, (acc || h > 0 || ks > 0) ? 1u : 0u);
+      mma_tf32(d, sdesc_sw128(ah + o), sdesc_sw128(bl + o), idesc, 1u);
+      mma_tf32(d, sdesc_sw128(al + o), sdesc_sw128(bh + o), idesc, 1u);
+    }
+  }
+}
+
+}  // namespace tc
+
+// Column panel kp of every window, for the rows below its diagonal block, as
+// a persistent kernel (one CTA per SM over a contiguous range of
+// (window, 128-row tile) items, window-major):
+//   T = A_{rows, panel} - A_{rows, kfrom:k0} A_{panel, kfrom:k0}^T   (K = k0 - kfrom, 0 or 64)
+//   A_{rows, panel} <- T inv(L_kk)^T
+// with both products on tcgen05 (3xTF32).  The diagonal block L_kk and its
+// inverse come from k_chol_step_tc.  Warp roles:
+//   producers (warps 0-3): per window, the right operands (A_{panel, kfrom:k0}
+//     and inv(L_kk)) split into TF32 hi/lo; per item, the left operand
+//     (A_{rows, kfrom:k0}, or A_{rows, panel} when K = 0), loaded one item
+//     ahead into registers, split into one of two stages;
+//   MMA warp (warp 4, lane 0 issues): the update into the item's
+//     accumulator (one of two, 64 columns each), then the solve;
+//   epilogue (warps 5-8, one row per thread): T = own row - update, written
+//     split into the item's stage as the solve's left operand; then the
+//     solved row is stored.
+// Two items are in flight, so one item's loads overlap another's products
+// and stores.  Every wait is bounded; on a timeout the CTA raises *err,
+// every role leaves its loop and the MMA warp waits for its products before
+// the tensor memory is freed.
+__global__ void __launch_bounds__(tc::kPtThreads, 1) k_chol_panel_pt(const Win* __restrict__ wins, int nwin,
+                                                                   float* __restrict__ buf,
+                                                                   const float* __restrict__ dinv, int kp, int kfrom,
+                                                                   int ntile, int* __restrict__ err) {
+  grid_dep_wait();
+  grid_dep_launch();
+  using namespace tc;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PtSmem& sm = *reinterpret_cast<PtSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k0 = kp * TB;
+  const bool upd = kfrom < k0;  // K = 64
+  const int64_t total = (int64_t)ntile * nwin;
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t ibeg = (int64_t)blockIdx.x * per, iend = min(total, ibeg + per);
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&sm.full[s], kPtProducers);
+      mbar_init(&sm.tfull[s], kPtEpilogue);
+      mbar_init(&sm.empty[s], 1);
+      mbar_init(&sm.upd[s], 1);
+      mbar_init(&sm.sol[s], 1);
+      mbar_init(&sm.afree[s], kPtEpilogue);
+    }
+    mbar_init(&sm.bfull, kPtProducers);
+    mbar_init(&sm.bempty, 1);
+    mbar_init(&sm.done, 1);
+    sm.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == kPtProducers) tmem_alloc(&sm.tmem, 128);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  volatile int* abort_flag = &sm.abort;
+  // item i -> window and first row; false when the tile holds no rows of the window
+  auto item = [&](int64_t i, int& wi, int& r0) -> bool {
+    wi = (int)(i / ntile);
+    const Win& w = wins[wi];
+    r0 = k0 + TB + (int)(i % ntile) * 128;
+    return k0 < w.npad && r0 < w.rows;
+  };
+  // bounded wait by lane 0, result shared with the warp
+  auto wait_warp = [&](uint64_t* bar, uint32_t parity) -> bool {
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(bar, parity) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) *abort_flag = 1;
+    return ok != 0;
+  };
+
+  if (warp < kPtProducers) {
+    // ---------------- producers ----------------
+    const int pt = tid;  // 0..127
+    float4 ra[16];
+    auto load_a = [&](int wi, int r0) {
+      const Win w = wins[wi];
+      const float* A = buf + w.base;
+      const int col = upd ? kfrom : k0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int i = pt + 128 * j, row = i >> 4, c4 = i & 15;
+        ra[j] = (r0 + row < w.rows) ? *reinterpret_cast<const float4*>(A + (int64_t)(r0 + row) * w.npad + col + 4 * c4)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    int64_t nxt = ibeg;
+    int wn = 0, rn = 0;
+    while (nxt < iend && !item(nxt, wn, rn)) ++nxt;
+    if (nxt < iend) load_a(wn, rn);
+    int t = 0, v = -1, wcur = -1;
+    while (nxt < iend) {
+      const int wi = wn, r0 = rn;
+      (void)r0;
+      const int s = t & 1, u = t >> 1;
+      if (wi != wcur) {  // right operands of a new window
+        ++v;
+        wcur = wi;
+        if (v >= 1 && !wait_warp(&sm.bempty, (v - 1) & 1)) break;
+        if (*abort_flag) break;
+        const Win w = wins[wi];
+        const float* A = buf + w.base;
+        const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int i = pt + 128 * j, row = i >> 4, c4 = i & 15;
+          if (upd) pt_store(sm.b1, row, 4 * c4, *reinterpret_cast<const float4*>(A + (int64_t)(k0 + row) * w.npad + kfrom + 4 * c4));
+          pt_store(sm.b2, row, 4 * c4, *reinterpret_cast<const float4*>(Dv + row * TB + 4 * c4));
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.bfull);
+      }
+      if (t >= 2 && !wait_warp(&sm.empty[s], (u - 1) & 1)) break;
+      if (*abort_flag) break;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int i = pt + 128 * j;
+        pt_store(sm.a[s], i >> 4, 4 * (i & 15), ra[j]);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.full[s]);
+      ++t;
+      ++nxt;
+      while (nxt < iend && !item(nxt, wn, rn)) ++nxt;
+      if (nxt < iend) load_a(wn, rn);
+    }
+  } else if (warp == kPtProducers) {
+    // ---------------- MMA issue (whole warp loops, lane 0 issues) ----------------
+    const uint32_t tmem = sm.tmem;
+    int t = 0, v = -1, wcur = -1;
+    int wi = 0, r0 = 0;
+    int64_t i = ibeg;
+    while (i < iend && !item(i, wi, r0)) ++i;
+    while (i < iend) {
+      int wn = 0, rn = 0;
+      int64_t nx = i + 1;
+      while (nx < iend && !item(nx, wn, rn)) ++nx;
+      const bool last_of_window = nx >= iend || wn != wi;
+      const int s = t & 1, u = t >> 1;
+      const uint32_t d = tmem + 64u * (uint32_t)s;
+      if (*abort_flag) break;
+      if (wi != wcur) {
+        ++v;
+        wcur = wi;
+        if (!wait_warp(&sm.bfull, v & 1)) break;
+      }
+      if (t >= 2 && !wait_warp(&sm.afree[s], (u - 1) & 1)) break;
+      if (!wait_warp(&sm.full[s], u & 1)) break;
+      fence_after_sync();
+      if (upd) {
+        if (lane == 0) {
+          pt_mma(d, sm.a[s], sm.b1, 0u);
+          mma_commit(&sm.upd[s]);
+        }
+        __syncwarp();
+        if (!wait_warp(&sm.tfull[s], u & 1)) break;
+        fence_after_sync();
+      }
+      if (lane == 0) {
+        pt_mma(d, sm.a[s], sm.b2, 0u);
+        mma_commit(&sm.sol[s]);
+        mma_commit(&sm.empty[s]);
+        if (last_of_window) mma_commit(&sm.bempty);
+      }
+      __syncwarp();
+      ++t;
+      i = nx;
+      wi = wn;
+      r0 = rn;
+    }
+    if (lane == 0) mma_commit(&sm.done);  // arrives once every MMA issued above has completed
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: one row per thread ----------------
+    const int q = warp & 3, e = q * 32 + lane;  // tensor-memory lane quadrant of this warp
+    const uint32_t tl = sm.tmem + ((uint32_t)(q * 32) << 16);
+    int t = 0;
+    for (int64_t i = ibeg; i < iend; ++i) {
+      int wi, r0;
+      if (!item(i, wi, r0)) continue;
+      const int s = t & 1, u = t >> 1;
+      const Win w = wins[wi];
+      const int row = r0 + e;
+      float* dst = buf + w.base + (int64_t)row * w.npad + k0;
+      if (*abort_flag) break;
+      if (upd) {
+        float4 own[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          own[j] = row < w.rows ? *reinterpret_cast<const float4*>(dst + 4 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!wait_warp(&sm.upd[s], u & 1)) break;
+        fence_after_sync();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          float x[16];
+          tmem_ld16(tl + 64u * (uint32_t)s + 16u * (uint32_t)g, x);
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4) {
+            float4 a = own[4 * g + j4];
+            a.x -= x[4 * j4];
+            a.y -= x[4 * j4 + 1];
+            a.z -= x[4 * j4 + 2];
+            a.w -= x[4 * j4 + 3];
+            pt_store(sm.a[s], e, 16 * g + 4 * j4, a);
+          }
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.tfull[s]);
+      }
+      if (!wait_warp(&sm.sol[s], u & 1)) break;
+      fence_after_sync();
+      float x[64];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float y[16];
+        tmem_ld16(tl + 64u * (uint32_t)s + 16u * (uint32_t)g, y);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[16 * g + j] = y[j];
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.afree[s]);
+      if (row < w.rows)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          *reinterpret_cast<float4*>(dst + 4 * j) = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+      ++t;
+    }
+  }
+  // every MMA this CTA issued has completed before its tensor memory is freed
+  const bool okd = mbar_wait(&sm.done, 0);
+  if ((!okd || *abort_flag) && tid == 0) atomicExch(err, 1);
+  fence_before_sync();
+  __syncthreads();
+  if (warp == kPtProducers) tmem_dealloc(sm.tmem, 128);
 }
 
 // Forward solve of the prediction right-hand sides on the tensor cores: CTA
