@@ -992,10 +992,11 @@ __global__ void __launch_bounds__(256, 2) k_chol_panel2_tc(const Win* __restrict
 
 namespace tc {
 
-// Persistent panel kernel (below): 4 producer warps, 1 MMA warp, 4 epilogue
-// warps.  Operands are 64 values of K wide, stored as two 128-byte-swizzled
-// 32-wide halves (TF32 hi and lo of each).
-constexpr int kPtProducers = 4, kPtEpilogue = 4;
+// Persistent panel kernel (below): 8 producer warps, 1 MMA warp, 4 epilogue
+// warps (13 warps: at most 4 on a scheduler, so 128 registers a thread).
+// Operands are 64 values of K wide, stored as two 128-byte-swizzled 32-wide
+// halves (TF32 hi and lo of each).
+constexpr int kPtProducers = 8, kPtEpilogue = 4;
 constexpr int kPtThreads = 32 * (kPtProducers + 1 + kPtEpilogue);
 
 struct alignas(1024) PtTileA {  // 128 rows x 64
@@ -1009,6 +1010,7 @@ struct alignas(1024) PtTileB {  // 64 rows x 64
 struct PtSmem {
   PtTileA a[2];     // per item in flight: the update's left operand, then T
   PtTileB b1, b2;   // per window: the update's right operand, inv(L_kk)
+  float xo[128 * 64];  // epilogue: rows between tensor memory (a row a thread) and coalesced global access
   uint64_t full[2], tfull[2], empty[2], upd[2], sol[2], afree[2], bfull, bempty, done;
   uint32_t tmem;
   int abort;
@@ -1047,20 +1049,20 @@ __device__ __forceinline__ void pt_mma(uint32_t d, const PtTileA& a, const PtTil
 //   A_{rows, panel} <- T inv(L_kk)^T
 // with both products on tcgen05 (3xTF32).  The diagonal block L_kk and its
 // inverse come from k_chol_step_tc.  Warp roles:
-//   producers (warps 0-3): per window, the right operands (A_{panel, kfrom:k0}
+//   producers (warps 0-7): per window, the right operands (A_{panel, kfrom:k0}
 //     and inv(L_kk)) split into TF32 hi/lo; per item, the left operand
-//     (A_{rows, kfrom:k0}, or A_{rows, panel} when K = 0), loaded one item
+//     (A_{rows, kfrom:k0}, or A_{rows, panel} when K = 0), loaded two items
 //     ahead into registers, split into one of two stages;
-//   MMA warp (warp 4, lane 0 issues): the update into the item's
+//   MMA warp (warp 8, lane 0 issues): the update into the item's
 //     accumulator (one of two, 64 columns each), then the solve;
-//   epilogue (warps 5-8, one row per thread): T = own row - update, written
-//     split into the item's stage as the solve's left operand; then the
-//     solved row is stored.
+//   epilogue (4 warps, a quarter of the rows each): T = own rows - update,
+//     written split into the item's stage as the solve's left operand; then
+//     the solved rows are stored (coalesced through shared memory).
 // Two items are in flight, so one item's loads overlap another's products
 // and stores.  Every wait is bounded; on a timeout the CTA raises *err,
 // every role leaves its loop and the MMA warp waits for its products before
 // the tensor memory is freed.
-__global__ void __launch_bounds__(tc::kPtThreads, 1) k_chol_panel_pt(const Win* __restrict__ wins, int nwin,
+__global__ void __maxnreg__(128) k_chol_panel_pt(const Win* __restrict__ wins, int nwin,
                                                                    float* __restrict__ buf,
                                                                    const float* __restrict__ dinv, int kp, int kfrom,
                                                                    int ntile, int* __restrict__ err) {
@@ -1112,61 +1114,76 @@ __global__ void __launch_bounds__(tc::kPtThreads, 1) k_chol_panel_pt(const Win* 
   };
 
   if (warp < kPtProducers) {
-    // ---------------- producers ----------------
-    const int pt = tid;  // 0..127
-    float4 ra[16];
-    auto load_a = [&](int wi, int r0) {
+    // ---------------- producers: two items' loads in flight ----------------
+    constexpr int PT = 32 * kPtProducers, NA = 128 * 16 / PT, NB = 64 * 16 / PT;  // float4 per thread
+    const int pt = tid;
+    float4 ra[2][NA];
+    auto load_a = [&](int wi, int r0, float4 (&x)[NA]) {
       const Win w = wins[wi];
       const float* A = buf + w.base;
       const int col = upd ? kfrom : k0;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = pt + 128 * j, row = i >> 4, c4 = i & 15;
-        ra[j] = (r0 + row < w.rows) ? *reinterpret_cast<const float4*>(A + (int64_t)(r0 + row) * w.npad + col + 4 * c4)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < NA; ++j) {
+        const int i = pt + PT * j, row = i >> 4, c4 = i & 15;
+        x[j] = (r0 + row < w.rows) ? *reinterpret_cast<const float4*>(A + (int64_t)(r0 + row) * w.npad + col + 4 * c4)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    int64_t nxt = ibeg;
-    int wn = 0, rn = 0;
-    while (nxt < iend && !item(nxt, wn, rn)) ++nxt;
-    if (nxt < iend) load_a(wn, rn);
+    auto next_item = [&](int64_t from, int& wi, int& r0) -> int64_t {
+      while (from < iend && !item(from, wi, r0)) ++from;
+      return from;
+    };
+    int64_t cur[2];
+    int wq[2] = {0, 0}, rq[2] = {0, 0};
+    cur[0] = next_item(ibeg, wq[0], rq[0]);
+    if (cur[0] < iend) load_a(wq[0], rq[0], ra[0]);
+    cur[1] = cur[0] < iend ? next_item(cur[0] + 1, wq[1], rq[1]) : iend;
+    if (cur[1] < iend) load_a(wq[1], rq[1], ra[1]);
     int t = 0, v = -1, wcur = -1;
-    while (nxt < iend) {
-      const int wi = wn, r0 = rn;
-      (void)r0;
+    // one item from register set P: stage, then refill the set with the item two ahead
+    auto step = [&](auto P) -> bool {
+      constexpr int p = decltype(P)::value;
+      const int wi = wq[p];
       const int s = t & 1, u = t >> 1;
       if (wi != wcur) {  // right operands of a new window
         ++v;
         wcur = wi;
-        if (v >= 1 && !wait_warp(&sm.bempty, (v - 1) & 1)) break;
-        if (*abort_flag) break;
+        if (v >= 1 && !wait_warp(&sm.bempty, (v - 1) & 1)) return false;
+        if (*abort_flag) return false;
         const Win w = wins[wi];
         const float* A = buf + w.base;
         const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int i = pt + 128 * j, row = i >> 4, c4 = i & 15;
-          if (upd) pt_store(sm.b1, row, 4 * c4, *reinterpret_cast<const float4*>(A + (int64_t)(k0 + row) * w.npad + kfrom + 4 * c4));
+        for (int j = 0; j < NB; ++j) {
+          const int i = pt + PT * j, row = i >> 4, c4 = i & 15;
+          if (upd)
+            pt_store(sm.b1, row, 4 * c4, *reinterpret_cast<const float4*>(A + (int64_t)(k0 + row) * w.npad + kfrom + 4 * c4));
           pt_store(sm.b2, row, 4 * c4, *reinterpret_cast<const float4*>(Dv + row * TB + 4 * c4));
         }
         fence_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.bfull);
       }
-      if (t >= 2 && !wait_warp(&sm.empty[s], (u - 1) & 1)) break;
-      if (*abort_flag) break;
+      if (t >= 2 && !wait_warp(&sm.empty[s], (u - 1) & 1)) return false;
+      if (*abort_flag) return false;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = pt + 128 * j;
-        pt_store(sm.a[s], i >> 4, 4 * (i & 15), ra[j]);
+      for (int j = 0; j < NA; ++j) {
+        const int i = pt + PT * j;
+        pt_store(sm.a[s], i >> 4, 4 * (i & 15), ra[p][j]);
       }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.full[s]);
       ++t;
-      ++nxt;
-      while (nxt < iend && !item(nxt, wn, rn)) ++nxt;
-      if (nxt < iend) load_a(wn, rn);
+      const int64_t after = cur[p ^ 1] < iend ? cur[p ^ 1] : iend;
+      cur[p] = after < iend ? next_item(after + 1, wq[p], rq[p]) : iend;
+      if (cur[p] < iend) load_a(wq[p], rq[p], ra[p]);
+      return true;
+    };
+    while (cur[0] < iend) {
+      if (!step(std::integral_constant<int, 0>{})) break;
+      if (cur[1] >= iend) break;
+      if (!step(std::integral_constant<int, 1>{})) break;
     }
   } else if (warp == kPtProducers) {
     // ---------------- MMA issue (whole warp loops, lane 0 issues) ----------------
@@ -1215,61 +1232,83 @@ __global__ void __launch_bounds__(tc::kPtThreads, 1) k_chol_panel_pt(const Win* 
     if (lane == 0) mma_commit(&sm.done);  // arrives once every MMA issued above has completed
     __syncwarp();
   } else {
-    // ---------------- epilogue: one row per thread ----------------
-    const int q = warp & 3, e = q * 32 + lane;  // tensor-memory lane quadrant of this warp
+    // ---------------- epilogue ----------------
+    // Tensor memory gives a row per thread; global memory is read and
+    // written coalesced (lane L: row 2k + L/16 of the warp's 32, float4
+    // L%16, k = 0..15), through the warp's 32 rows of xo (float4 slots
+    // swizzled by the row, so that both access patterns are conflict-free).
+    const int q = warp & 3;  // tensor-memory lane quadrant: rows 32q .. 32q + 31 of the item
     const uint32_t tl = sm.tmem + ((uint32_t)(q * 32) << 16);
+    float4* xs = reinterpret_cast<float4*>(sm.xo) + q * 32 * 16;
+    auto xs_at = [&](int r, int c4) -> float4& { return xs[r * 16 + (c4 ^ (r & 15))]; };
+    const int cr = lane >> 4, cc = lane & 15;
+    auto rows_to_xs = [&](int s) {  // the 64 accumulator columns of this lane's row into xo
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float x[16];
+        tmem_ld16(tl + 64u * (uint32_t)s + 16u * (uint32_t)g, x);
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4)
+          xs_at(lane, 4 * g + j4) = make_float4(x[4 * j4], x[4 * j4 + 1], x[4 * j4 + 2], x[4 * j4 + 3]);
+      }
+    };
+    float4 own[16];  // the warp's rows of the current item's panel (update form), loaded one solve ahead
+    auto load_own = [&](int64_t i) {
+      int wi, r0;
+      while (i < iend && !item(i, wi, r0)) ++i;
+      if (i >= iend) return;
+      const Win w = wins[wi];
+      const float* src = buf + w.base + k0 + 4 * cc;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int row = r0 + 32 * q + 2 * k + cr;
+        own[k] = row < w.rows ? *reinterpret_cast<const float4*>(src + (int64_t)row * w.npad)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    if (upd) load_own(ibeg);
     int t = 0;
     for (int64_t i = ibeg; i < iend; ++i) {
       int wi, r0;
       if (!item(i, wi, r0)) continue;
       const int s = t & 1, u = t >> 1;
       const Win w = wins[wi];
-      const int row = r0 + e;
-      float* dst = buf + w.base + (int64_t)row * w.npad + k0;
       if (*abort_flag) break;
       if (upd) {
-        float4 own[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          own[j] = row < w.rows ? *reinterpret_cast<const float4*>(dst + 4 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (!wait_warp(&sm.upd[s], u & 1)) break;
         fence_after_sync();
+        rows_to_xs(s);
+        __syncwarp();
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          float x[16];
-          tmem_ld16(tl + 64u * (uint32_t)s + 16u * (uint32_t)g, x);
-#pragma unroll
-          for (int j4 = 0; j4 < 4; ++j4) {
-            float4 a = own[4 * g + j4];
-            a.x -= x[4 * j4];
-            a.y -= x[4 * j4 + 1];
-            a.z -= x[4 * j4 + 2];
-            a.w -= x[4 * j4 + 3];
-            pt_store(sm.a[s], e, 16 * g + 4 * j4, a);
-          }
+        for (int k = 0; k < 16; ++k) {
+          const int r = 2 * k + cr;
+          const float4 b = xs_at(r, cc);
+          float4 a = own[k];
+          a.x -= b.x;
+          a.y -= b.y;
+          a.z -= b.z;
+          a.w -= b.w;
+          pt_store(sm.a[s], 32 * q + r, 4 * cc, a);
         }
         fence_async_smem();
         fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.tfull[s]);
+        load_own(i + 1);  // the next item's rows, while this item is solved
       }
       if (!wait_warp(&sm.sol[s], u & 1)) break;
       fence_after_sync();
-      float x[64];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        float y[16];
-        tmem_ld16(tl + 64u * (uint32_t)s + 16u * (uint32_t)g, y);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) x[16 * g + j] = y[j];
-      }
+      rows_to_xs(s);
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.afree[s]);
-      if (row < w.rows)
+      float* dst = buf + w.base + k0 + 4 * cc;
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          *reinterpret_cast<float4*>(dst + 4 * j) = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+      for (int k = 0; k < 16; ++k) {
+        const int r = 2 * k + cr, row = r0 + 32 * q + r;
+        if (row < w.rows) *reinterpret_cast<float4*>(dst + (int64_t)row * w.npad) = xs_at(r, cc);
+      }
+      __syncwarp();  // xo is rewritten by the next item
       ++t;
     }
   }
