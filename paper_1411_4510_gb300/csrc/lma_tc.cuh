@@ -823,32 +823,54 @@ __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __re
   const bool ok = ws_product(sm, s0 - kfrom, rowA, rowB);
   if (!ok && tid == 0) atomicExch(err, 1);
   if (ok && warp < kWsProducers) {
-    constexpr int NPART = kWsProducers / 4, PW = BN / NPART;  // column groups of PW per producer warp
+    // Each producer warp subtracts the accumulator of 32 rows (its lane
+    // quadrant q) x PW columns (its part).  Tensor memory gives a row per
+    // lane; the rows go through the now idle stage ring (float4 slots
+    // swizzled by the row, conflict-free both ways) so that global memory is
+    // read and written coalesced, PW4 lanes per row.
+    constexpr int NPART = kWsProducers / 4, PW = BN / NPART, PW4 = PW / 4, RPI = 32 / PW4;
+    static_assert(PW4 == 16 || PW4 == 32, "a row part is 16 or 32 float4");
     const int q = warp & 3, part = warp >> 2;
-    const int row = r0 + q * 32 + lane;
-    float* dst = A + (int64_t)row * ld + s0;
+    float4* xs = reinterpret_cast<float4*>(&sm.st[0]) + warp * 32 * PW4;
+    auto slot = [&](int r, int c4) { return r * PW4 + (c4 ^ (r & (PW4 - 1))); };
     for (int g = 0; g < PW / 16; ++g) {
       const int c0 = part * PW + 16 * g;
       if (c0 >= ncol) break;  // warp-uniform
       float t[16];
       tmem_ld16(sm.tmem + ((uint32_t)(q * 32) << 16) + c0, t);
-      if (row < w.rows) {
-        float4 a[4];
 #pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) a[j4] = *reinterpret_cast<const float4*>(dst + c0 + 4 * j4);
-        if (s0 + c0 + 15 <= row) {
+      for (int j4 = 0; j4 < 4; ++j4)
+        xs[slot(lane, 4 * g + j4)] = make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
+    }
+    __syncwarp();
+    const int cr = lane / PW4, cc = lane % PW4;
+    const int col = part * PW + 4 * cc;  // local column of this lane's float4
+    constexpr int NR = 32 / RPI, NL = 8;  // rows per lane, loaded NL at a time before any store
+    for (int k0 = 0; k0 < NR; k0 += NL) {
+      float4 a[NL];
 #pragma unroll
-          for (int j4 = 0; j4 < 4; ++j4) {
-            a[j4].x -= t[4 * j4];
-            a[j4].y -= t[4 * j4 + 1];
-            a[j4].z -= t[4 * j4 + 2];
-            a[j4].w -= t[4 * j4 + 3];
-            *reinterpret_cast<float4*>(dst + c0 + 4 * j4) = a[j4];
+      for (int k = 0; k < NL; ++k) {
+        const int row = r0 + q * 32 + (k0 + k) * RPI + cr;
+        a[k] = (row < w.rows && col < ncol) ? *reinterpret_cast<const float4*>(A + (int64_t)row * ld + s0 + col)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < NL; ++k) {
+        const int r = (k0 + k) * RPI + cr, row = r0 + q * 32 + r;
+        if (row < w.rows && col < ncol) {
+          float* p = A + (int64_t)row * ld + s0 + col;
+          const float4 b = xs[slot(r, cc)];
+          a[k].x -= b.x;
+          a[k].y -= b.y;
+          a[k].z -= b.z;
+          a[k].w -= b.w;
+          if (s0 + col + 3 <= row) {
+            *reinterpret_cast<float4*>(p) = a[k];
+          } else {  // the diagonal: lower triangle only
+            if (s0 + col <= row) p[0] = a[k].x;
+            if (s0 + col + 1 <= row) p[1] = a[k].y;
+            if (s0 + col + 2 <= row) p[2] = a[k].z;
           }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (s0 + c0 + j <= row) dst[c0 + j] = reinterpret_cast<float*>(a)[j] - t[j];
         }
       }
     }
