@@ -359,6 +359,18 @@ int lma_profile_trace(char* names, int names_cap, double* t0_ms, double* t1_ms, 
  * the order of FP64 partial sums.                                          */
 void lma_autotune(int enabled);
 
+/* Frees the device workspace that the fit entry points (lma_fit,
+ * lma_fit_predict, lma_fit_local, lma_loglik, lma_loglik_grad) of the calling
+ * host thread keep on the current device from one call to the next: the
+ * bfloat16 planes of K_SD read by the mixed form's projection, then those of
+ * the summary rows read by its Gram (3 N rnd64(|S|) or 3 M (|S|+1) rnd64(b)
+ * 16-bit values, whichever is larger; about 25 GB at N = 2M, |S| = 2,048).
+ * Taking that much from the stream-ordered pool in every call cost tens of
+ * milliseconds of host time while the GPU waited, so the library holds it;
+ * the next fit allocates it again.  Waits for the device first.  Returns
+ * LMA_OK, or a CUDA error status.                                          */
+lma_status lma_workspace_release(void);
+
 /* Pins the launch shape of every shape class whose key starts with `prefix`
  * (the keys are those of lma_autotune_report, e.g. "fp64 factor" for the
  * FP64 factorisations of Sigma_SS and I + A, whose choices are 0 one launch

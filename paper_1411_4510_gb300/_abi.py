@@ -15,7 +15,7 @@ EXPORTED = (
     "lma_window_residual", "lma_window_rows", "lma_model_free", "lma_status_string", "lma_last_error_info",
     "lma_kernel_launch_count", "lma_profile_start", "lma_profile_stop", "lma_profile_trace", "lma_tc_gemm_check",
     "lma_global_step_noalloc", "lma_fit_local", "lma_model_local_summary", "lma_model_set_global",
-    "lma_fit_predict", "lma_predict_cov", "lma_predict_cov_blocks", "lma_model_precision", "lma_autotune", "lma_autotune_pin", "lma_autotune_report",
+    "lma_fit_predict", "lma_predict_cov", "lma_predict_cov_blocks", "lma_model_precision", "lma_autotune", "lma_autotune_pin", "lma_autotune_report", "lma_workspace_release",
 )
 
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     lib.lma_autotune.restype = None
     lib.lma_autotune_pin.argtypes = [C.c_char_p, C.c_int]
     lib.lma_autotune_pin.restype = None
+    lib.lma_workspace_release.argtypes = []
+    lib.lma_workspace_release.restype = C.c_int
     lib.lma_autotune_report.argtypes = [C.c_char_p, C.c_int]
     lib.lma_autotune_report.restype = C.c_int
     _lib = lib

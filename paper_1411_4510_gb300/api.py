@@ -396,6 +396,12 @@ def lma_autotune(enabled: bool) -> None:
     _abi.load().lma_autotune(int(bool(enabled)))
 
 
+def lma_workspace_release() -> None:
+    """Frees the device workspace the fits of this thread keep between calls
+    (see lma_workspace_release in lma.h)."""
+    _abi.check(_abi.load().lma_workspace_release())
+
+
 def lma_autotune_pin(prefix, choice: int = 0) -> None:
     """Pin the launch shape of every tuner key starting with `prefix` to
     `choice`; prefix None removes every pin (see lma_autotune_pin in lma.h)."""

@@ -651,6 +651,10 @@ extern "C" void lma_autotune(int enabled) { lma::tune::set_enabled(enabled != 0)
 
 extern "C" void lma_autotune_pin(const char* prefix, int choice) { lma::tune::pin(prefix, choice); }
 
+extern "C" lma_status lma_workspace_release(void) {
+  return guarded([] { lma::fit_workspace_release(); });
+}
+
 extern "C" int lma_autotune_report(char* buf, int cap) {
   const std::string r = lma::tune::report();
   if (buf && cap > 0) {

@@ -166,12 +166,26 @@ struct Staging {
   char* base = nullptr;
   size_t cap = 0, used = 0;
   bool hold = false;  // an enqueued call's uploads may still be in flight: no reuse before a device sync
+  std::vector<char*> retired;  // outgrown buffers whose uploads may still be in flight
   void* take(size_t bytes, cudaStream_t st);
-  void reset() {
-    if (!hold) used = 0;
-  }
+  // after the calling thread's work has completed: the buffer may be reused
+  // from its start and the outgrown ones freed
+  void reset();
 };
 Staging& staging();
+
+// Device workspace for the two largest transient buffers of a fit (the
+// bfloat16 planes of K_SD that the projection reads, then those of the
+// summary rows that the Gram reads; about 25 GB each at N = 2M, |S| = 2,048),
+// kept from call to call, one per host thread and device.  Taking buffers of
+// that size from the stream-ordered pool cost 18-21 ms of host time in every
+// call (the pool mapped them anew each time), during which the GPU went
+// idle.  Only the synchronous fit entry points use it, in stream order, and
+// their work has completed when they return, so calls never overlap on it.
+// Grows (after a device synchronisation) when a larger one is asked for;
+// lma_workspace_release frees it.
+void* fit_workspace(size_t bytes);
+void fit_workspace_release();
 
 // Upload `bytes` of host data to device memory `dst` through the staging buffer.
 inline void stage_copy(void* dst, const void* host, size_t bytes, cudaStream_t st) {

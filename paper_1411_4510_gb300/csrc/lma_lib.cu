@@ -88,23 +88,89 @@ std::vector<int> fused_test_rows(int64_t M, int64_t B, const int64_t* tptr) {
 }
 
 void* Staging::take(size_t bytes, cudaStream_t st) {
+  (void)st;
   bytes = (bytes + 255) & ~size_t(255);
   if (used + bytes > cap) {
-    // every earlier upload (of any stream of this thread) must have landed
-    (void)st;
-    LMA_CK(cudaDeviceSynchronize());
-    hold = false;
-    if (bytes > cap) {
-      if (base) cudaFreeHost(base);
+    if (hold) {
+      // enqueued calls' uploads may still be in flight: every earlier upload
+      // (of any stream of this thread) must have landed before reuse
+      LMA_CK(cudaDeviceSynchronize());
+      hold = false;
+      reset();
+    }
+    if (used + bytes > cap) {
+      // a larger buffer; the outgrown one stays until the next reset (its
+      // uploads may still be in flight), so a call never waits for the GPU here
+      if (base) retired.push_back(base);
       base = nullptr;
       cap = std::max<size_t>({bytes, 2 * cap, size_t(1) << 20});
       LMA_CK(cudaMallocHost((void**)&base, cap));
+      used = 0;
     }
-    used = 0;
   }
   void* p = base + used;
   used += bytes;
   return p;
+}
+
+void Staging::reset() {
+  if (hold) return;
+  used = 0;
+  for (char* b : retired) cudaFreeHost(b);
+  retired.clear();
+}
+
+namespace {
+struct FitWorkspace {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+FitWorkspace& fit_ws() {
+  static thread_local FitWorkspace ws[64];
+  int dev = 0;
+  LMA_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    fail(LMA_ERR_INTERNAL, "device index out of range");
+    throw Fail{};
+  }
+  return ws[dev];
+}
+}  // namespace
+
+void* fit_workspace(size_t bytes) {
+  FitWorkspace& w = fit_ws();
+  if (bytes > w.cap) {
+    if (w.p) {
+      LMA_CK(cudaDeviceSynchronize());  // the previous calls' work on it has completed anyway
+      LMA_CK(cudaFree(w.p));
+      w.p = nullptr;
+      w.cap = 0;
+    }
+    if (cudaMalloc(&w.p, bytes) != cudaSuccess) {
+      // the stream-ordered pool keeps freed memory (release threshold at
+      // its maximum): hand it back and try once more
+      cudaGetLastError();
+      w.p = nullptr;
+      int dev = 0;
+      cudaMemPool_t pool;
+      LMA_CK(cudaGetDevice(&dev));
+      LMA_CK(cudaDeviceSynchronize());
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+      LMA_CK(cudaMalloc(&w.p, bytes));
+    }
+    w.cap = bytes;
+  }
+  return w.p;
+}
+
+void fit_workspace_release() {
+  FitWorkspace& w = fit_ws();
+  if (w.p) {
+    LMA_CK(cudaDeviceSynchronize());
+    LMA_CK(cudaFree(w.p));
+  }
+  w.p = nullptr;
+  w.cap = 0;
 }
 
 Staging& staging() {
@@ -200,16 +266,18 @@ static void proj_tc(cudaStream_t st, const char* name, const uint16_t* Ap, int64
 // the planes of L_SS^-1 (bf16x6); otherwise K_SD is formed and multiplied by
 // ET = L_SS^-T on the CUDA cores.
 template <typename T>
-static void project(const ModelCore& mc, const T* xsP, int64_t npts, T* out, Arena& tmp, cudaStream_t st, int* err) {
+static void project(const ModelCore& mc, const T* xsP, int64_t npts, T* out, Arena& tmp, cudaStream_t st, int* err,
+                    bool use_workspace = false) {
   const int64_t s = mc.s;
   const int d = (int)mc.d;
   if (npts == 0) return;
   if (sizeof(T) == 4 && mc.linv3) {
-    uint16_t* Ap = tmp.alloc<uint16_t>((size_t)3 * npts * mc.ldk);
+    const size_t nA = (size_t)3 * npts * mc.ldk;
+    uint16_t* Ap = use_workspace ? (uint16_t*)fit_workspace(nA * sizeof(uint16_t)) : tmp.alloc<uint16_t>(nA);
     launch("k_kds_bf3", pad_dim(d) == 8 ? k_kds_bf3<8> : k_kds_bf3<MAXD>, dim3((unsigned)(mc.ldk / 64), nblk(npts, 32)),
            256, 0, st, (const float*)xsP, npts, d, (const float*)mc.ssT, (int)s, (float)mc.ss2, mc.ldk, Ap);
     proj_tc(st, "k_proj_tc", Ap, npts, mc.linv3, mc.brows, (int)s, mc.ldk, (float*)out, s, err);
-    tmp.free_one(Ap);
+    if (!use_workspace) tmp.free_one(Ap);
     return;
   }
   T* Kds = tmp.alloc<T>(npts * s);
@@ -590,8 +658,8 @@ void Impl<T>::prepare(ModelCore& mc, const lma_problem* P, const lma_hyper* H, A
     launch("k_linv_bf3", k_linv_bf3, nblk((int64_t)mc.brows * mc.ldk), NT, 0, st, (const double*)kb, (int64_t)npS,
            (int)s, mc.brows, mc.ldk, mc.linv3);
   }
-  // V = L_SS^-1 Sigma_SD, point-major
-  project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2);
+  // V = L_SS^-1 Sigma_SD, point-major (the K_SD planes in the fit workspace)
+  project<T>(mc, xsT, n, Vt, tmp, st, mc.flags + 2, true);
 }
 
 // Local part of a fit: windows of blocks [w_begin, own_end) are formed and
@@ -713,8 +781,10 @@ void Impl<T>::fit_local(ModelCore& mc, const lma_problem* P, const lma_hyper* H,
         const Win& w = mc.wins[m - w_begin];
         kmax = std::max(kmax, (int)roundup(w.n - w.nB, bf6::KC));
       }
-      // the summary rows in three bfloat16 planes (bf16x6 products, lma_bf6.cuh)
-      uint16_t* sb3 = tmp.alloc<uint16_t>((size_t)3 * nown * se * kmax);
+      // the summary rows in three bfloat16 planes (bf16x6 products,
+      // lma_bf6.cuh), in the fit workspace (the projection's planes in it
+      // were consumed earlier on this stream)
+      uint16_t* sb3 = (uint16_t*)fit_workspace(sizeof(uint16_t) * (size_t)3 * nown * se * kmax);
       launch("k_split_summary", k_split_summary_bf3, dim3((unsigned)((se + 7) / 8), (unsigned)nown), dim3(32, 8), 0,
              st, wown, (const float*)wbuf, se, (int)nown, kmax, sb3);
       const CUtensorMap sb = bf16_tensor_map(sb3, 3 * nown * se, kmax);
