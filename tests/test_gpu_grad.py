@@ -2,7 +2,7 @@
 oracle's adjoint, central finite differences and the autograd wrapper.
 
 Tolerance for the FP64 form: 1e-9 relative, norm-wise and element-wise (the
-spec figure; measured at most 2.4e-13 on these cases).  Mixed form:
+accuracy target; measured at most 2.4e-13 on these cases).  Mixed form:
 the adjoint inherits the FP32 error of the residual precision R_W^-1 through
 every term; it is held to about three times the largest error measured on
 the GB300 at the default jitter (tests/_parity.py reports it).

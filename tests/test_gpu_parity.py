@@ -3,9 +3,9 @@
 Every check is norm-wise and element-wise (tests/_parity.py; LMA_PARITY_REPORT
 records the measured errors).
 
-Tolerances.  FP64 form: 1e-9 relative (the benchmark spec's figure), norm-wise and
+Tolerances.  FP64 form: 1e-9 relative (the accuracy target), norm-wise and
 element-wise.  Mixed form: predictive mean 1e-4 norm-wise relative and RMSE
-within 0.1 % of the oracle's (spec figures); the other bounds are about
+within 0.1 % of the oracle's (the accuracy targets); the other bounds are about
 three times the largest error measured on the GB300 over these cases at the
 default jitter 1e-6 (cond(Sigma_SS) up to 4e7):
   mean element-wise (max |dmean| / max |mean|)   measured 7.5e-5 -> 3e-4

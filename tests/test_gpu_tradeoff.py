@@ -2,7 +2,7 @@
 problem: more support points or a higher Markov order do not make the test
 RMSE worse (within 3%), every row carries a positive time, and two cells'
 RMSE and log-likelihood match the FP64 oracle's for the same (|S|, B)
-(RMSE within 0.1 %, the benchmark spec's figure; log-likelihood within the mixed
+(RMSE within 0.1 %, the accuracy target; log-likelihood within the mixed
 bound of test_gpu_parity.py)."""
 import pytest
 
