@@ -161,3 +161,19 @@ def _hc(f, cv, p, B):
         Z = P @ (cv.K(p.X[rows], Xu) - WJ.T @ Wu)
         out[n] = sla.solve_triangular(f.Lc, WJ @ Z - Wu, lower=True)
     return out
+
+
+@pytest.mark.parametrize("noisy", [True, False])
+def test_full_markov_order_is_the_full_gp_covariance(noisy):
+    """B = M-1: the approximation is exact (R-bar = R), so the covariance
+    between any two test blocks is the textbook GP posterior covariance."""
+    p = make_random_problem(11, (9, 12, 7, 10, 8), d=2, s=6, B=4, test_sizes=(3, 0, 4, 2, 3))
+    f = O2.fit(p)
+    full = O1.full_gp(p, noisy=noisy)["cov"]
+    tp = p.test_block_ptr
+    pairs = _all_pairs(p)
+    scale = np.abs(full).max()
+    for (a, b), C in zip(pairs, O2.predict_cov_blocks(f, pairs, noisy=noisy)):
+        ref = full[tp[a]:tp[a + 1], tp[b]:tp[b + 1]]
+        if ref.size:
+            assert np.abs(C - ref).max() <= 1e-9 * scale, (a, b)
