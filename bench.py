@@ -118,14 +118,13 @@ def kernel_work(p, B, fused=True):
     tp = p.test_block_ptr
     nu = [int(tp[m + 1] - tp[m]) for m in range(M)]
     trows = [sum(nu[n] for n in range(m, min(m + B, M - 1) + 1)) for m in range(M)] if fused else [0] * M
-    step = wide = mid = tri = below = 0.0
+    wide = mid = tri = below = 0.0
     SP, HP = 256, 128  # the 256-wide update applies [0, kb), the 128-wide one [kb, kh), the 64-wide steps [kh, k0)
     for (n, b, nb), t in zip(ws, trows):
         rows = n + s + 1 + t
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
             kb, kh = (k0 // SP) * SP, (k0 // HP) * HP
-            step += 2.0 * ((rows - k0) * w - w * (w - 1) / 2.0) * (k0 - kh)
             below += 2.0 * max(0, rows - k0 - w) * w * (k0 - kh)
             tri += 2.0 * max(0, rows - k0 - w) * w * w / 2.0
             if k0 == kb and kb > 0:
@@ -150,9 +149,8 @@ def kernel_work(p, B, fused=True):
     f64 = 2.0 * s ** 3 / 3.0             # Cholesky of Sigma_SS and of I + A, s^3 / 6 multiply-adds each
     # the panel steps' update (columns [kh, k0), at most 64) of the rows below
     # the diagonal block and the panel solves run in k_chol_panel_pt
-    # (k_chol_step_tc updates and factorises the diagonal block itself); the
-    # alternative form k_chol_panel2_tc does the diagonal blocks' update too
-    return {"k_chol_panel_pt": below + tri, "k_chol_panel2_tc": step + tri, "k_chol_wide": wide,
+    # (k_chol_step_tc updates and factorises the diagonal block itself)
+    return {"k_chol_panel_pt": below + tri, "k_chol_wide": wide,
             "k_chol_mid": mid, "k_resid_bf6": resid,
             "k_gram_bf6": gram, "k_pred_rhs_bf6": prhs, "k_pred_accum_tc": pacc, "k_proj": proj,
             "k_proj_tc": proj, "k_var_gemm": var,
@@ -187,7 +185,7 @@ def sources_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-TENSOR_KERNELS = {"k_chol_panel_pt", "k_chol_panel2_tc", "k_chol_wide", "k_chol_mid", "k_pred_sweep_tc",
+TENSOR_KERNELS = {"k_chol_panel_pt", "k_chol_wide", "k_chol_mid", "k_pred_sweep_tc",
                   "k_pred_accum_tc", "k_bwd_sweep_tc", "k_grad_G_tc",
                   "k_grad_gv_tc", "k_grad_rhs_tc"}
 BF16X6_KERNELS = {"k_proj_tc", "k_gram_bf6", "k_resid_bf6", "k_pred_rhs_bf6"}   # bfloat16 x 6 split products (the variance term shares the name k_var_gemm)

@@ -181,17 +181,6 @@ Staging& staging() {
 static size_t tc_chol_smem() { return sizeof(tc::TcSmem<64>) + tc::kTcAlignSlack; }
 static size_t pt_smem() { return sizeof(tc::PtSmem) + tc::kTcAlignSlack; }
 
-// Form of the sweep's 64-wide panel level: 1 = the persistent panel kernel
-// (k_chol_panel_pt, after a diagonal-block launch per panel), 2 = one
-// launch per panel that also factorises the next diagonal block
-// (k_chol_panel2_tc).  LMA_PANEL_FORM selects it (default 1).
-static int panel_form() {
-  static const int f = [] {
-    const char* e = getenv("LMA_PANEL_FORM");
-    return (e && atoi(e) == 2) ? 2 : 1;
-  }();
-  return f;
-}
 template <int BN>
 static size_t wide_smem() { return sizeof(tc::WsSmem<2, BN>) + tc::kTcAlignSlack; }
 static size_t tc_resid_smem() { return sizeof(CompSmem<RB>) + tc::kTcAlignSlack; }
@@ -327,7 +316,6 @@ void Impl<T>::setup_attributes() {
     set_smem_attr<T>();
     set_smem_attr<double>();
     cudaFuncSetAttribute(k_chol_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
-    cudaFuncSetAttribute(k_chol_panel2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_chol_panel_pt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pt_smem());
     cudaFuncSetAttribute(k_pred_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_chol_smem());
     cudaFuncSetAttribute(k_gram_bf6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
@@ -385,32 +373,16 @@ void chol_sweep(cudaStream_t st, const std::vector<Win>& wins, Win* wins_d, T* b
           launch_pdl("k_chol_mid", k_chol_wide<128>, dim3(nw, gy), tc::kWsThreads, wide_smem<128>(), st, wins_d,
                      (float*)buf, kh, kb, tc_err);
         }
-        if (panel_form() == 1) {
-          // every panel: its diagonal block (the first panel of a 128-column
-          // group has every column to its left applied; the second adds the
-          // first's 64 columns), then the persistent kernel updates the rows
-          // below with the same columns and solves them
-          launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, 1), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-                     (float*)dinv, info, kp, kh, tc_err);
-          if (maxrows - (kp + 1) * TB > 0) {
-            const int ntile = (maxrows - (kp + 1) * TB + 127) / 128;
-            launch_pdl("k_chol_panel_pt", k_chol_panel_pt, persistent_grid((size_t)ntile * nw), tc::kPtThreads,
-                       pt_smem(), st, wins_d, (int)nw, (float*)buf, (const float*)dinv, kp, kh, ntile, tc_err);
-          }
-        } else {
-          // first panel of a 128-column group: its diagonal block has every
-          // column to its left applied, so only the row tile holding it runs
-          // (factorisation); k_chol_panel2_tc then solves the rows below and
-          // finishes the group's second diagonal block, whose panel needs only
-          // the first panel's columns (K = 64) before its own solve
-          if (k0 == kh)
-            launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, 1), 256, tc_chol_smem(), st, wins_d, (float*)buf,
-                       (float*)dinv, info, kp, kh, tc_err);
-          if (maxrows - (kp + 1) * TB > 0) {
-            const unsigned gx = (unsigned)((maxrows - (kp + 1) * TB + 127) / 128);
-            launch_pdl("k_chol_panel2_tc", k_chol_panel2_tc, dim3(gx, nw), 256, tc_chol_smem(), st, wins_d,
-                       (float*)buf, (float*)dinv, info, kp, kh, k0 == kh ? 1 : 0, tc_err);
-          }
+        // every panel: its diagonal block (the first panel of a 128-column
+        // group has every column to its left applied; the second adds the
+        // first's 64 columns), then the persistent kernel updates the rows
+        // below with the same columns and solves them
+        launch_pdl("k_chol_step_tc", k_chol_step_tc, dim3(nw, 1), 256, tc_chol_smem(), st, wins_d, (float*)buf,
+                   (float*)dinv, info, kp, kh, tc_err);
+        if (maxrows - (kp + 1) * TB > 0) {
+          const int ntile = (maxrows - (kp + 1) * TB + 127) / 128;
+          launch_pdl("k_chol_panel_pt", k_chol_panel_pt, persistent_grid((size_t)ntile * nw), tc::kPtThreads,
+                     pt_smem(), st, wins_d, (int)nw, (float*)buf, (const float*)dinv, kp, kh, ntile, tc_err);
         }
       } else {
         launch("k_chol_step", k_chol_step<T>, dim3(maxrt - kp, nw), NT, sizeof(CholSmem<T>), st, wins_d, buf, dinv,

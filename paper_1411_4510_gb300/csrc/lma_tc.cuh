@@ -882,136 +882,6 @@ __global__ void __launch_bounds__(tc::kWsThreads, 1) k_chol_wide(const Win* __re
 
 namespace lma {
 
-// Update and solve of column panel kp in one pass (mixed form), for the rows
-// below its diagonal block: CTA (row tile x, window y) owns rows
-// [k0 + 64 + 128 x, ... + 128) and computes
-//   T = A_{rows, panel} - A_{rows, kfrom:k0} A_{panel, kfrom:k0}^T   (skipped when kfrom = k0)
-//   A_{rows, panel} <- T inv(L_kk)^T
-// with both products on tcgen05 (3xTF32); columns [0, kfrom) were applied
-// by the wider updates and inv(L_kk) is in dinv.  With `next`, row tile 0
-// then also finishes panel kp + 1's diagonal block: its rows are the tile's
-// first 64, whose panel-kp values it has just written, so
-//   D = A_{kp+1, kp+1} - L_{kp+1, kp} L_{kp+1, kp}^T
-// is the block with every column left of panel kp + 1 applied (those left of
-// panel kp came from the wider updates), and the CTA factorises it into
-// L_{kp+1, kp+1} and inv(L_{kp+1, kp+1}).  Row tile 0 of every window comes
-// first in launch order, so the factorisations start in the first wave.
-__global__ void __launch_bounds__(256, 2) k_chol_panel2_tc(const Win* __restrict__ wins, float* __restrict__ buf,
-                                                        float* __restrict__ dinv, int* __restrict__ info, int kp,
-                                                        int kfrom, int next, int* __restrict__ err) {
-  grid_dep_wait();
-  grid_dep_launch();
-  using namespace tc;
-  const Win w = wins[blockIdx.y];
-  const int k0 = kp * TB;
-  if (k0 >= w.npad) return;
-  const int r0 = k0 + TB + blockIdx.x * 128;
-  if (r0 >= w.rows) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TcSmem<64>& sm = tc_smem<64>(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float* A = buf + w.base;
-  const int64_t ld = w.npad;
-  if (tid == 0) {
-    mbar_init(&sm.bar[0], 1);
-    mbar_init(&sm.bar[1], 1);
-    mbar_fence_init();
-  }
-  if (warp == 0) tmem_alloc(&sm.tmem, 64);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = sm.tmem;
-  TcPipe pipe;
-  const int q = warp & 3, half = warp >> 2;
-  const int rl = q * 32 + lane, row = r0 + rl;
-  const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + half * 32;
-  float* myrow = A + (int64_t)row * ld + k0 + half * 32;
-  bool ok = true;
-  const int K = k0 - kfrom;
-  if (K > 0) {
-    auto rowA = [&](int r) -> const float* {
-      return r0 + r < w.rows ? A + (int64_t)(r0 + r) * ld + kfrom : nullptr;
-    };
-    auto rowB = [&](int c) -> const float* { return A + (int64_t)(k0 + c) * ld + kfrom; };
-    ok = tile_product<64>(sm, pipe, tmem, K, rowA, rowB);
-    if (ok) {
-      float v[32], t[16];
-      tmem_ld16(taddr, t);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = t[j];
-      tmem_ld16(taddr + 16, t);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[16 + j] = t[j];
-      if (row < w.rows) {
-        float4 av[8];
-#pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) av[j4] = *reinterpret_cast<const float4*>(myrow + 4 * j4);
-#pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          float4 a = av[j4];
-          a.x -= v[4 * j4 + 0];
-          a.y -= v[4 * j4 + 1];
-          a.z -= v[4 * j4 + 2];
-          a.w -= v[4 * j4 + 3];
-          *reinterpret_cast<float4*>(myrow + 4 * j4) = a;
-        }
-      }
-    }
-    fence_before_sync();
-    __syncthreads();
-  }
-  if (ok) {
-    const float* Dv = dinv + w.dinv + (int64_t)kp * TB * TB;
-    auto rowT = [&](int r) -> const float* { return r0 + r < w.rows ? A + (int64_t)(r0 + r) * ld + k0 : nullptr; };
-    auto rowD = [&](int c) -> const float* { return Dv + (int64_t)c * TB; };
-    ok = tile_product<64>(sm, pipe, tmem, TB, rowT, rowD);
-    if (ok) {
-      float t[16];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        tmem_ld16(taddr + 16 * h, t);
-        if (row < w.rows)
-#pragma unroll
-          for (int j4 = 0; j4 < 4; ++j4)
-            *reinterpret_cast<float4*>(myrow + 16 * h + 4 * j4) =
-                make_float4(t[4 * j4], t[4 * j4 + 1], t[4 * j4 + 2], t[4 * j4 + 3]);
-      }
-    }
-    fence_before_sync();
-    __syncthreads();
-  }
-  const bool diag = ok && next && blockIdx.x == 0 && k0 + TB < w.npad;
-  if (diag) {
-    // D = A_{kp+1, kp+1} - X X^T over the 64 panel-kp columns of rows [k0 + 64, k0 + 128)
-    const int d0 = k0 + TB;
-    auto rowX = [&](int r) -> const float* { return r < TB ? A + (int64_t)(d0 + r) * ld + k0 : nullptr; };
-    auto rowY = [&](int c) -> const float* { return A + (int64_t)(d0 + c) * ld + k0; };
-    ok = tile_product<64>(sm, pipe, tmem, TB, rowX, rowY);
-  }
-  float* scratch = reinterpret_cast<float*>(&sm.st[0]);
-  float(*Dm)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(scratch);
-  if (diag && ok) {
-    float t[16];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld16(taddr + 16 * h, t);  // whole warps; only rows < 64 are used
-      if (rl < TB) {
-        const float* src = A + (int64_t)(k0 + TB + rl) * ld + k0 + TB + half * 32 + 16 * h;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) Dm[rl][half * 32 + 16 * h + j] = src[j] - t[j];
-      }
-    }
-  }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 64);
-  if (diag && ok)
-    diag_factor<float>(Dm, A + (int64_t)(k0 + TB) * ld + k0 + TB, ld, dinv + w.dinv + (int64_t)(kp + 1) * TB * TB,
-                       info + blockIdx.y, k0 + TB);
-}
-
 namespace tc {
 
 // Persistent panel kernel (below): 8 producer warps, 1 MMA warp, 4 epilogue

@@ -19,7 +19,7 @@ def test_work_model_c2():
     assert all(v > 0 for v in fused.values())
     assert "k_pred_sweep_tc" not in fused and plain["k_pred_sweep_tc"] > 0
     # the test rows add work to the fit's sweep only
-    for k in ("k_chol_panel_pt", "k_chol_panel2_tc", "k_chol_wide", "k_chol_mid"):
+    for k in ("k_chol_panel_pt", "k_chol_wide", "k_chol_mid"):
         assert fused[k] > plain[k]
     for k in ("k_resid_bf6", "k_gram_bf6", "k_pred_rhs_bf6", "k_proj", "k_f64_chain"):
         assert fused[k] == plain[k]
@@ -37,13 +37,13 @@ def test_work_model_c2():
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
             tri += max(0, rows - k0 - w) * w * w
-    panel_update = plain["k_chol_panel2_tc"] - tri
-    assert abs(plain["k_chol_wide"] + plain["k_chol_mid"] + panel_update - full) <= 1e-9 * full
-    # the persistent form leaves the diagonal blocks' update (64 x 64 lower
-    # triangles, K = k0 - kh) to k_chol_step_tc
+    # the persistent panel kernel's update of the rows below each diagonal
+    # block plus the diagonal blocks' own update (64 x 64 lower triangles,
+    # K = k0 - kh, left to k_chol_step_tc) complete the sum
     diag = 0.0
     for n, b, nb in bench.window_sizes(p.block_ptr, 1):
         for k0 in range(0, n, 64):
             w = min(64, n - k0)
             diag += 2.0 * (w * w - w * (w - 1) / 2.0) * (k0 - (k0 // 128) * 128)
-    assert abs(plain["k_chol_panel2_tc"] - plain["k_chol_panel_pt"] - diag) <= 1e-9 * full
+    panel_update = plain["k_chol_panel_pt"] - tri
+    assert abs(plain["k_chol_wide"] + plain["k_chol_mid"] + panel_update + diag - full) <= 1e-9 * full
