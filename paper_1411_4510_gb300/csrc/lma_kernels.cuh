@@ -838,12 +838,6 @@ __global__ void k_copy_block(const double* __restrict__ src, int64_t ld, int s, 
   dst[e] = (T)src[(int64_t)i * ld + j];
 }
 
-template <typename T>
-__global__ void k_convert(const double* __restrict__ src, int64_t n, T* __restrict__ dst) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) dst[e] = (T)src[e];
-}
-
 // Per window: L^-1 e over the window, with e = r - Vt beta (the residual
 // after the support-set fit), from the extra rows: X0 - sum_k beta_k X_{1+k}.
 template <typename T>

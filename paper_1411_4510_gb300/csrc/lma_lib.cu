@@ -323,7 +323,6 @@ void Impl<T>::setup_attributes() {
     cudaFuncSetAttribute(k_resid_bf6<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
     cudaFuncSetAttribute(k_pred_rhs_bf6<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
     cudaFuncSetAttribute(k_pred_rhs_bf6<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf6::smem_bytes());
-    cudaFuncSetAttribute(k_pred_accum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_pred_accum_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_resid_smem());
     cudaFuncSetAttribute(k_chol_wide<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<256>());
     cudaFuncSetAttribute(k_chol_wide<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<128>());

@@ -1564,58 +1564,6 @@ __device__ __forceinline__ float dist2(const float (&a)[D], const float* b) {
 // Input dimension padded for the unrolled epilogues (a multiple of 4).
 __host__ __device__ constexpr int pad_dim(int d) { return d <= 8 ? 8 : MAXD; }
 
-
-
-
-// h[u][k] = sum over the pairs (n, m) of test block n of
-// sum_{c in kept columns} P[u][c] X_{1+k}[c]  -  Vu[u][k]  on the tensor
-// cores (mixed form): P rows are the swept right-hand sides, X_{1+k} the
-// extra rows (L^-1 Vt_W)^T of window m, so the sum over a pair is a product
-// with K over the window's kept columns [c0, c1).  Items: x = first pair of
-// the test block, y = pair count, z = 128-row u tile, w = RB-wide s tile.
-__global__ void __launch_bounds__(comp_threads<RB>(), 1) k_pred_accum_tc(const Pair* __restrict__ pairs,
-                                                                       const int4* __restrict__ items,
-                                                                       const Win* __restrict__ wins,
-                                                                       const float* __restrict__ buf,
-                                                                       const float* __restrict__ P,
-                                                                       const float* __restrict__ Vu, int s,
-                                                                       float* __restrict__ h, int* __restrict__ err) {
-  using namespace tc;
-  const int4 it = items[blockIdx.x];
-  const int u0 = it.z * 128, k0 = it.w * RB;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  CompSmem<RB>& sm = comp_smem<RB>(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  comp_setup(sm);
-  CompState cs;
-  float hi[32], lo[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
-  bool ok = true;
-  for (int pi = 0; pi < it.y && ok; ++pi) {
-    const Pair pr = pairs[it.x + pi];
-    const Win w = wins[pr.win];
-    const float* Pp = P + pr.pbase;
-    const float* E = buf + w.base + (int64_t)w.npad * w.npad;
-    const int64_t ld = w.npad;
-    auto rowA = [&](int r) -> const float* { return (u0 + r < pr.nu) ? Pp + (int64_t)(u0 + r) * ld : nullptr; };
-    auto rowB = [&](int c) -> const float* { return (k0 + c < s) ? E + (int64_t)(1 + k0 + c) * ld : nullptr; };
-    ok = comp_product<RB, true>(sm, cs, pr.c0, pr.c1, rowA, rowB, hi, lo);
-  }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  const Pair first = pairs[it.x];
-  const int q = warp & 3, half = warp >> 2;
-  const int uu = u0 + q * 32 + lane;
-  const int kg = k0 + half * 32;
-  if (ok && warp < RB / 8 && uu < first.nu) {
-    const int64_t row = first.u0 + uu;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (kg + j < s) h[row * s + kg + j] = (hi[j] + lo[j]) - Vu[row * s + kg + j];
-  }
-  comp_teardown(sm);
-}
-
 // The h accumulation per window (mixed form): the test rows that use window m
 // (the pairs (n, m), n = m .. m + B) share its extra rows X_{1+k} as the B
 // operand, so one 128-row tile covers the test points of several blocks.
