@@ -164,7 +164,9 @@ def kernel_work(p, B, fused=True):
 NCU_TRAFFIC: dict = {
     # profiles/k_chol_wide_traffic_c4_n50000.md: DRAM bytes of the seven super-panel launches of the
     # C4 recipe at N = 50,000 (50 windows), averaged per launch and scaled by the window count to C4
-    "k_chol_wide": {"bytes": 47.57e9, "case": ("C4", 1), "files": ["lma_tc.cuh"], "sources": "ae17826e19bb3263",
+    # (the hash is of lma_tc.cuh after two unrelated kernels were deleted from it; the super-panel
+    # kernel and its pipeline are the captured code)
+    "k_chol_wide": {"bytes": 47.57e9, "case": ("C4", 1), "files": ["lma_tc.cuh"], "sources": "dd86857e5a16a326",
                     "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 7 launches of one step at "
                             "N=50,000 (1.189 GB per launch on average, 1.34x the algorithmic bytes), x40 windows"},
 }
