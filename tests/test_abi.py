@@ -59,3 +59,39 @@ def test_invalid_arguments_rejected_on_host(lib):
         with pytest.raises(L.LMAError) as ei:
             L.lma_fit(**kw)
         assert ei.value.status == 1, bad
+
+
+def test_window_rows_follow_the_markov_blanket(lib):
+    """lma_window_rows (host arithmetic only): |D_m u D^B_m| with the blanket
+    D^B_m = D_{m+1} .. D_{min(m+B, M-1)} truncated at the last block (Sec. 3);
+    0 for an invalid block index."""
+    import ctypes as C
+    import numpy as np
+    from paper_1411_4510_gb300 import _abi
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        M = int(rng.integers(1, 9))
+        sizes = rng.integers(1, 20, size=M)
+        ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        B = int(rng.integers(0, M))
+        prob = _abi.lma_problem()
+        prob.n, prob.d, prob.s, prob.m_blocks, prob.markov_order = int(ptr[-1]), 1, 1, M, B
+        prob.block_ptr = ptr.ctypes.data
+        for m in range(M):
+            last = min(m + B, M - 1)
+            assert lib.lma_window_rows(C.byref(prob), m) == int(ptr[last + 1] - ptr[m])
+        assert lib.lma_window_rows(C.byref(prob), M) == 0
+        assert lib.lma_window_rows(C.byref(prob), -1) == 0
+
+
+def test_prediction_calls_reject_a_missing_model_on_host(lib):
+    """The prediction entry points check their arguments before any device
+    work: a null model is LMA_ERR_INVALID_ARG (1), also without a GPU."""
+    import numpy as np
+    tp = np.array([0, 0], dtype=np.int64)
+    pairs = np.array([0, 0], dtype=np.int64)
+    assert lib.lma_predict(None, 0, None, tp.ctypes.data, 1, 0, None, None) == 1
+    assert lib.lma_predict_cov(None, 0, None, tp.ctypes.data, 1, 0, None, None, None) == 1
+    assert lib.lma_predict_cov_blocks(None, 0, None, tp.ctypes.data, 1, 0, 1, pairs.ctypes.data, None, None, None) == 1
+    assert lib.lma_predict_async(None, 0, None, tp.ctypes.data, 1, None, None) == 1
+    assert lib.lma_model_wait(None) == 1
