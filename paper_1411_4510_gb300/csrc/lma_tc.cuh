@@ -954,10 +954,9 @@ __device__ __forceinline__ void pt_mma(uint32_t d, const PtTileA& a, const PtTil
 // and stores.  Every wait is bounded; on a timeout the CTA raises *err,
 // every role leaves its loop and the MMA warp waits for its products before
 // the tensor memory is freed.
-__global__ void __maxnreg__(128) k_chol_panel_pt(const Win* __restrict__ wins, int nwin,
-                                                                   float* __restrict__ buf,
-                                                                   const float* __restrict__ dinv, int kp, int kfrom,
-                                                                   int ntile, int* __restrict__ err) {
+__global__ void __maxnreg__(128) k_chol_panel_pt(const Win* __restrict__ wins, int nwin, float* __restrict__ buf,
+                                                 const float* __restrict__ dinv, int kp, int kfrom, int ntile,
+                                                 int* __restrict__ err) {
   grid_dep_wait();
   grid_dep_launch();
   using namespace tc;
